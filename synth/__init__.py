@@ -1,0 +1,183 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module draws random numbers and builds input arrays; it holds none of the
+SPIIR arithmetic (no filtering, no antenna patterns, no delays, no coherent
+statistic).  Every draw is made in FP64 by NumPy's PCG64 and then rounded to
+FP32 where the hot path takes FP32; the FP32 values are the canonical inputs
+for both the CUDA path and the FP64 oracle.
+
+Workloads (the paper's O2 data and LVC template banks are not available, so
+these synthetic recipes stand in for them):
+
+* ``tiny``      2 detectors, 32768 samples of white noise at 2048 Hz, one bank
+                of 4 templates x 64 filters, HEALPix nside 4, unit noise weights.
+* ``online``    3 detectors, 2048 Hz noise in 1 s chunks, 1024 templates with
+                200..900 filters each, delays up to 2 s, nside 16, noise
+                weights uniform in [0.5, 2].
+* ``multirate`` 8 banks of uneven size over bands at 2048/512/128 Hz.
+* ``chirp``     Newtonian complex chirps used as targets for the adjoint.
+
+Filter coefficients follow one recipe: |a1| uniform in [0.9, 0.999] with a
+uniform phase, b0 complex normal (unit variance) scaled by 1/sqrt(F), integer
+delay uniform in [0, d_max].
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 20110678
+EARTH_RADIUS_M = 6371.0e3
+
+# stream identifiers: one independent PCG64 stream per purpose
+_STREAMS = {"detectors": 1, "noise": 2, "bank": 3, "sigma": 4, "snr": 5, "chirp": 6,
+            "bands": 7, "inject": 8, "misc": 9}
+
+
+def rng(config_index: int, purpose: str, sub: int = 0) -> np.random.Generator:
+    """Independent generator for (workload, purpose, sub-stream)."""
+    ss = np.random.SeedSequence([SEED_BASE + int(config_index), _STREAMS[purpose], int(sub)])
+    return np.random.Generator(np.random.PCG64(ss))
+
+
+@dataclasses.dataclass
+class Detectors:
+    pos_m: np.ndarray    # [n_det][3] fp64, Earth-fixed position (m)
+    arm_x: np.ndarray    # [n_det][3] fp64, unit vector of arm X
+    arm_y: np.ndarray    # [n_det][3] fp64, unit vector of arm Y (orthogonal to X, tangent plane)
+
+
+def detectors(config_index: int, n_det: int) -> Detectors:
+    """Detectors placed uniformly on a 6371 km sphere with seeded arm azimuths.
+
+    Arm X = cos(alpha) e_north + sin(alpha) e_east with alpha uniform; arm Y =
+    r_hat x X, so the arms are orthogonal and tangent to the sphere.
+    """
+    g = rng(config_index, "detectors")
+    pos = np.empty((n_det, 3))
+    ax = np.empty((n_det, 3))
+    ay = np.empty((n_det, 3))
+    for i in range(n_det):
+        cz = g.uniform(-1.0, 1.0)
+        lon = g.uniform(0.0, 2.0 * math.pi)
+        sz = math.sqrt(max(0.0, 1.0 - cz * cz))
+        rhat = np.array([sz * math.cos(lon), sz * math.sin(lon), cz])
+        east = np.array([-math.sin(lon), math.cos(lon), 0.0])
+        north = np.cross(rhat, east)
+        alpha = g.uniform(0.0, 2.0 * math.pi)
+        x = math.cos(alpha) * north + math.sin(alpha) * east
+        x /= np.linalg.norm(x)
+        y = np.cross(rhat, x)
+        y /= np.linalg.norm(y)
+        pos[i] = EARTH_RADIUS_M * rhat
+        ax[i] = x
+        ay[i] = y
+    return Detectors(pos, ax, ay)
+
+
+def white_noise(config_index: int, n_det: int, n: int, sub: int = 0) -> np.ndarray:
+    """Unit-variance white Gaussian strain, [n_det][n] float32."""
+    g = rng(config_index, "noise", sub)
+    return g.standard_normal((n_det, n)).astype(np.float32)
+
+
+@dataclasses.dataclass
+class Bank:
+    offsets: np.ndarray  # [T+1] int64, CSR over templates
+    a1: np.ndarray       # [F] complex64 feedback coefficient
+    b0: np.ndarray       # [F] complex64 feedforward coefficient
+    delay: np.ndarray    # [F] int32 integer delay in samples
+
+    @property
+    def n_templates(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def n_filters(self) -> int:
+        return int(self.offsets[-1])
+
+    def counts(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+    def subset(self, templates) -> "Bank":
+        """Bank made of the listed templates (in that order)."""
+        idx = []
+        off = [0]
+        for t in templates:
+            lo, hi = int(self.offsets[t]), int(self.offsets[t + 1])
+            idx.extend(range(lo, hi))
+            off.append(off[-1] + hi - lo)
+        idx = np.asarray(idx, dtype=np.int64)
+        return Bank(np.asarray(off, dtype=np.int64), self.a1[idx].copy(), self.b0[idx].copy(),
+                    self.delay[idx].copy())
+
+
+def random_bank(g: np.random.Generator, counts, d_max: int, mag=(0.9, 0.999),
+                phase=(0.0, 2.0 * math.pi), d_min: int = 0) -> Bank:
+    """Bank with the given filter count per template (recipe in the module docstring)."""
+    counts = np.asarray(counts, dtype=np.int64)
+    off = np.zeros(counts.size + 1, dtype=np.int64)
+    np.cumsum(counts, out=off[1:])
+    F = int(off[-1])
+    r = g.uniform(mag[0], mag[1], F)
+    ph = g.uniform(phase[0], phase[1], F)
+    a1 = (r * np.exp(1j * ph)).astype(np.complex64)
+    scale = np.repeat(1.0 / np.sqrt(np.maximum(counts, 1)), counts)
+    b0 = ((g.standard_normal(F) + 1j * g.standard_normal(F)) / math.sqrt(2.0) * scale).astype(np.complex64)
+    d = g.integers(d_min, d_max + 1, F).astype(np.int32)
+    return Bank(off, a1, b0, d)
+
+
+def noise_weights(config_index: int, n_det: int, lo: float, hi: float) -> np.ndarray:
+    if lo == hi:
+        return np.full(n_det, lo, dtype=np.float64)
+    return rng(config_index, "sigma").uniform(lo, hi, n_det)
+
+
+def complex_gaussian_snr(config_index: int, shape, sub: int = 0) -> np.ndarray:
+    """i.i.d. complex Gaussian SNR samples with E|z|^2 = 2 (complex64)."""
+    g = rng(config_index, "snr", sub)
+    return (g.standard_normal(shape) + 1j * g.standard_normal(shape)).astype(np.complex64)
+
+
+# ----------------------------------------------------------------------------------------------
+# workload recipes
+
+TINY = dict(index=0, n_det=2, rate=2048, n=32768, n_templates=4, n_filters=64, d_max=2047,
+            nside=4, sigma=(1.0, 1.0))
+ONLINE = dict(index=1, n_det=3, rate=2048, chunk=2048, n_chunks=32, n_templates=1024,
+              f_range=(200, 900), d_max=4096, nside=16, sigma=(0.5, 2.0))
+
+
+def tiny_workload():
+    c = TINY
+    det = detectors(c["index"], c["n_det"])
+    strain = white_noise(c["index"], c["n_det"], c["n"])
+    bank = random_bank(rng(c["index"], "bank"), [c["n_filters"]] * c["n_templates"], c["d_max"])
+    sigma = noise_weights(c["index"], c["n_det"], *c["sigma"])
+    return dict(cfg=c, det=det, strain=strain, bank=bank, sigma=sigma)
+
+
+def online_bank(n_templates: int = ONLINE["n_templates"]) -> Bank:
+    c = ONLINE
+    g = rng(c["index"], "bank")
+    counts = g.integers(c["f_range"][0], c["f_range"][1] + 1, c["n_templates"])
+    full = random_bank(g, counts, c["d_max"])
+    if n_templates == c["n_templates"]:
+        return full
+    return full.subset(range(n_templates))
+
+
+def online_workload(n_templates: int = ONLINE["n_templates"]):
+    c = ONLINE
+    det = detectors(c["index"], c["n_det"])
+    sigma = noise_weights(c["index"], c["n_det"], *c["sigma"])
+    return dict(cfg=c, det=det, bank=online_bank(n_templates), sigma=sigma)
+
+
+def online_chunk(chunk_index: int) -> np.ndarray:
+    """1 s chunk number ``chunk_index`` of the online-sized strain, [3][2048] float32."""
+    c = ONLINE
+    return white_noise(c["index"], c["n_det"], c["chunk"], sub=1000 + chunk_index)
