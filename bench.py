@@ -1,0 +1,360 @@
+"""Benchmark of the SPIIR hot path on the online-sized workload.
+
+One step = one 1 s chunk (2048 samples) of 3-detector strain through the whole path:
+filter bank (1024 templates, 200..900 filters each, delays up to 2 s) -> SNR history ->
+coherent scan over 3072 HEALPix pixels (max statistic, argmax pixel, null stream).
+
+Prints one JSON line.  value = filter-sample updates per second of the whole step
+(all ranks); the coherent stage's sky-pixel-samples per second over the same steps is
+reported beside it.  Timing: W warm-up steps, then K steps each timed with CUDA events on
+the launching stream; the L2 cache is flushed (a 512 MiB write) before every timed step.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (bounded sample of
+the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "online-sized: 3 det, 1024 templates x U{200..900} filters, d<=4096, 2048 Hz 1 s chunks, nside 16"
+METRIC = "IIR filter·sample updates/s; coherent sky-pixel·samples/s; batched vs plain"
+UNIT = "filter·sample updates/s"
+K1_FLOPS_PER_UPDATE = 12          # Sec. II.B.2
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2032.0
+
+
+def k2_flops_per_pixel_sample(n_det):
+    # projection on two signal columns (2 complex outputs x n_det real-complex MACs) and
+    # the squared norm of the two outputs: (4 n_det + 4) multiply-adds, 2 flops each
+    return 2 * (4 * n_det + 4)
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash(*paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        p = line.split()
+        if len(p) >= 3 and not line.startswith("#") and p[0] == kernel and p[1] == src_hash:
+            return float(p[2])
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle arm
+
+
+def oracle_sample(n_templates, n_coh_templates, threads):
+    """Time the FP64 oracle on a bounded sample of the workload: the filter bank for
+    n_templates templates over one chunk (with history from a previous chunk) and the
+    coherent scan for n_coh_templates templates over one chunk."""
+    import oracle
+    oracle.set_threads(threads)
+    w = synth.online_workload(n_templates)
+    bank, det, sigma = w["bank"], w["det"], w["sigma"]
+    x0, x1 = synth.online_chunk(0), synth.online_chunk(1)
+    _, st, hist = oracle.filter_bank(x0, bank.offsets, bank.a1, bank.b0, bank.delay)
+    t0 = time.perf_counter()
+    z, _, _ = oracle.filter_bank(x1, bank.offsets, bank.a1, bank.b0, bank.delay, state=st, history=hist)
+    t_filter = time.perf_counter() - t0
+    _, G, d = oracle.sky_geometry(det, sigma, 16, 2048.0)
+    H = int(np.abs(d).max())
+    zc = np.concatenate([np.zeros((n_coh_templates, 3, 2 * H)), z[:n_coh_templates]], axis=2)
+    t0 = time.perf_counter()
+    oracle.coherent(zc, G, d, H, 2048)
+    t_coh = time.perf_counter() - t0
+    updates = int(bank.n_filters) * 3 * 2048
+    pix = n_coh_templates * 2048 * G.shape[0]
+    # whole-step rate: time per template of both stages, scaled to a step of all templates
+    t_step_per_template = t_filter / n_templates + t_coh / n_coh_templates
+    return dict(updates=updates, pixel_samples=pix, t_filter=t_filter, t_coh=t_coh,
+                updates_per_s=updates / t_filter, pixel_samples_per_s=pix / t_coh,
+                step_updates_per_s=(updates / n_templates) / t_step_per_template)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    T_f, T_c = 16, 2
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(T_f, T_c, threads)
+        if i >= args.warmup:
+            vals.append(r["step_updates_per_s"])
+            last = r
+    v = float(np.mean(vals))
+    sample = (f"per step: filter bank on {T_f} of 1024 templates and coherent scan on {T_c} templates, "
+              "one 2048-sample chunk; rate scaled per template")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * (last["t_filter"] * 1024 / T_f + last["t_coh"] * 1024 / T_c),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "parallelism": "host cores", "l2": "n/a"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "coherent_pixel_samples_per_s": last["pixel_samples_per_s"],
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+
+
+def run_gpu(args):
+    import torch
+    import paper_2011_06787_b300 as sp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+
+    # each rank filters its own 1024-template bank (weak scaling over template shards)
+    w = synth.online_workload()
+    bank, det, sigma = w["bank"], w["det"], w["sigma"]
+    n_det, T, n = 3, bank.n_templates, 2048
+    tabs = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 16, 2048.0)
+    sky = sp.Sky(*tabs)
+    b = sp.Bank(n_det, bank.offsets, bank.a1, bank.b0, bank.delay)
+    pipe = sp.Pipeline(b, sky, max_chunk=n)
+    P, H = sky.n_pix, sky.halo
+    updates_per_step = int(bank.n_filters) * n_det * n
+    pix_per_step = T * n * P
+
+    chunks = [torch.from_numpy(synth.online_chunk(i)).to(dev) for i in range(args.warmup + args.steps)]
+    ms = torch.empty((T, n), dtype=torch.float32, device=dev)
+    am = torch.empty((T, n), dtype=torch.int32, device=dev)
+    nl = torch.empty((T, n), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed_loop(fn, steps):
+        times = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(i)
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in times]
+
+    # warm-up (also JIT-free: the library is precompiled)
+    for i in range(args.warmup):
+        pipe.run(chunks[i], ms, am, nl)
+    barrier()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    step_ms = timed_loop(lambda i: pipe.run(chunks[args.warmup + i], ms, am, nl), args.steps)
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    sp.device_status()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * updates_per_step * args.steps / (total_ms * 1e-3)
+    pix_rate = world * pix_per_step * args.steps / (total_ms * 1e-3)
+
+    # per-kernel timing on the same stream: filter bank alone, coherent scan alone
+    zbuf = torch.zeros((T, n_det, n + 2 * H), dtype=torch.complex64, device=dev)
+    k1_ms = timed_loop(lambda i: b.filter_chunk(chunks[i % len(chunks)], zbuf[:, :, 2 * H:]), args.steps)
+    k2_ms = timed_loop(lambda i: sky.scan(zbuf, n, ms, am, nl), args.steps)
+    k1 = float(np.mean(k1_ms))
+    k2 = float(np.mean(k2_ms))
+    sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_max = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12          # TFLOP/s at max clock
+    peak_run = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    if k2 >= k1:
+        kern, src = "k_coherent", ["paper_2011_06787_b300/csrc/coherent.cu", "paper_2011_06787_b300/csrc/coherent.cuh"]
+        achieved = k2_flops_per_pixel_sample(n_det) * pix_per_step / (k2 * 1e-3) / 1e12
+    else:
+        kern, src = "k_filter_bank", ["paper_2011_06787_b300/csrc/bank.cu", "paper_2011_06787_b300/csrc/bank.cuh"]
+        achieved = K1_FLOPS_PER_UPDATE * updates_per_step / (k1 * 1e-3) / 1e12
+    traffic = recorded_traffic(kern, source_hash(*src))
+
+    # end to end through the host-buffer C entry point: pinned strain in, results out
+    hs = [torch.from_numpy(synth.online_chunk(i)).pin_memory() for i in range(args.warmup + args.steps)]
+    h_ms = torch.empty((T, n), dtype=torch.float32).pin_memory()
+    h_am = torch.empty((T, n), dtype=torch.int32).pin_memory()
+    h_nl = torch.empty((T, n), dtype=torch.float32).pin_memory()
+    pipe.reset()
+    for i in range(args.warmup):
+        pipe.run_host(hs[i].numpy(), h_ms.numpy(), h_am.numpy(), h_nl.numpy())
+    barrier()
+    e2e_s = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pipe.run_host(hs[args.warmup + i].numpy(), h_ms.numpy(), h_am.numpy(), h_nl.numpy())
+        e2e_s += time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * updates_per_step * args.steps / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r = oracle_sample(16, 2, threads)
+        cpu = {"value": r["step_updates_per_s"], "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "filter bank on 16 of 1024 templates and coherent scan on 2 templates over one 2048-sample "
+                         "chunk (FP64 C oracle, OpenMP over templates); whole-step rate scaled per template",
+               "filter_updates_per_s": r["updates_per_s"], "coherent_pixel_samples_per_s": r["pixel_samples_per_s"]}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "templates_per_gpu": T, "filters_per_gpu": int(bank.n_filters),
+                       "chunk_samples": n, "n_pix": P, "parallelism": f"template shards x{world}",
+                       "l2": "flushed before every timed step (512 MiB write)"},
+            "coherent_pixel_samples_per_s": pix_rate,
+            "kernel_ms": {"k_filter_bank": k1, "k_coherent": k2},
+            "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+                         "frac": achieved / peak_max, "frac_at_run_clock": achieved / peak_run,
+                         "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
+                         "traffic": traffic},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_det * n * 4,
+                    "d2h_bytes_per_step": T * n * 12},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

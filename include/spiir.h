@@ -1,0 +1,190 @@
+/*
+ * spiir.h -- C ABI of the B300 (sm_103a) SPIIR hot path.
+ *
+ * The library computes the data-parallel part of the SPIIR coherent search
+ * (arxiv 2011.06787): whitened multi-detector strain -> bank of complex first-order
+ * IIR filters -> complex SNR per template and detector -> coherent all-sky scan ->
+ * maximum network statistic, its sky pixel and the null stream.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: SPIIR_OK (0) or a negative SPIIR_E* code.  spiir_last_error()
+ *     returns a text description of the last failure on the calling thread.  No C++
+ *     exception crosses this interface and nothing aborts the process.
+ *   - Pointers named *_dev are CUDA device pointers on the current device; *_host are
+ *     host pointers.  The caller owns every buffer it passes; the library owns the
+ *     objects it creates (banks, sky tables, pipelines) and everything inside them.
+ *   - Complex values are interleaved (re, im) float pairs.  Sizes are in elements.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously on it unless the entry point says otherwise.
+ *   - Arguments are validated on the host before anything is launched; a rejected call
+ *     leaves every object unchanged.
+ *   - Kernels never trap.  A device-side wait that runs out of iterations sets a sticky
+ *     error word that spiir_device_status() reports (SPIIR_ETIMEOUT).
+ */
+#ifndef SPIIR_H
+#define SPIIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPIIR_OK 0
+#define SPIIR_EINVAL (-1)       /* invalid argument (shape, range, non-finite value, NULL) */
+#define SPIIR_ECUDA (-2)        /* a CUDA runtime call failed */
+#define SPIIR_ENOMEM (-3)       /* host or device allocation failed */
+#define SPIIR_EUNSUPPORTED (-4) /* valid input outside what this build supports */
+#define SPIIR_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
+
+typedef struct spiir_bank_s *spiir_bank_t;
+typedef struct spiir_sky_s *spiir_sky_t;
+typedef struct spiir_pipeline_s *spiir_pipeline_t;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int spiir_version(void);
+
+/* Copy the last error message of the calling thread into buf (NUL-terminated,
+ * truncated to len).  Returns the full message length. */
+int spiir_last_error(char *buf, size_t len);
+
+/* Test hook: make the next n allocations made by the library fail with SPIIR_ENOMEM
+ * (0 disables).  Used to exercise allocation-failure paths without a real shortage. */
+void spiir_debug_fail_allocs(int n);
+
+/* Sticky device-side status: SPIIR_OK, or SPIIR_ETIMEOUT after a bounded wait inside a
+ * kernel gave up.  Synchronises the device.  clear != 0 resets the word. */
+int spiir_device_status(int clear);
+
+/* ------------------------------------------------------------------------------------
+ * Filter bank -- Sec. II.B.1, Eq. (zk), read per filter (the commented closed form
+ * u(t) = sum_m b_m a_m^(t - t_m) beside it fixes that reading):
+ *     y_l[k] = a1_l * y_l[k-1] + b0_l * x_I[k - d_l]
+ *     z_{t,I}[k] = sum_{l in template t} y_l[k]
+ * for every detector I.  12 flops per filter per sample (Sec. II.B.2).
+ * ---------------------------------------------------------------------------------- */
+
+/* Create a bank of n_templates templates for a network of n_det detectors.
+ *   filter_offsets_host [n_templates + 1]  CSR offsets; template t owns filters
+ *                                          [off[t], off[t+1]); off[0] = 0.
+ *   a1_host [2 F]   feedback coefficients (re, im), |a1| < 1 required (stability; the
+ *                   paper does not state the bound).
+ *   b0_host [2 F]   feedforward coefficients (re, im), finite.
+ *   delay_host [F]  integer delays d_l in samples, 0 <= d_l <= 1<<20.
+ * The coefficients are copied; the bank owns its IIR states (all zero) and a strain
+ * history of max(d_l) samples per detector (zero).  Errors: SPIIR_EINVAL for bad
+ * shapes or values, SPIIR_EUNSUPPORTED when one template has more filters than one
+ * thread block can hold (4096 in this build), SPIIR_ENOMEM, SPIIR_ECUDA. */
+int spiir_bank_create(int n_det, int n_templates, const int64_t *filter_offsets_host,
+                      const float *a1_host, const float *b0_host, const int32_t *delay_host,
+                      spiir_bank_t *out);
+void spiir_bank_destroy(spiir_bank_t bank);
+
+/* Shape query.  Any output pointer may be NULL. */
+int spiir_bank_info(spiir_bank_t bank, int *n_det, int *n_templates, int64_t *n_filters,
+                    int32_t *max_delay);
+
+/* Zero the IIR states and the strain history (start of a new stream).  Enqueued on
+ * stream. */
+int spiir_bank_reset(spiir_bank_t bank, void *stream);
+
+/* Checkpoint / resume of the streaming state.  The state is the IIR state y_l of every
+ * filter and detector plus the last max(d_l) strain samples per detector, serialised
+ * in the caller's filter order.  spiir_bank_state_bytes gives the size.  get/set
+ * synchronise the device; set_state rejects a buffer of the wrong size or of another
+ * bank shape (SPIIR_EINVAL). */
+int spiir_bank_state_bytes(spiir_bank_t bank, size_t *bytes);
+int spiir_bank_get_state(spiir_bank_t bank, void *host, size_t bytes);
+int spiir_bank_set_state(spiir_bank_t bank, const void *host, size_t bytes);
+
+/* Filter one chunk of strain and advance the streaming state.
+ *   strain_dev [n_det][strain_pitch] float; samples 0..n-1 of each row are this chunk,
+ *              continuing the stream seen by previous calls.
+ *   snr_dev    [n_templates][n_det][snr_pitch] complex (2 floats); sample k of the
+ *              chunk is written at index k of each row; other entries are untouched.
+ * n >= 1, strain_pitch >= n, snr_pitch >= n.  Enqueued on stream.  Calls on the same
+ * bank must be ordered (one stream, or explicit synchronisation). */
+int spiir_filter_chunk(spiir_bank_t bank, const float *strain_dev, int64_t strain_pitch,
+                       int64_t n, float *snr_dev, int64_t snr_pitch, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Sky tables -- Sec. II.C.1 (HEALPix tiling, U and time-offset look-up tables) and
+ * App. A Eqs. (strain_sngl), (svd).
+ * ---------------------------------------------------------------------------------- */
+
+/* Host-side FP64 construction of the per-pixel tables for one epoch (no Earth
+ * rotation) from detector geometry, stored as int32 / FP32.
+ *   det_pos_m [n_det][3]  Earth-fixed detector positions (m)
+ *   arm_x, arm_y [n_det][3] unit arm directions
+ *   sigma [n_det]          noise weights sigma_I (App. A Eq. (h_prop))
+ *   nside                  HEALPix resolution; n_pix = 12 nside^2, RING order
+ *   rate_hz                sample rate of the SNR series
+ * Outputs (caller-allocated host arrays):
+ *   delays [n_pix][n_det]   Delta_I(p) = round(-rate * nhat_p . r_I / c), half away from
+ *                           zero: detector I's SNR for geocentric sample k is read at
+ *                           k + Delta_I(p).
+ *   u_sig  [n_pix][n_det][2]          first two columns of U in G_sigma = U Lambda V^T
+ *   u_null [n_pix][n_det][n_det - 2] remaining columns (may be NULL when n_det = 2)
+ * 2 <= n_det <= 4, 1 <= nside <= 64.  A pixel whose G_sigma has sigma_2 / sigma_1 <
+ * 1e-6 gets a zero second signal column (projection onto the numerical rank). */
+int spiir_sky_tables(int n_det, const double *det_pos_m, const double *arm_x,
+                     const double *arm_y, const double *sigma, int nside, double rate_hz,
+                     int32_t *delays, float *u_sig, float *u_null);
+
+/* Upload per-pixel tables (layouts as produced by spiir_sky_tables) to the device.
+ * The halo H = max |delays| sets the SNR padding that spiir_coherent_scan needs.
+ * |delays| <= 1024.  Errors: SPIIR_EINVAL, SPIIR_ENOMEM, SPIIR_ECUDA. */
+int spiir_sky_create(int n_det, int n_pix, const int32_t *delays_host, const float *u_sig_host,
+                     const float *u_null_host, spiir_sky_t *out);
+void spiir_sky_destroy(spiir_sky_t sky);
+int spiir_sky_info(spiir_sky_t sky, int *n_det, int *n_pix, int *halo);
+
+/* Coherent all-sky scan -- Sec. II.C.1 Eq. (llr_form) and Eq. (null_def), App. A:
+ *     w_I(p, k)   = z_I[k + Delta_I(p)]
+ *     rho_C^2(p,k) = sum_{j=1,2} | sum_I U_s[p][I][j] w_I |^2
+ *     max_stat[k] = max_p rho_C^2(p, k), argmax[k] = lowest p attaining it
+ *     null_stat[k] = sum_{j>2} | sum_I U_null[p][I][j] w_I |^2 at p = argmax[k]
+ *                    (0 when n_det = 2)
+ *   snr_dev [n_templates][n_det][snr_pitch] complex; entry H + j of a row holds the
+ *           SNR of output sample j (H = halo), so rows need snr_pitch >= n + 2 H.
+ *   max_stat_dev, null_stat_dev [n_templates][n] float; argmax_dev [n_templates][n] int32.
+ *   skymap_dev  NULL, or [n_templates][n_pix][n] float receiving rho_C^2 of every pixel
+ *               (pixel-major so that consecutive samples are contiguous).
+ * Enqueued on stream. */
+int spiir_coherent_scan(spiir_sky_t sky, const float *snr_dev, int64_t snr_pitch,
+                        int n_templates, int64_t n, float *max_stat_dev, int32_t *argmax_dev,
+                        float *null_stat_dev, float *skymap_dev, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Streaming pipeline: one call per strain chunk runs the whole hot path (filter bank,
+ * SNR history of 2 H samples, coherent scan).  Output sample j of a call is geocentric
+ * sample (stream position of the chunk start) + j - H: the coherent stage lags the
+ * strain by H samples so that every detector's delayed SNR is available.
+ * ---------------------------------------------------------------------------------- */
+
+/* bank and sky must have the same n_det and must outlive the pipeline.  max_chunk
+ * bounds n in later calls. */
+int spiir_pipeline_create(spiir_bank_t bank, spiir_sky_t sky, int64_t max_chunk,
+                          spiir_pipeline_t *out);
+void spiir_pipeline_destroy(spiir_pipeline_t pipe);
+/* Zero all streaming state (bank states, strain and SNR history). */
+int spiir_pipeline_reset(spiir_pipeline_t pipe, void *stream);
+
+/* Device buffers: strain_dev [n_det][strain_pitch]; outputs [n_templates][n] as in
+ * spiir_coherent_scan; skymap_dev NULL or [n_templates][n_pix][n].  Enqueued on stream. */
+int spiir_pipeline_run(spiir_pipeline_t pipe, const float *strain_dev, int64_t strain_pitch,
+                       int64_t n, float *max_stat_dev, int32_t *argmax_dev,
+                       float *null_stat_dev, float *skymap_dev, void *stream);
+
+/* Same with host buffers: copies the strain [n_det][n] to the device, runs, copies
+ * max_stat, argmax and null_stat [n_templates][n] back and synchronises stream.  Host
+ * buffers should be page-locked for full copy bandwidth. */
+int spiir_pipeline_run_host(spiir_pipeline_t pipe, const float *strain_host, int64_t n,
+                            float *max_stat_host, int32_t *argmax_host,
+                            float *null_stat_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPIIR_H */

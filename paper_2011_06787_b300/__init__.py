@@ -1,0 +1,234 @@
+"""B300 (sm_103a) SPIIR hot path: filter bank and coherent sky scan behind a C ABI.
+
+The classes here marshal arguments into the C entry points of libspiir.so
+(include/spiir.h); every step of the computation runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native
+from .native import SpiirError, check
+
+__all__ = ["Bank", "Sky", "Pipeline", "sky_tables", "SpiirError", "device_status", "version"]
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+
+
+def version() -> int:
+    return native.lib().spiir_version()
+
+
+def device_status(clear: bool = True) -> None:
+    """Raise SpiirError(ETIMEOUT) if a bounded device-side wait gave up since the last check."""
+    check(native.lib().spiir_device_status(1 if clear else 0))
+
+
+class Bank:
+    """SPIIR filter bank (Sec. II.B.1, Eq. (zk)); see spiir_bank_create in include/spiir.h.
+
+    offsets [T+1] int64, a1 / b0 [F] complex, delay [F] int32 (host arrays).
+    """
+
+    def __init__(self, n_det: int, offsets, a1, b0, delay):
+        L = native.lib()
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        a = np.ascontiguousarray(np.asarray(a1, dtype=np.complex64)).view(np.float32)
+        b = np.ascontiguousarray(np.asarray(b0, dtype=np.complex64)).view(np.float32)
+        d = np.ascontiguousarray(delay, dtype=np.int32)
+        h = ctypes.c_void_p()
+        check(L.spiir_bank_create(int(n_det), int(off.size - 1), _host_ptr(off), _host_ptr(a), _host_ptr(b),
+                                  _host_ptr(d), ctypes.byref(h)))
+        self._h = h
+        self.n_det = int(n_det)
+        self.n_templates = int(off.size - 1)
+        self.n_filters = int(off[-1])
+        self.max_delay = int(d.max()) if d.size else 0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            native.lib().spiir_bank_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        check(native.lib().spiir_bank_reset(self._h, _stream_ptr(stream)))
+
+    def filter_chunk(self, strain, out, stream=None):
+        """strain: float32 CUDA tensor [n_det][n] (row stride = pitch); out: complex64 CUDA tensor
+        [T][n_det][>= n] whose first n samples of each row are written."""
+        import torch
+        _require_cuda(strain, torch.float32, "strain")
+        _require_cuda(out, torch.complex64, "out")
+        if strain.dim() != 2 or strain.shape[0] != self.n_det or strain.stride(1) != 1:
+            raise ValueError("strain must be [n_det][n] with unit stride along time")
+        n = strain.shape[1]
+        if out.dim() != 3 or out.shape[0] != self.n_templates or out.shape[1] != self.n_det or out.stride(2) != 1 \
+                or out.stride(1) != out.stride(0) // self.n_det or out.shape[2] < n:
+            raise ValueError("out must be a [T][n_det][pitch] complex64 tensor with contiguous rows")
+        check(native.lib().spiir_filter_chunk(self._h, _dev_ptr(strain), strain.stride(0), n, _dev_ptr(out),
+                                              out.stride(1), _stream_ptr(stream)))
+        return out
+
+    def state_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        check(native.lib().spiir_bank_state_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_state(self) -> bytes:
+        buf = ctypes.create_string_buffer(self.state_bytes())
+        check(native.lib().spiir_bank_get_state(self._h, buf, len(buf)))
+        return buf.raw
+
+    def set_state(self, state: bytes) -> None:
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        check(native.lib().spiir_bank_set_state(self._h, buf, len(state)))
+
+
+def sky_tables(det_pos_m, arm_x, arm_y, sigma, nside: int, rate_hz: float):
+    """Host FP64 per-pixel tables (delays [P][n_det] int32, u_sig [P][n_det][2], u_null [P][n_det][n_det-2])."""
+    pos = np.ascontiguousarray(det_pos_m, dtype=np.float64)
+    ax = np.ascontiguousarray(arm_x, dtype=np.float64)
+    ay = np.ascontiguousarray(arm_y, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    nd = pos.shape[0]
+    P = 12 * nside * nside
+    delays = np.zeros((P, nd), dtype=np.int32)
+    u_sig = np.zeros((P, nd, 2), dtype=np.float32)
+    u_null = np.zeros((P, nd, max(nd - 2, 1)), dtype=np.float32)
+    check(native.lib().spiir_sky_tables(nd, _host_ptr(pos), _host_ptr(ax), _host_ptr(ay), _host_ptr(sg), int(nside),
+                                        float(rate_hz), _host_ptr(delays), _host_ptr(u_sig), _host_ptr(u_null)))
+    return delays, u_sig, u_null[:, :, : max(nd - 2, 0)].copy()
+
+
+class Sky:
+    """Per-pixel coherent-scan tables on the device (spiir_sky_create)."""
+
+    def __init__(self, delays, u_sig, u_null):
+        L = native.lib()
+        d = np.ascontiguousarray(delays, dtype=np.int32)
+        us = np.ascontiguousarray(u_sig, dtype=np.float32)
+        P, nd = d.shape
+        un = np.ascontiguousarray(u_null, dtype=np.float32) if nd > 2 else np.zeros(1, dtype=np.float32)
+        h = ctypes.c_void_p()
+        check(L.spiir_sky_create(nd, P, _host_ptr(d), _host_ptr(us), _host_ptr(un), ctypes.byref(h)))
+        self._h = h
+        self.n_det = nd
+        self.n_pix = P
+        H = ctypes.c_int()
+        check(L.spiir_sky_info(h, None, None, ctypes.byref(H)))
+        self.halo = H.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            native.lib().spiir_sky_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def scan(self, snr, n: int, max_stat, argmax, null_stat, skymap=None, stream=None):
+        """snr: complex64 CUDA tensor [T][n_det][pitch], entry H + k = output sample k.
+        Outputs: float32 [T][n], int32 [T][n], float32 [T][n], optional float32 [T][P][n]."""
+        import torch
+        _require_cuda(snr, torch.complex64, "snr")
+        T = snr.shape[0]
+        for t, dt, nm in ((max_stat, torch.float32, "max_stat"), (argmax, torch.int32, "argmax"),
+                          (null_stat, torch.float32, "null_stat")):
+            _require_cuda(t, dt, nm)
+            if not t.is_contiguous() or t.numel() < T * n:
+                raise ValueError(f"{nm} must be contiguous with T*n elements")
+        if skymap is not None:
+            _require_cuda(skymap, torch.float32, "skymap")
+            if not skymap.is_contiguous() or skymap.numel() < T * self.n_pix * n:
+                raise ValueError("skymap must be contiguous [T][n_pix][n]")
+        if snr.stride(2) != 1 or snr.stride(1) != snr.stride(0) // self.n_det:
+            raise ValueError("snr rows must be contiguous [T][n_det][pitch]")
+        check(native.lib().spiir_coherent_scan(self._h, _dev_ptr(snr), snr.stride(1), T, int(n), _dev_ptr(max_stat),
+                                               _dev_ptr(argmax), _dev_ptr(null_stat),
+                                               _dev_ptr(skymap) if skymap is not None else None,
+                                               _stream_ptr(stream)))
+
+
+class Pipeline:
+    """Filter bank + SNR history + coherent scan per strain chunk (spiir_pipeline_*)."""
+
+    def __init__(self, bank: Bank, sky: Sky, max_chunk: int):
+        h = ctypes.c_void_p()
+        check(native.lib().spiir_pipeline_create(bank.handle, sky.handle, int(max_chunk), ctypes.byref(h)))
+        self._h = h
+        self.bank = bank
+        self.sky = sky
+        self.max_chunk = int(max_chunk)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            native.lib().spiir_pipeline_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        check(native.lib().spiir_pipeline_reset(self._h, _stream_ptr(stream)))
+
+    def run(self, strain, max_stat, argmax, null_stat, skymap=None, stream=None):
+        import torch
+        _require_cuda(strain, torch.float32, "strain")
+        n = strain.shape[1]
+        check(native.lib().spiir_pipeline_run(self._h, _dev_ptr(strain), strain.stride(0), n, _dev_ptr(max_stat),
+                                              _dev_ptr(argmax), _dev_ptr(null_stat),
+                                              _dev_ptr(skymap) if skymap is not None else None,
+                                              _stream_ptr(stream)))
+
+    def run_host(self, strain: np.ndarray, max_stat: np.ndarray, argmax: np.ndarray, null_stat: np.ndarray,
+                 stream=None):
+        """Host buffers (ideally page-locked): strain [n_det][n] float32 C-contiguous; outputs [T][n]."""
+        for a, dt in ((strain, np.float32), (max_stat, np.float32), (argmax, np.int32), (null_stat, np.float32)):
+            if a.dtype != dt or not a.flags.c_contiguous:
+                raise ValueError("host buffers must be C-contiguous with the documented dtypes")
+        n = strain.shape[1]
+        check(native.lib().spiir_pipeline_run_host(self._h, _host_ptr(strain), n, _host_ptr(max_stat),
+                                                   _host_ptr(argmax), _host_ptr(null_stat), _stream_ptr(stream)))

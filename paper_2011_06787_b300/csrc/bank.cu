@@ -1,0 +1,553 @@
+// SPIIR filter bank (Sec. II.B.1, Eq. (zk), per-filter reading):
+//     y_l[k] = a1_l y_l[k-1] + b0_l x_I[k - d_l],     z_{t,I}[k] = sum_{l in t} y_l[k].
+//
+// Device mapping (K1):
+//   * A thread ("lane") owns S filters of one template and keeps their coefficients and
+//     complex states in registers as packed FP32 pairs (two filters per f32x2 register),
+//     so one packed update costs 8 FP32-pipe operations for two filter-samples.
+//   * Templates occupy contiguous lane ranges; whole templates are packed into thread
+//     blocks of NL lanes (best-fit decreasing), so no template straddles two blocks.
+//   * blockIdx.y selects the detector.  The strain window of a time tile plus the maximum
+//     delay is copied into shared memory by one bulk asynchronous copy completed on an
+//     mbarrier.
+//   * Every lane writes its per-step partial sum (over its S filters) to a shared buffer
+//     of R steps.  After R steps each warp sums its 32 rows column by column, split at
+//     template boundaries (warp-uniform), and one more pass adds the pieces of templates
+//     that span several warps and writes z with coalesced stores.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <vector>
+
+#include "bank.cuh"
+
+namespace spiir {
+
+// ---------------------------------------------------------------------------------------
+// Kernel
+
+template <int S>
+__global__ void __launch_bounds__(kBankLanes, 1) k_filter_bank(const __grid_constant__ BankArgs a) {
+    constexpr int NP = S / 2;
+    constexpr int NL = kBankLanes;
+    constexpr int R = kBankSteps;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *xw = reinterpret_cast<float *>(smem);
+    float2 *red = reinterpret_cast<float2 *>(smem + a.red_offset);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_offset);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int cta = blockIdx.x, det = blockIdx.y;
+    const int active = a.cta_active[cta];
+    const bool busy = (warp * 32) < active;
+
+    // coefficients and states -> registers
+    u64 are[NP], aim[NP], naim[NP], bre[NP], bim[NP], yre[NP], yim[NP];
+    int dof[S];
+    const int64_t pbase = (int64_t)cta * NP * NL + tid;
+    float4 *st = a.state + (int64_t)det * a.state_det_stride + pbase;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float2 v;
+        v = a.are[pbase + (int64_t)p * NL];
+        are[p] = pack2(v.x, v.y);
+        v = a.aim[pbase + (int64_t)p * NL];
+        aim[p] = pack2(v.x, v.y);
+        naim[p] = neg2(aim[p]);
+        v = a.bre[pbase + (int64_t)p * NL];
+        bre[p] = pack2(v.x, v.y);
+        v = a.bim[pbase + (int64_t)p * NL];
+        bim[p] = pack2(v.x, v.y);
+        float4 y = st[(int64_t)p * NL];
+        yre[p] = pack2(y.x, y.y);
+        yim[p] = pack2(y.z, y.w);
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) dof[s] = a.D_pad - a.delay[((int64_t)cta * S + s) * NL + tid];
+
+    // segment tables of this block
+    const int seg0 = a.seg_off[cta];
+    const int nseg = a.seg_off[cta + 1] - seg0;
+    const int wfirst = a.wfirst[cta * kBankWarps + warp];
+
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const float *xsrc = a.xbuf + (int64_t)det * a.xpitch;
+
+    for (int64_t k0 = 0; k0 < a.n; k0 += a.c_tile) {
+        const int nt = (int)min((int64_t)a.c_tile, a.n - k0);
+        const uint32_t bytes = (uint32_t)(a.D_pad + ((nt + 3) & ~3)) * 4u;
+        __syncthreads();  // all reads of the previous window are done
+        if (tid == 0) bulk_load(xw, xsrc + k0, bytes, bar);
+        const bool ok = mbar_wait(bar, phase);
+        if (__syncthreads_or(!ok)) {
+            // bounded wait ran out: record it, give the copy one more bounded wait, leave
+            if (tid == 0) {
+                report_timeout(a.status);
+                mbar_wait(bar, phase);
+            }
+            return;
+        }
+        phase ^= 1u;
+
+        for (int kb = 0; kb < nt; kb += R) {
+            const int nr = min(R, nt - kb);
+            if (busy) {
+                const float *xp[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) xp[s] = xw + dof[s] + kb;
+                float2 *rrow = red + tid * (R + 1);
+                auto step = [&](int r) {
+                    u64 accr = 0, acci = 0;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const u64 X = pack2(xp[2 * p][r], xp[2 * p + 1][r]);
+                        u64 t = fma2(are[p], yre[p], mul2(bre[p], X));  // a.re y.re + b.re x
+                        u64 u = fma2(are[p], yim[p], mul2(bim[p], X));  // a.re y.im + b.im x
+                        const u64 nr_ = fma2(naim[p], yim[p], t);       // - a.im y.im
+                        const u64 ni_ = fma2(aim[p], yre[p], u);        // + a.im y.re
+                        yre[p] = nr_;
+                        yim[p] = ni_;
+                        if (p == 0) {
+                            accr = nr_;
+                            acci = ni_;
+                        } else {
+                            accr = add2(accr, nr_);
+                            acci = add2(acci, ni_);
+                        }
+                    }
+                    const float2 ar = unpack2(accr), ai = unpack2(acci);
+                    rrow[r] = make_float2(ar.x + ar.y, ai.x + ai.y);
+                };
+                if (nr == R) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) step(r);
+                } else {
+#pragma unroll 1
+                    for (int r = 0; r < nr; ++r) step(r);
+                }
+            }
+            __syncthreads();
+            // pass 1: each warp sums its own rows per column, split at template boundaries;
+            // piece j of the warp overwrites row 32*warp + j (a row it has already read)
+            if (busy && wfirst >= 0) {
+                int j = 0;
+                for (int sg = wfirst; sg < nseg; ++sg) {
+                    const int4 g = a.segs[seg0 + sg];
+                    const int lo = max(g.y, warp * 32) - warp * 32;
+                    const int hi = min(g.z, warp * 32 + 32) - warp * 32;
+                    if (hi <= lo) break;
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int i = lo; i < hi; ++i) {
+                        const float2 v = red[(warp * 32 + i) * (R + 1) + lane];
+                        acc.x += v.x;
+                        acc.y += v.y;
+                    }
+                    red[(warp * 32 + j) * (R + 1) + lane] = acc;
+                    ++j;
+                }
+            }
+            __syncthreads();
+            // pass 2: add the pieces of each template over the warps it spans, write z
+            for (int o = tid; o < nseg * R; o += NL) {
+                const int sg = o / R, r = o % R;
+                if (r >= nr) continue;
+                const int4 g = a.segs[seg0 + sg];
+                float2 acc = make_float2(0.f, 0.f);
+                for (int w = g.y >> 5; w <= (g.z - 1) >> 5; ++w) {
+                    const float2 v = red[(w * 32 + (sg - a.wfirst[cta * kBankWarps + w])) * (R + 1) + r];
+                    acc.x += v.x;
+                    acc.y += v.y;
+                }
+                float2 *zrow = a.z + ((int64_t)g.x * a.n_det + det) * a.zpitch;
+                zrow[k0 + kb + r] = acc;
+            }
+            __syncthreads();
+        }
+    }
+    // states back to global memory
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float2 r = unpack2(yre[p]), i = unpack2(yim[p]);
+        st[(int64_t)p * NL] = make_float4(r.x, r.y, i.x, i.y);
+    }
+}
+
+template <int S>
+static int launch_bank(const BankArgs &a, int n_cta, int n_det, size_t smem, cudaStream_t stream) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_filter_bank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kBankMaxSmem));
+        attr_set = true;
+    }
+    k_filter_bank<S><<<dim3(n_cta, n_det), kBankLanes, smem, stream>>>(a);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Host: packing
+
+int bank_pack(spiir_bank_s *b) {
+    const int T = b->T;
+    const int S = b->S;
+    const int NL = kBankLanes;
+    std::vector<int> lanes(T);
+    for (int t = 0; t < T; ++t) {
+        const int64_t f = b->offsets[t + 1] - b->offsets[t];
+        lanes[t] = (int)std::max<int64_t>(1, (f + S - 1) / S);
+        if (lanes[t] > NL)
+            return fail(SPIIR_EUNSUPPORTED, "template %d has %lld filters; at most %d per template", t,
+                        (long long)f, NL * S);
+    }
+    // best-fit decreasing: place the largest templates first into the fullest block that
+    // still has room
+    std::vector<int> order(T);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lanes[x] > lanes[y]; });
+    std::multimap<int, int> by_free;  // free lanes -> block
+    std::vector<std::vector<int>> members;
+    std::vector<int> used;
+    for (int t : order) {
+        auto it = by_free.lower_bound(lanes[t]);
+        int c;
+        if (it == by_free.end()) {
+            c = (int)members.size();
+            members.emplace_back();
+            used.push_back(0);
+        } else {
+            c = it->second;
+            by_free.erase(it);
+        }
+        members[c].push_back(t);
+        used[c] += lanes[t];
+        by_free.emplace(NL - used[c], c);
+    }
+    const int n_cta = (int)members.size();
+    b->n_cta = n_cta;
+    const int NP = S / 2;
+    const int64_t n_slots = (int64_t)n_cta * S * NL;
+    b->h_are.assign((size_t)n_cta * NP * NL, make_float2(0, 0));
+    b->h_aim = b->h_are;
+    b->h_bre = b->h_are;
+    b->h_bim = b->h_are;
+    b->h_delay.assign((size_t)n_slots, 0);
+    b->slot_of_filter.assign((size_t)b->F, -1);
+    b->h_segs.clear();
+    b->h_seg_off.assign(n_cta + 1, 0);
+    b->h_wfirst.assign((size_t)n_cta * kBankWarps, -1);
+    b->h_active.assign(n_cta, 0);
+    for (int c = 0; c < n_cta; ++c) {
+        // within a block, templates in ascending index order
+        std::sort(members[c].begin(), members[c].end());
+        int lane0 = 0;
+        b->h_seg_off[c] = (int)b->h_segs.size();
+        for (int t : members[c]) {
+            const int64_t lo = b->offsets[t], hi = b->offsets[t + 1];
+            std::vector<int64_t> fl(hi - lo);
+            std::iota(fl.begin(), fl.end(), lo);
+            // longest delays first: a lane's filters then read neighbouring window entries
+            std::stable_sort(fl.begin(), fl.end(),
+                             [&](int64_t x, int64_t y) { return b->delay[x] > b->delay[y]; });
+            for (size_t q = 0; q < fl.size(); ++q) {
+                const int ln = lane0 + (int)(q / S), s = (int)(q % S);
+                const int64_t l = fl[q];
+                const int64_t slot = ((int64_t)c * S + s) * NL + ln;
+                b->slot_of_filter[l] = slot;
+                b->h_delay[slot] = b->delay[l];
+                const size_t pi = ((size_t)c * NP + s / 2) * NL + ln;
+                float2 *ar = &b->h_are[pi], *ai = &b->h_aim[pi], *br = &b->h_bre[pi], *bi = &b->h_bim[pi];
+                if (s % 2 == 0) {
+                    ar->x = b->a1[2 * l]; ai->x = b->a1[2 * l + 1];
+                    br->x = b->b0[2 * l]; bi->x = b->b0[2 * l + 1];
+                } else {
+                    ar->y = b->a1[2 * l]; ai->y = b->a1[2 * l + 1];
+                    br->y = b->b0[2 * l]; bi->y = b->b0[2 * l + 1];
+                }
+            }
+            b->h_segs.push_back(make_int4(t, lane0, lane0 + lanes[t], 0));
+            lane0 += lanes[t];
+        }
+        b->h_active[c] = lane0;
+        const int s0 = b->h_seg_off[c];
+        const int ns = (int)b->h_segs.size() - s0;
+        for (int w = 0; w < kBankWarps; ++w) {
+            for (int sg = 0; sg < ns; ++sg) {
+                const int4 g = b->h_segs[s0 + sg];
+                if (g.z > w * 32 && g.y < w * 32 + 32) {
+                    b->h_wfirst[c * kBankWarps + w] = sg;
+                    break;
+                }
+            }
+        }
+    }
+    b->h_seg_off[n_cta] = (int)b->h_segs.size();
+    return SPIIR_OK;
+}
+
+static int upload(void **dst, const void *src, size_t bytes, const char *what) {
+    SPIIR_TRY(dev_alloc(dst, bytes, what));
+    if (bytes) SPIIR_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return SPIIR_OK;
+}
+
+static void bank_free(spiir_bank_s *b) {
+    if (!b) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (b->device >= 0) cudaSetDevice(b->device);
+    dev_free(b->are); dev_free(b->aim); dev_free(b->bre); dev_free(b->bim);
+    dev_free(b->dly); dev_free(b->state); dev_free(b->segs); dev_free(b->seg_off);
+    dev_free(b->wfirst); dev_free(b->active);
+    dev_free(b->xbuf[0]); dev_free(b->xbuf[1]);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete b;
+}
+
+static int bank_alloc_device(spiir_bank_s *b) {
+    SPIIR_TRY(upload((void **)&b->are, b->h_are.data(), b->h_are.size() * sizeof(float2), "a1.re"));
+    SPIIR_TRY(upload((void **)&b->aim, b->h_aim.data(), b->h_aim.size() * sizeof(float2), "a1.im"));
+    SPIIR_TRY(upload((void **)&b->bre, b->h_bre.data(), b->h_bre.size() * sizeof(float2), "b0.re"));
+    SPIIR_TRY(upload((void **)&b->bim, b->h_bim.data(), b->h_bim.size() * sizeof(float2), "b0.im"));
+    SPIIR_TRY(upload((void **)&b->dly, b->h_delay.data(), b->h_delay.size() * sizeof(int), "delays"));
+    SPIIR_TRY(upload((void **)&b->segs, b->h_segs.data(), b->h_segs.size() * sizeof(int4), "segments"));
+    SPIIR_TRY(upload((void **)&b->seg_off, b->h_seg_off.data(), b->h_seg_off.size() * sizeof(int), "segment offsets"));
+    SPIIR_TRY(upload((void **)&b->wfirst, b->h_wfirst.data(), b->h_wfirst.size() * sizeof(int), "warp segments"));
+    SPIIR_TRY(upload((void **)&b->active, b->h_active.data(), b->h_active.size() * sizeof(int), "active lanes"));
+    b->state_det_stride = (int64_t)b->n_cta * (b->S / 2) * kBankLanes;
+    SPIIR_TRY(dev_alloc((void **)&b->state, sizeof(float4) * b->state_det_stride * b->n_det, "IIR states"));
+    SPIIR_CUDA_TRY(cudaMemset(b->state, 0, sizeof(float4) * b->state_det_stride * b->n_det));
+    return SPIIR_OK;
+}
+
+// (Re)allocate the two strain windows for chunks of up to ncap samples, keeping history.
+static int bank_reserve(spiir_bank_s *b, int64_t ncap, cudaStream_t stream) {
+    if (ncap <= b->ncap && b->xbuf[0]) return SPIIR_OK;
+    const int64_t pitch = ((b->D_pad + ncap + 3) / 4) * 4 + 4;
+    float *nb[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2; ++i) {
+        int rc = dev_alloc((void **)&nb[i], sizeof(float) * pitch * b->n_det, "strain window");
+        if (rc != SPIIR_OK) {
+            dev_free(nb[0]);
+            return rc;
+        }
+        SPIIR_CUDA_TRY(cudaMemsetAsync(nb[i], 0, sizeof(float) * pitch * b->n_det, stream));
+    }
+    if (b->xbuf[0] && b->D_pad > 0)
+        SPIIR_CUDA_TRY(cudaMemcpy2DAsync(nb[0], pitch * 4, b->xbuf[b->cur], b->xpitch * 4, b->D_pad * 4,
+                                         b->n_det, cudaMemcpyDeviceToDevice, stream));
+    SPIIR_CUDA_TRY(cudaStreamSynchronize(stream));
+    dev_free(b->xbuf[0]);
+    dev_free(b->xbuf[1]);
+    b->xbuf[0] = nb[0];
+    b->xbuf[1] = nb[1];
+    b->cur = 0;
+    b->xpitch = pitch;
+    b->ncap = ncap;
+    return SPIIR_OK;
+}
+
+int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int64_t n, float2 *z,
+                int64_t zpitch, cudaStream_t stream) {
+    SPIIR_TRY(bank_reserve(b, std::max<int64_t>(n, 2048), stream));
+    float *x = b->xbuf[b->cur];
+    SPIIR_CUDA_TRY(cudaMemcpy2DAsync(x + b->D_pad, b->xpitch * 4, strain, strain_pitch * 4, n * 4, b->n_det,
+                                     cudaMemcpyDeviceToDevice, stream));
+    BankArgs a{};
+    a.xbuf = x;
+    a.xpitch = b->xpitch;
+    a.D_pad = b->D_pad;
+    a.n = n;
+    a.c_tile = b->c_tile;
+    a.are = b->are; a.aim = b->aim; a.bre = b->bre; a.bim = b->bim;
+    a.delay = b->dly;
+    a.state = b->state;
+    a.state_det_stride = b->state_det_stride;
+    a.segs = b->segs; a.seg_off = b->seg_off; a.wfirst = b->wfirst; a.cta_active = b->active;
+    a.z = z;
+    a.zpitch = zpitch;
+    a.n_det = b->n_det;
+    a.status = device_status_word();
+    a.red_offset = (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
+    a.bar_offset = a.red_offset + (size_t)kBankLanes * (kBankSteps + 1) * sizeof(float2);
+    const size_t smem = a.bar_offset + 16;
+    if (smem > (size_t)kBankMaxSmem)
+        return fail(SPIIR_EUNSUPPORTED, "strain window of %d + %d samples does not fit in shared memory",
+                    b->D_pad, b->c_tile);
+    if (b->S == 8) {
+        SPIIR_TRY(launch_bank<8>(a, b->n_cta, b->n_det, smem, stream));
+    } else {
+        SPIIR_TRY(launch_bank<16>(a, b->n_cta, b->n_det, smem, stream));
+    }
+    // the last D_pad samples become the history of the next call
+    const int nxt = 1 - b->cur;
+    if (b->D_pad > 0)
+        SPIIR_CUDA_TRY(cudaMemcpy2DAsync(b->xbuf[nxt], b->xpitch * 4, x + n, b->xpitch * 4, b->D_pad * 4,
+                                         b->n_det, cudaMemcpyDeviceToDevice, stream));
+    b->cur = nxt;
+    return SPIIR_OK;
+}
+
+}  // namespace spiir
+
+using namespace spiir;
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+
+extern "C" int spiir_bank_create(int n_det, int n_templates, const int64_t *off, const float *a1,
+                                 const float *b0, const int32_t *delay, spiir_bank_t *out) {
+    clear_error();
+    if (!out) return fail(SPIIR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_det < 1 || n_det > 8) return fail(SPIIR_EINVAL, "n_det = %d outside [1, 8]", n_det);
+    if (n_templates < 1) return fail(SPIIR_EINVAL, "n_templates = %d < 1", n_templates);
+    if (!off) return fail(SPIIR_EINVAL, "filter_offsets is NULL");
+    if (off[0] != 0) return fail(SPIIR_EINVAL, "filter_offsets[0] = %lld, expected 0", (long long)off[0]);
+    for (int t = 0; t < n_templates; ++t)
+        if (off[t + 1] < off[t]) return fail(SPIIR_EINVAL, "filter_offsets decrease at template %d", t);
+    const int64_t F = off[n_templates];
+    if (F > 0 && (!a1 || !b0 || !delay)) return fail(SPIIR_EINVAL, "coefficient pointer is NULL");
+    int32_t dmax = 0;
+    for (int64_t l = 0; l < F; ++l) {
+        const double ar = a1[2 * l], ai = a1[2 * l + 1], br = b0[2 * l], bi = b0[2 * l + 1];
+        if (!std::isfinite(ar) || !std::isfinite(ai) || !std::isfinite(br) || !std::isfinite(bi))
+            return fail(SPIIR_EINVAL, "filter %lld has a non-finite coefficient", (long long)l);
+        if (ar * ar + ai * ai >= 1.0)
+            return fail(SPIIR_EINVAL, "filter %lld has |a1| >= 1 (unstable)", (long long)l);
+        if (delay[l] < 0 || delay[l] > kBankMaxDelay)
+            return fail(SPIIR_EINVAL, "filter %lld has delay %d outside [0, %d]", (long long)l, delay[l],
+                        kBankMaxDelay);
+        dmax = std::max(dmax, delay[l]);
+    }
+    spiir_bank_s *b = new (std::nothrow) spiir_bank_s();
+    if (!b) return fail(SPIIR_ENOMEM, "host allocation of the bank failed");
+    cudaGetDevice(&b->device);
+    b->n_det = n_det;
+    b->T = n_templates;
+    b->F = F;
+    b->dmax = dmax;
+    b->D_pad = ((dmax + 3) / 4) * 4;
+    b->offsets.assign(off, off + n_templates + 1);
+    b->a1.assign(a1, a1 + 2 * F);
+    b->b0.assign(b0, b0 + 2 * F);
+    b->delay.assign(delay, delay + F);
+    int64_t fmax = 0;
+    for (int t = 0; t < n_templates; ++t) fmax = std::max(fmax, off[t + 1] - off[t]);
+    b->S = fmax <= (int64_t)8 * kBankLanes ? 8 : 16;
+    b->c_tile = kBankTile;
+    int rc = bank_pack(b);
+    if (rc == SPIIR_OK) {
+        const size_t smem = (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128 +
+                            (size_t)kBankLanes * (kBankSteps + 1) * sizeof(float2) + 16;
+        if (smem > (size_t)kBankMaxSmem)
+            rc = fail(SPIIR_EUNSUPPORTED, "maximum delay %d needs a %zu-byte window; limit %d", dmax, smem,
+                      kBankMaxSmem);
+    }
+    if (rc == SPIIR_OK) rc = bank_alloc_device(b);
+    if (rc == SPIIR_OK) rc = bank_reserve(b, 2048, 0);
+    if (rc != SPIIR_OK) {
+        bank_free(b);
+        return rc;
+    }
+    *out = b;
+    return SPIIR_OK;
+}
+
+extern "C" void spiir_bank_destroy(spiir_bank_t b) { bank_free(b); }
+
+extern "C" int spiir_bank_info(spiir_bank_t b, int *n_det, int *n_templates, int64_t *n_filters,
+                               int32_t *max_delay) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (n_det) *n_det = b->n_det;
+    if (n_templates) *n_templates = b->T;
+    if (n_filters) *n_filters = b->F;
+    if (max_delay) *max_delay = b->dmax;
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_bank_reset(spiir_bank_t b, void *stream) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    SPIIR_CUDA_TRY(cudaMemsetAsync(b->state, 0, sizeof(float4) * b->state_det_stride * b->n_det, s));
+    for (int i = 0; i < 2; ++i)
+        if (b->xbuf[i]) SPIIR_CUDA_TRY(cudaMemsetAsync(b->xbuf[i], 0, sizeof(float) * b->xpitch * b->n_det, s));
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_bank_state_bytes(spiir_bank_t b, size_t *bytes) {
+    if (!b || !bytes) return fail(SPIIR_EINVAL, "NULL argument");
+    *bytes = (size_t)b->n_det * b->F * 2 * sizeof(float) + (size_t)b->n_det * b->dmax * sizeof(float);
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_bank_get_state(spiir_bank_t b, void *host, size_t bytes) {
+    size_t need = 0;
+    SPIIR_TRY(spiir_bank_state_bytes(b, &need));
+    if (!host || bytes != need) return fail(SPIIR_EINVAL, "state buffer has %zu bytes, need %zu", bytes, need);
+    SPIIR_CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<float4> st((size_t)b->state_det_stride * b->n_det);
+    SPIIR_CUDA_TRY(cudaMemcpy(st.data(), b->state, st.size() * sizeof(float4), cudaMemcpyDeviceToHost));
+    float *o = static_cast<float *>(host);
+    const int NP = b->S / 2;
+    for (int d = 0; d < b->n_det; ++d)
+        for (int64_t l = 0; l < b->F; ++l) {
+            const int64_t slot = b->slot_of_filter[l];
+            const int64_t ln = slot % kBankLanes, cs = slot / kBankLanes, s = cs % b->S, c = cs / b->S;
+            const float4 v = st[(size_t)d * b->state_det_stride + ((size_t)c * NP + s / 2) * kBankLanes + ln];
+            o[((size_t)d * b->F + l) * 2] = (s % 2 == 0) ? v.x : v.y;
+            o[((size_t)d * b->F + l) * 2 + 1] = (s % 2 == 0) ? v.z : v.w;
+        }
+    float *h = o + (size_t)b->n_det * b->F * 2;
+    if (b->dmax > 0)
+        SPIIR_CUDA_TRY(cudaMemcpy2D(h, b->dmax * 4, b->xbuf[b->cur] + (b->D_pad - b->dmax), b->xpitch * 4,
+                                    b->dmax * 4, b->n_det, cudaMemcpyDeviceToHost));
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_bank_set_state(spiir_bank_t b, const void *host, size_t bytes) {
+    size_t need = 0;
+    SPIIR_TRY(spiir_bank_state_bytes(b, &need));
+    if (!host || bytes != need) return fail(SPIIR_EINVAL, "state buffer has %zu bytes, need %zu", bytes, need);
+    const float *in = static_cast<const float *>(host);
+    for (size_t i = 0; i < need / sizeof(float); ++i)
+        if (!std::isfinite(in[i])) return fail(SPIIR_EINVAL, "state holds a non-finite value at %zu", i);
+    SPIIR_CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<float4> st((size_t)b->state_det_stride * b->n_det, make_float4(0, 0, 0, 0));
+    const int NP = b->S / 2;
+    for (int d = 0; d < b->n_det; ++d)
+        for (int64_t l = 0; l < b->F; ++l) {
+            const int64_t slot = b->slot_of_filter[l];
+            const int64_t ln = slot % kBankLanes, cs = slot / kBankLanes, s = cs % b->S, c = cs / b->S;
+            float4 &v = st[(size_t)d * b->state_det_stride + ((size_t)c * NP + s / 2) * kBankLanes + ln];
+            const float re = in[((size_t)d * b->F + l) * 2], im = in[((size_t)d * b->F + l) * 2 + 1];
+            if (s % 2 == 0) { v.x = re; v.z = im; } else { v.y = re; v.w = im; }
+        }
+    SPIIR_CUDA_TRY(cudaMemcpy(b->state, st.data(), st.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    for (int i = 0; i < 2; ++i)
+        SPIIR_CUDA_TRY(cudaMemset(b->xbuf[i], 0, sizeof(float) * b->xpitch * b->n_det));
+    const float *h = in + (size_t)b->n_det * b->F * 2;
+    if (b->dmax > 0)
+        SPIIR_CUDA_TRY(cudaMemcpy2D(b->xbuf[b->cur] + (b->D_pad - b->dmax), b->xpitch * 4, h, b->dmax * 4,
+                                    b->dmax * 4, b->n_det, cudaMemcpyHostToDevice));
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_filter_chunk(spiir_bank_t b, const float *strain, int64_t strain_pitch, int64_t n,
+                                  float *snr, int64_t snr_pitch, void *stream) {
+    clear_error();
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (!strain || !snr) return fail(SPIIR_EINVAL, "strain or snr pointer is NULL");
+    if (n < 1) return fail(SPIIR_EINVAL, "n = %lld < 1", (long long)n);
+    if (strain_pitch < n || snr_pitch < n)
+        return fail(SPIIR_EINVAL, "pitch smaller than n (strain %lld, snr %lld, n %lld)", (long long)strain_pitch,
+                    (long long)snr_pitch, (long long)n);
+    if (((uintptr_t)snr) % 8 != 0) return fail(SPIIR_EINVAL, "snr pointer is not 8-byte aligned");
+    return bank_filter(b, strain, strain_pitch, n, reinterpret_cast<float2 *>(snr), snr_pitch,
+                       (cudaStream_t)stream);
+}

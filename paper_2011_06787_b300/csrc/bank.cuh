@@ -1,0 +1,73 @@
+// Filter-bank object and kernel arguments (internal).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace spiir {
+
+constexpr int kBankLanes = 256;                // threads (lanes) per block
+constexpr int kBankWarps = kBankLanes / 32;
+constexpr int kBankSteps = 32;                 // time steps per reduction block (R)
+constexpr int kBankTile = 1024;                // time steps per staged strain window
+constexpr int kBankMaxSmem = 227 * 1024;       // dynamic shared memory limit per block
+constexpr int kBankMaxDelay = 32768;           // largest delay whose window fits
+
+struct BankArgs {
+    const float *xbuf;        // [n_det][xpitch] window source: D_pad history + chunk
+    int64_t xpitch;
+    int D_pad;                // history length (>= max delay, multiple of 4)
+    int64_t n;                // samples in this call
+    int c_tile;               // samples per staged window
+    const float2 *are, *aim, *bre, *bim;  // [n_cta][S/2][NL] packed pairs of filters
+    const int *delay;         // [n_cta][S][NL]
+    float4 *state;            // [n_det][n_cta][S/2][NL] (re0, re1, im0, im1)
+    int64_t state_det_stride;
+    const int4 *segs;         // (template, lane_lo, lane_hi, 0) per template, grouped by block
+    const int *seg_off;       // [n_cta + 1]
+    const int *wfirst;        // [n_cta][warps] first block-local segment touching each warp, -1 none
+    const int *cta_active;    // [n_cta] lanes in use
+    float2 *z;                // [T][n_det][zpitch]
+    int64_t zpitch;
+    int n_det;
+    int *status;
+    size_t red_offset, bar_offset;
+};
+
+}  // namespace spiir
+
+struct spiir_bank_s {
+    int device = -1;
+    int n_det = 0, T = 0;
+    int64_t F = 0;
+    int32_t dmax = 0;
+    int D_pad = 0;
+    int S = 8;
+    int c_tile = 1024;
+    int n_cta = 0;
+    std::vector<int64_t> offsets;
+    std::vector<float> a1, b0;
+    std::vector<int32_t> delay;
+    // packed host images
+    std::vector<float2> h_are, h_aim, h_bre, h_bim;
+    std::vector<int> h_delay;
+    std::vector<int64_t> slot_of_filter;
+    std::vector<int4> h_segs;
+    std::vector<int> h_seg_off, h_wfirst, h_active;
+    // device
+    float2 *are = nullptr, *aim = nullptr, *bre = nullptr, *bim = nullptr;
+    int *dly = nullptr;
+    float4 *state = nullptr;
+    int64_t state_det_stride = 0;
+    int4 *segs = nullptr;
+    int *seg_off = nullptr, *wfirst = nullptr, *active = nullptr;
+    float *xbuf[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t xpitch = 0, ncap = 0;
+};
+
+namespace spiir {
+int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int64_t n, float2 *z,
+                int64_t zpitch, cudaStream_t stream);
+}

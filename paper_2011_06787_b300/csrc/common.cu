@@ -1,0 +1,121 @@
+// Error reporting, allocation hook and device status word of the C ABI.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+namespace spiir {
+
+static thread_local std::string g_last_error;
+static std::atomic<int> g_fail_allocs{0};
+
+int fail(int code, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+static bool take_injected_failure() {
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    }
+    return false;
+}
+
+int dev_alloc(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (bytes == 0) return SPIIR_OK;
+    if (take_injected_failure())
+        return fail(SPIIR_ENOMEM, "device allocation of %zu bytes for %s failed (injected)", bytes,
+                    what);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SPIIR_ENOMEM : SPIIR_ECUDA,
+                    "cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+    }
+    return SPIIR_OK;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+int host_alloc_pinned(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (bytes == 0) return SPIIR_OK;
+    if (take_injected_failure())
+        return fail(SPIIR_ENOMEM, "pinned host allocation of %zu bytes for %s failed (injected)",
+                    bytes, what);
+    cudaError_t e = cudaMallocHost(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(SPIIR_ENOMEM, "cudaMallocHost of %zu bytes for %s failed: %s", bytes, what,
+                    cudaGetErrorString(e));
+    }
+    return SPIIR_OK;
+}
+
+void host_free_pinned(void *p) {
+    if (p) cudaFreeHost(p);
+}
+
+static std::mutex g_status_mu;
+static int *g_status[64];
+
+int *device_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status[dev]) {
+        int *p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaMemset(p, 0, sizeof(int));
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+}  // namespace spiir
+
+using namespace spiir;
+
+extern "C" int spiir_version(void) { return 100; }
+
+extern "C" int spiir_last_error(char *buf, size_t len) {
+    const std::string &m = g_last_error;
+    if (buf && len) {
+        size_t n = m.size() < len - 1 ? m.size() : len - 1;
+        memcpy(buf, m.data(), n);
+        buf[n] = 0;
+    }
+    return (int)m.size();
+}
+
+extern "C" void spiir_debug_fail_allocs(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
+
+extern "C" int spiir_device_status(int clear) {
+    int *w = device_status_word();
+    if (!w) return fail(SPIIR_ECUDA, "device status word unavailable");
+    SPIIR_CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    SPIIR_CUDA_TRY(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear) SPIIR_CUDA_TRY(cudaMemset(w, 0, sizeof(int)));
+    if (v & kStatusTimeout) return fail(SPIIR_ETIMEOUT, "a bounded device-side wait gave up");
+    return SPIIR_OK;
+}

@@ -1,0 +1,124 @@
+// Streaming pipeline: per strain chunk, filter bank -> SNR rows with 2 H samples of
+// history -> coherent scan.  Output sample j of a call is geocentric sample
+// (chunk start) + j - H, so that the SNR of every detector at k + Delta_I(p) is
+// available when the scan runs.
+#include <algorithm>
+
+#include "bank.cuh"
+#include "coherent.cuh"
+
+struct spiir_pipeline_s {
+    spiir_bank_s *bank = nullptr;
+    spiir_sky_s *sky = nullptr;
+    int64_t max_chunk = 0;
+    int H = 0;
+    int64_t pitch = 0;  // float2 entries per SNR row: 2 H history + max_chunk
+    float2 *zpad[2] = {nullptr, nullptr};
+    int cur = 0;
+    // device staging for the host-buffer entry point
+    float *strain_dev = nullptr;
+    float *ms_dev = nullptr, *nl_dev = nullptr;
+    int32_t *am_dev = nullptr;
+};
+
+namespace spiir {
+
+static void pipe_free(spiir_pipeline_s *p) {
+    if (!p) return;
+    dev_free(p->zpad[0]);
+    dev_free(p->zpad[1]);
+    dev_free(p->strain_dev);
+    dev_free(p->ms_dev);
+    dev_free(p->nl_dev);
+    dev_free(p->am_dev);
+    delete p;
+}
+
+static int pipe_run(spiir_pipeline_s *p, const float *strain, int64_t spitch, int64_t n, float *ms, int32_t *am,
+                    float *nl, float *map, cudaStream_t s) {
+    const int T = p->bank->T, nd = p->bank->n_det, H = p->H;
+    float2 *z = p->zpad[p->cur];
+    SPIIR_TRY(bank_filter(p->bank, strain, spitch, n, z + 2 * H, p->pitch, s));
+    SPIIR_TRY(coherent_scan(p->sky, z, p->pitch, T, n, ms, am, nl, map, s));
+    const int nxt = 1 - p->cur;
+    if (H > 0)
+        SPIIR_CUDA_TRY(cudaMemcpy2DAsync(p->zpad[nxt], p->pitch * sizeof(float2), z + n, p->pitch * sizeof(float2),
+                                         2 * H * sizeof(float2), (size_t)T * nd, cudaMemcpyDeviceToDevice, s));
+    p->cur = nxt;
+    return SPIIR_OK;
+}
+
+}  // namespace spiir
+
+using namespace spiir;
+
+extern "C" int spiir_pipeline_create(spiir_bank_t bank, spiir_sky_t sky, int64_t max_chunk, spiir_pipeline_t *out) {
+    clear_error();
+    if (!out) return fail(SPIIR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!bank || !sky) return fail(SPIIR_EINVAL, "bank or sky is NULL");
+    if (bank->n_det != sky->n_det)
+        return fail(SPIIR_EINVAL, "bank has %d detectors, sky tables %d", bank->n_det, sky->n_det);
+    if (max_chunk < 1 || max_chunk > (1 << 24)) return fail(SPIIR_EINVAL, "max_chunk = %lld", (long long)max_chunk);
+    spiir_pipeline_s *p = new (std::nothrow) spiir_pipeline_s();
+    if (!p) return fail(SPIIR_ENOMEM, "host allocation of the pipeline failed");
+    p->bank = bank;
+    p->sky = sky;
+    p->max_chunk = max_chunk;
+    p->H = sky->halo;
+    p->pitch = ((2 * p->H + max_chunk + 1) / 2) * 2;
+    const size_t zbytes = sizeof(float2) * (size_t)p->pitch * bank->T * bank->n_det;
+    int rc = SPIIR_OK;
+    for (int i = 0; i < 2 && rc == SPIIR_OK; ++i) {
+        rc = dev_alloc((void **)&p->zpad[i], zbytes, "SNR rows");
+        if (rc == SPIIR_OK && cudaMemset(p->zpad[i], 0, zbytes) != cudaSuccess) rc = fail(SPIIR_ECUDA, "memset failed");
+    }
+    if (rc == SPIIR_OK) rc = dev_alloc((void **)&p->strain_dev, sizeof(float) * bank->n_det * max_chunk, "strain staging");
+    if (rc == SPIIR_OK) rc = dev_alloc((void **)&p->ms_dev, sizeof(float) * bank->T * max_chunk, "max staging");
+    if (rc == SPIIR_OK) rc = dev_alloc((void **)&p->nl_dev, sizeof(float) * bank->T * max_chunk, "null staging");
+    if (rc == SPIIR_OK) rc = dev_alloc((void **)&p->am_dev, sizeof(int32_t) * bank->T * max_chunk, "argmax staging");
+    if (rc != SPIIR_OK) {
+        pipe_free(p);
+        return rc;
+    }
+    *out = p;
+    return SPIIR_OK;
+}
+
+extern "C" void spiir_pipeline_destroy(spiir_pipeline_t p) { pipe_free(p); }
+
+extern "C" int spiir_pipeline_reset(spiir_pipeline_t p, void *stream) {
+    if (!p) return fail(SPIIR_EINVAL, "pipeline is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    SPIIR_TRY(spiir_bank_reset(p->bank, stream));
+    const size_t zbytes = sizeof(float2) * (size_t)p->pitch * p->bank->T * p->bank->n_det;
+    for (int i = 0; i < 2; ++i) SPIIR_CUDA_TRY(cudaMemsetAsync(p->zpad[i], 0, zbytes, s));
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_pipeline_run(spiir_pipeline_t p, const float *strain, int64_t spitch, int64_t n, float *ms,
+                                  int32_t *am, float *nl, float *map, void *stream) {
+    clear_error();
+    if (!p) return fail(SPIIR_EINVAL, "pipeline is NULL");
+    if (!strain || !ms || !am || !nl) return fail(SPIIR_EINVAL, "NULL buffer");
+    if (n < 1 || n > p->max_chunk) return fail(SPIIR_EINVAL, "n = %lld outside [1, %lld]", (long long)n, (long long)p->max_chunk);
+    if (spitch < n) return fail(SPIIR_EINVAL, "strain_pitch < n");
+    return pipe_run(p, strain, spitch, n, ms, am, nl, map, (cudaStream_t)stream);
+}
+
+extern "C" int spiir_pipeline_run_host(spiir_pipeline_t p, const float *strain_host, int64_t n, float *ms_host,
+                                       int32_t *am_host, float *nl_host, void *stream) {
+    clear_error();
+    if (!p) return fail(SPIIR_EINVAL, "pipeline is NULL");
+    if (!strain_host || !ms_host || !am_host || !nl_host) return fail(SPIIR_EINVAL, "NULL buffer");
+    if (n < 1 || n > p->max_chunk) return fail(SPIIR_EINVAL, "n = %lld outside [1, %lld]", (long long)n, (long long)p->max_chunk);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int T = p->bank->T, nd = p->bank->n_det;
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(p->strain_dev, strain_host, sizeof(float) * nd * n, cudaMemcpyHostToDevice, s));
+    SPIIR_TRY(pipe_run(p, p->strain_dev, n, n, p->ms_dev, p->am_dev, p->nl_dev, nullptr, s));
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(ms_host, p->ms_dev, sizeof(float) * T * n, cudaMemcpyDeviceToHost, s));
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(am_host, p->am_dev, sizeof(int32_t) * T * n, cudaMemcpyDeviceToHost, s));
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(nl_host, p->nl_dev, sizeof(float) * T * n, cudaMemcpyDeviceToHost, s));
+    SPIIR_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPIIR_OK;
+}

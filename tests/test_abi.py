@@ -1,0 +1,73 @@
+"""C ABI: the library loads, exports every entry point declared in include/spiir.h, and rejects
+invalid arguments on the host before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2011_06787_b300 as sp
+from paper_2011_06787_b300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(spiir_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = native.lib()
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared == set(native.SIGNATURES), declared ^ set(native.SIGNATURES)
+
+
+def test_version_and_error_text():
+    assert sp.version() >= 100
+    assert isinstance(native.last_error(), str)
+
+
+@pytest.mark.parametrize("kwargs,msg", [
+    (dict(n_det=0), "n_det"),
+    (dict(offsets=[0, 3, 2]), "decrease"),
+    (dict(offsets=[1, 2, 3]), "filter_offsets[0]"),
+    (dict(a1=np.array([0.5, 1.2, 0.3], dtype=np.complex64)), "|a1| >= 1"),
+    (dict(b0=np.array([np.nan, 0, 0], dtype=np.complex64)), "non-finite"),
+    (dict(delay=[0, -1, 2]), "delay"),
+])
+def test_bank_create_rejects_invalid_arguments(kwargs, msg):
+    args = dict(n_det=2, offsets=[0, 1, 3], a1=np.full(3, 0.5, np.complex64), b0=np.ones(3, np.complex64),
+                delay=[0, 1, 2])
+    args.update(kwargs)
+    with pytest.raises(sp.SpiirError) as e:
+        sp.Bank(args["n_det"], args["offsets"], args["a1"], args["b0"], args["delay"])
+    assert e.value.code == native.EINVAL
+    assert msg in str(e.value)
+
+
+def test_sky_create_rejects_invalid_arguments():
+    with pytest.raises(sp.SpiirError):
+        sp.Sky(np.zeros((4, 5), np.int32), np.zeros((4, 5, 2), np.float32), np.zeros((4, 5, 3), np.float32))
+    with pytest.raises(sp.SpiirError):
+        sp.Sky(np.full((4, 3), 5000, np.int32), np.zeros((4, 3, 2), np.float32), np.zeros((4, 3, 1), np.float32))
+
+
+def test_sky_tables_rejects_bad_geometry():
+    pos = np.zeros((3, 3))
+    arms = np.eye(3)
+    with pytest.raises(sp.SpiirError):
+        sp.sky_tables(pos, arms * 2.0, arms, np.ones(3), 4, 2048.0)   # arms not unit
+    with pytest.raises(sp.SpiirError):
+        sp.sky_tables(pos, arms, arms, np.array([1.0, -1.0, 1.0]), 4, 2048.0)  # negative sigma
+    with pytest.raises(sp.SpiirError):
+        sp.sky_tables(pos, arms, arms, np.ones(3), 0, 2048.0)

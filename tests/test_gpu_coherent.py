@@ -1,0 +1,133 @@
+"""GPU coherent scan (K2) and the streaming pipeline against the FP64 oracle, through the C ABI
+(Sec. II.C.1 Eq. (llr_form), Eq. (null_def); App. A)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import assert_coherent_close, assert_snr_close, cuda_ok
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs CUDA")]
+
+
+def _sky(cfg, n_det, nside, sig):
+    import paper_2011_06787_b300 as sp
+    det = synth.detectors(cfg, n_det)
+    sigma = synth.noise_weights(cfg, n_det, *sig)
+    tabs = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, nside, 2048.0)
+    _, G, d_or = oracle.sky_geometry(det, sigma, nside, 2048.0)
+    return sp.Sky(*tabs), G, d_or
+
+
+def _scan(sky, z_pad, n, skymap=False):
+    import torch
+    T = z_pad.shape[0]
+    zt = torch.from_numpy(np.ascontiguousarray(z_pad.astype(np.complex64))).cuda()
+    ms = torch.empty((T, n), dtype=torch.float32, device="cuda")
+    am = torch.empty((T, n), dtype=torch.int32, device="cuda")
+    nl = torch.empty((T, n), dtype=torch.float32, device="cuda")
+    mp = torch.empty((T, sky.n_pix, n), dtype=torch.float32, device="cuda") if skymap else None
+    sky.scan(zt, n, ms, am, nl, mp)
+    torch.cuda.synchronize()
+    return ms.cpu().numpy(), am.cpu().numpy(), nl.cpu().numpy(), (mp.cpu().numpy() if skymap else None)
+
+
+@pytest.mark.parametrize("cfg,n_det,nside,sig,T,n", [
+    (0, 2, 4, (1.0, 1.0), 4, 2000),
+    (1, 3, 16, (0.5, 2.0), 3, 700),
+    (5, 4, 4, (0.7, 1.6), 2, 1100),
+])
+def test_scan_parity_gaussian_snr(cfg, n_det, nside, sig, T, n):
+    sky, G, d_or = _sky(cfg, n_det, nside, sig)
+    H = sky.halo
+    z = synth.complex_gaussian_snr(cfg, (T, n_det, n + 2 * H + 5))
+    ms, am, nl, _ = _scan(sky, z, n)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    if n_det == 2:
+        assert np.all(nl == 0)
+
+
+def test_skymap_mode_matches_oracle_map():
+    sky, G, d_or = _sky(1, 3, 4, (0.5, 2.0))
+    H = sky.halo
+    n = 777
+    z = synth.complex_gaussian_snr(1, (2, 3, n + 2 * H), sub=3)
+    ms, am, nl, mp = _scan(sky, z, n, skymap=True)
+    _, _, _, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    # device map is [T][P][n]; oracle map is [T][n][P]
+    mp = np.transpose(mp, (0, 2, 1))
+    assert np.all(np.abs(mp - sm_or) <= 1e-4 * sm_or.max(axis=-1, keepdims=True))
+    np.testing.assert_array_equal(ms, mp.max(axis=-1))
+
+
+def test_noiseless_injection_found_at_true_pixel():
+    sky, G, d_or = _sky(1, 3, 16, (0.5, 2.0))
+    H = sky.halo
+    n, k0, pstar = 300, 120, 1999
+    j = np.arange(-4 * H, n + 4 * H)
+    f = np.exp(-0.5 * ((j - k0) / 0.6) ** 2) * np.exp(0.9j * j)
+    A = np.array([1.0 + 0.3j, -0.4 + 0.8j])
+    amp = G[pstar] @ A
+    z = np.zeros((1, 3, n + 2 * H), dtype=np.complex128)
+    for I in range(3):
+        idx = np.arange(n + 2 * H) - H - d_or[pstar, I]
+        z[0, I] = amp[I] * f[idx + 4 * H]
+    ms, am, nl, _ = _scan(sky, z, n)
+    tot = sum(abs(z[0, I, H + k0 + d_or[pstar, I]]) ** 2 for I in range(3))
+    ms_or, am_or, _, _ = oracle.coherent(z.astype(np.complex64), G, d_or, H, n)
+    assert am_or[0, k0] == pstar
+    assert am[0, k0] == pstar
+    assert abs(ms[0, k0] - tot) <= 1e-4 * tot
+    assert nl[0, k0] <= 1e-4 * tot
+
+
+def test_argmax_ties_take_lowest_pixel():
+    import paper_2011_06787_b300 as sp
+    # four identical pixels
+    d = np.zeros((4, 3), np.int32)
+    us = np.tile(np.array([[1, 0], [0, 1], [0, 0]], np.float32)[None], (4, 1, 1))
+    un = np.tile(np.array([[0], [0], [1]], np.float32)[None], (4, 1, 1))
+    sky = sp.Sky(d, us, un)
+    z = np.ones((2, 3, 50), np.complex64)
+    ms, am, nl, _ = _scan(sky, z, 50)
+    assert np.all(am == 0) and np.allclose(ms, 2.0) and np.allclose(nl, 1.0)
+
+
+def _pipeline_stream(bank, sky, strain, chunk, host=False):
+    import torch
+    import paper_2011_06787_b300 as sp
+    b = sp.Bank(strain.shape[0], bank.offsets, bank.a1, bank.b0, bank.delay)
+    pipe = sp.Pipeline(b, sky, max_chunk=chunk)
+    T = bank.n_templates
+    outs = []
+    for s in range(0, strain.shape[1], chunk):
+        x = np.ascontiguousarray(strain[:, s:s + chunk])
+        n = x.shape[1]
+        if host:
+            ms = np.zeros((T, n), np.float32); am = np.zeros((T, n), np.int32); nl = np.zeros((T, n), np.float32)
+            pipe.run_host(x, ms, am, nl)
+            outs.append((ms, am, nl))
+        else:
+            ms = torch.empty((T, n), dtype=torch.float32, device="cuda")
+            am = torch.empty((T, n), dtype=torch.int32, device="cuda")
+            nl = torch.empty((T, n), dtype=torch.float32, device="cuda")
+            pipe.run(torch.from_numpy(x).cuda(), ms, am, nl)
+            outs.append((ms.cpu().numpy(), am.cpu().numpy(), nl.cpu().numpy()))
+    return [np.concatenate([o[i] for o in outs], axis=1) for i in range(3)]
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_streaming_pipeline_matches_oracle(host):
+    sky, G, d_or = _sky(1, 3, 4, (0.5, 2.0))
+    H = sky.halo
+    bank = synth.online_bank(6)
+    strain = np.concatenate([synth.online_chunk(i) for i in range(3)], axis=1)[:, :5000]
+    ms, am, nl = _pipeline_stream(bank, sky, strain, 1024, host=host)
+    # oracle: whole-stream SNR, H zeros before the stream start (values before it are 0),
+    # output j of the stream is geocentric sample j - H
+    z_or, _, _ = oracle.filter_bank(strain, bank.offsets, bank.a1, bank.b0, bank.delay)
+    N = strain.shape[1]
+    zp = np.concatenate([np.zeros((bank.n_templates, 3, 2 * H)), z_or], axis=2)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(zp, G, d_or, H, N, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
