@@ -98,6 +98,19 @@ int spiir_bank_state_bytes(spiir_bank_t bank, size_t *bytes);
 int spiir_bank_get_state(spiir_bank_t bank, void *host, size_t bytes);
 int spiir_bank_set_state(spiir_bank_t bank, const void *host, size_t bytes);
 
+/* Launch shape of the filter-bank kernel, a tuning knob: the filtered values do not depend on
+ * it beyond the order of floating-point summation.  filters_per_lane in {4, 8, 16},
+ * lanes_per_block in {128, 256}, steps_per_reduce in {16, 32}, tile a multiple of
+ * steps_per_reduce up to 8192 (samples per staged strain window).  The streaming state is
+ * kept.  Synchronises the device.  SPIIR_EUNSUPPORTED if a template does not fit or the
+ * window does not fit in shared memory; the bank then keeps its previous shape.
+ * Defaults: 8, 128, 32, 1024; 256 lanes when a template exceeds 1024 filters and 16
+ * filters per lane when it exceeds 2048. */
+int spiir_bank_set_shape(spiir_bank_t bank, int filters_per_lane, int lanes_per_block,
+                         int steps_per_reduce, int tile);
+int spiir_bank_get_shape(spiir_bank_t bank, int *filters_per_lane, int *lanes_per_block,
+                         int *steps_per_reduce, int *tile);
+
 /* Filter one chunk of strain and advance the streaming state.
  *   strain_dev [n_det][strain_pitch] float; samples 0..n-1 of each row are this chunk,
  *              continuing the stream seen by previous calls.
@@ -139,6 +152,14 @@ int spiir_sky_create(int n_det, int n_pix, const int32_t *delays_host, const flo
                      const float *u_null_host, spiir_sky_t *out);
 void spiir_sky_destroy(spiir_sky_t sky);
 int spiir_sky_info(spiir_sky_t sky, int *n_det, int *n_pix, int *halo);
+
+/* Launch shape of the coherent scan for 2 and 3 detectors, a tuning knob that does not change
+ * results: threads per block in {256, 512}, pairs of output samples per thread in {1, 2}.
+ * Synchronises the device.  grouped (output) is 1 when the grouped scan applies: 2 or 3
+ * detectors, an orthonormal U with a rank-2 signal plane, at most 65535 pixels.  Default
+ * 256 threads, 2 pairs. */
+int spiir_sky_set_scan_shape(spiir_sky_t sky, int threads, int pairs);
+int spiir_sky_get_scan_shape(spiir_sky_t sky, int *threads, int *pairs, int *grouped);
 
 /* Coherent all-sky scan -- Sec. II.C.1 Eq. (llr_form) and Eq. (null_def), App. A:
  *     w_I(p, k)   = z_I[k + Delta_I(p)]

@@ -102,6 +102,16 @@ class Bank:
                                               out.stride(1), _stream_ptr(stream)))
         return out
 
+    def set_shape(self, filters_per_lane=8, lanes_per_block=128, steps_per_reduce=32, tile=1024):
+        """Launch shape of the filter-bank kernel (spiir_bank_set_shape); keeps the stream state."""
+        check(native.lib().spiir_bank_set_shape(self._h, int(filters_per_lane), int(lanes_per_block),
+                                                int(steps_per_reduce), int(tile)))
+
+    def get_shape(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        check(native.lib().spiir_bank_get_shape(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     def state_bytes(self) -> int:
         n = ctypes.c_size_t()
         check(native.lib().spiir_bank_state_bytes(self._h, ctypes.byref(n)))
@@ -165,6 +175,14 @@ class Sky:
             self.close()
         except Exception:
             pass
+
+    def set_scan_shape(self, threads=256, pairs=2):
+        check(native.lib().spiir_sky_set_scan_shape(self._h, int(threads), int(pairs)))
+
+    def get_scan_shape(self):
+        v = [ctypes.c_int() for _ in range(3)]
+        check(native.lib().spiir_sky_get_scan_shape(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def scan(self, snr, n: int, max_stat, argmax, null_stat, skymap=None, stream=None):
         """snr: complex64 CUDA tensor [T][n_det][pitch], entry H + k = output sample k.

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "bank.cuh"
@@ -28,11 +29,10 @@ namespace spiir {
 // ---------------------------------------------------------------------------------------
 // Kernel
 
-template <int S>
-__global__ void __launch_bounds__(kBankLanes, 1) k_filter_bank(const __grid_constant__ BankArgs a) {
+template <int S, int NL, int R>
+__global__ void __launch_bounds__(NL, 1) k_filter_bank(const __grid_constant__ BankArgs a) {
     constexpr int NP = S / 2;
-    constexpr int NL = kBankLanes;
-    constexpr int R = kBankSteps;
+    constexpr int NW = NL / 32;
     extern __shared__ __align__(128) unsigned char smem[];
     float *xw = reinterpret_cast<float *>(smem);
     float2 *red = reinterpret_cast<float2 *>(smem + a.red_offset);
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kBankLanes, 1) k_filter_bank(const __grid_cons
     // segment tables of this block
     const int seg0 = a.seg_off[cta];
     const int nseg = a.seg_off[cta + 1] - seg0;
-    const int wfirst = a.wfirst[cta * kBankWarps + warp];
+    const int wfirst = a.wfirst[cta * NW + warp];
 
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kBankLanes, 1) k_filter_bank(const __grid_cons
                 const int4 g = a.segs[seg0 + sg];
                 float2 acc = make_float2(0.f, 0.f);
                 for (int w = g.y >> 5; w <= (g.z - 1) >> 5; ++w) {
-                    const float2 v = red[(w * 32 + (sg - a.wfirst[cta * kBankWarps + w])) * (R + 1) + r];
+                    const float2 v = red[(w * 32 + (sg - a.wfirst[cta * NW + w])) * (R + 1) + r];
                     acc.x += v.x;
                     acc.y += v.y;
                 }
@@ -177,26 +177,137 @@ __global__ void __launch_bounds__(kBankLanes, 1) k_filter_bank(const __grid_cons
     }
 }
 
-template <int S>
+template <int S, int NL, int R>
 static int launch_bank(const BankArgs &a, int n_cta, int n_det, size_t smem, cudaStream_t stream) {
     static bool attr_set = false;
     if (!attr_set) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_filter_bank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_filter_bank<S, NL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kBankMaxSmem));
         attr_set = true;
     }
-    k_filter_bank<S><<<dim3(n_cta, n_det), kBankLanes, smem, stream>>>(a);
+    k_filter_bank<S, NL, R><<<dim3(n_cta, n_det), NL, smem, stream>>>(a);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
+}
+
+template <int S, int NL>
+static int launch_bank_r(const BankArgs &a, int R, int n_cta, int n_det, size_t smem, cudaStream_t s) {
+    return R == 16 ? launch_bank<S, NL, 16>(a, n_cta, n_det, smem, s) : launch_bank<S, NL, 32>(a, n_cta, n_det, smem, s);
+}
+
+template <int S>
+static int launch_bank_nl(const BankArgs &a, int NL, int R, int n_cta, int n_det, size_t smem, cudaStream_t s) {
+    return NL == 128 ? launch_bank_r<S, 128>(a, R, n_cta, n_det, smem, s) : launch_bank_r<S, 256>(a, R, n_cta, n_det, smem, s);
+}
+
+static int launch_bank_any(const spiir_bank_s *b, const BankArgs &a, size_t smem, cudaStream_t s) {
+    switch (b->S) {
+        case 4: return launch_bank_nl<4>(a, b->NL, b->R, b->n_cta, b->n_det, smem, s);
+        case 8: return launch_bank_nl<8>(a, b->NL, b->R, b->n_cta, b->n_det, smem, s);
+        default: return launch_bank_nl<16>(a, b->NL, b->R, b->n_cta, b->n_det, smem, s);
+    }
+}
+
+size_t bank_smem_bytes(const spiir_bank_s *b) {
+    const size_t win = (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
+    return win + (size_t)b->NL * (b->R + 1) * sizeof(float2) + 16;
 }
 
 // ---------------------------------------------------------------------------------------
 // Host: packing
 
+// Place the filters of the templates of block c into (lane, slot) cells.  In the kernel, the
+// 32 lanes of a warp load x[k - d] for the same slot in one shared-memory instruction; two
+// different delays with the same residue mod 32 hit the same bank and serialise.  Rows
+// (warp, slot) are therefore filled greedily with distinct residues: each cell takes a filter
+// of its own template from the residue class with the most filters left that is still free in
+// the row, most loaded templates first.  When every remaining residue of a template is taken
+// in the row, the cell stays empty (zero coefficients) if the template has spare cells, and
+// otherwise accepts a conflict.  Empty cells reuse a delay already read in the row, so they
+// cost no extra bank access.
+static void assign_cells(spiir_bank_s *b, int c, const std::vector<int> &lane_t, const std::vector<int> &members) {
+    const int S = b->S, NL = b->NL, NP = S / 2;
+    std::map<int, std::vector<std::vector<int64_t>>> pools;  // template -> residue -> filters
+    std::map<int, int64_t> rem_f, rem_c;
+    for (int t : members) {
+        auto &P = pools[t];
+        P.assign(32, {});
+        for (int64_t l = b->offsets[t]; l < b->offsets[t + 1]; ++l) P[b->delay[l] & 31].push_back(l);
+        // pop from the back: keep a deterministic order within a residue class
+        for (auto &v : P) std::reverse(v.begin(), v.end());
+        rem_f[t] = b->offsets[t + 1] - b->offsets[t];
+        int64_t ln = 0;
+        for (int j = 0; j < NL; ++j) ln += (lane_t[j] == t);
+        rem_c[t] = ln * S;
+    }
+    auto place = [&](int ln, int s, int64_t l, int32_t d) {
+        const int64_t slot = ((int64_t)c * S + s) * NL + ln;
+        b->h_delay[slot] = d;
+        if (l < 0) return;
+        b->slot_of_filter[l] = slot;
+        const size_t pi = ((size_t)c * NP + s / 2) * NL + ln;
+        float2 *ar = &b->h_are[pi], *ai = &b->h_aim[pi], *br = &b->h_bre[pi], *bi = &b->h_bim[pi];
+        if (s % 2 == 0) {
+            ar->x = b->a1[2 * l]; ai->x = b->a1[2 * l + 1];
+            br->x = b->b0[2 * l]; bi->x = b->b0[2 * l + 1];
+        } else {
+            ar->y = b->a1[2 * l]; ai->y = b->a1[2 * l + 1];
+            br->y = b->b0[2 * l]; bi->y = b->b0[2 * l + 1];
+        }
+    };
+    for (int s = 0; s < S; ++s) {
+        for (int w = 0; w < NL / 32; ++w) {
+            std::vector<int> ls;
+            for (int j = 32 * w; j < 32 * w + 32; ++j)
+                if (lane_t[j] >= 0) ls.push_back(j);
+            if (ls.empty()) continue;
+            std::stable_sort(ls.begin(), ls.end(), [&](int x, int y) {
+                const int tx = lane_t[x], ty = lane_t[y];
+                return (double)rem_f[tx] / std::max<int64_t>(1, rem_c[tx]) >
+                       (double)rem_f[ty] / std::max<int64_t>(1, rem_c[ty]);
+            });
+            uint32_t used = 0;
+            int32_t row_delay = -1;
+            std::vector<int> empty;
+            for (int ln : ls) {
+                const int t = lane_t[ln];
+                auto &P = pools[t];
+                rem_c[t] -= 1;
+                if (rem_f[t] == 0) {
+                    empty.push_back(ln);
+                    continue;
+                }
+                int best = -1;
+                for (int r = 0; r < 32; ++r)
+                    if (!P[r].empty() && !(used >> r & 1u) && (best < 0 || P[r].size() > P[best].size())) best = r;
+                if (best < 0) {
+                    if (rem_f[t] <= rem_c[t]) {
+                        empty.push_back(ln);
+                        continue;
+                    }
+                    for (int r = 0; r < 32; ++r)
+                        if (!P[r].empty() && (best < 0 || P[r].size() > P[best].size())) best = r;
+                }
+                const int64_t l = P[best].back();
+                P[best].pop_back();
+                rem_f[t] -= 1;
+                used |= 1u << best;
+                if (row_delay < 0) row_delay = b->delay[l];
+                place(ln, s, l, b->delay[l]);
+            }
+            for (int ln : empty) place(ln, s, -1, row_delay < 0 ? 0 : row_delay);
+            // unused lanes of a busy warp run zero filters too: read the same address
+            for (int j = 32 * w; j < 32 * w + 32; ++j)
+                if (lane_t[j] < 0) place(j, s, -1, row_delay < 0 ? 0 : row_delay);
+        }
+    }
+}
+
 int bank_pack(spiir_bank_s *b) {
     const int T = b->T;
     const int S = b->S;
-    const int NL = kBankLanes;
+    const int NL = b->NL;
+    const int NW = NL / 32;
     std::vector<int> lanes(T);
     for (int t = 0; t < T; ++t) {
         const int64_t f = b->offsets[t + 1] - b->offsets[t];
@@ -240,53 +351,37 @@ int bank_pack(spiir_bank_s *b) {
     b->slot_of_filter.assign((size_t)b->F, -1);
     b->h_segs.clear();
     b->h_seg_off.assign(n_cta + 1, 0);
-    b->h_wfirst.assign((size_t)n_cta * kBankWarps, -1);
+    b->h_wfirst.assign((size_t)n_cta * NW, -1);
     b->h_active.assign(n_cta, 0);
+    std::vector<int> lane_t(NL);
     for (int c = 0; c < n_cta; ++c) {
         // within a block, templates in ascending index order
         std::sort(members[c].begin(), members[c].end());
         int lane0 = 0;
         b->h_seg_off[c] = (int)b->h_segs.size();
+        std::fill(lane_t.begin(), lane_t.end(), -1);
         for (int t : members[c]) {
-            const int64_t lo = b->offsets[t], hi = b->offsets[t + 1];
-            std::vector<int64_t> fl(hi - lo);
-            std::iota(fl.begin(), fl.end(), lo);
-            // longest delays first: a lane's filters then read neighbouring window entries
-            std::stable_sort(fl.begin(), fl.end(),
-                             [&](int64_t x, int64_t y) { return b->delay[x] > b->delay[y]; });
-            for (size_t q = 0; q < fl.size(); ++q) {
-                const int ln = lane0 + (int)(q / S), s = (int)(q % S);
-                const int64_t l = fl[q];
-                const int64_t slot = ((int64_t)c * S + s) * NL + ln;
-                b->slot_of_filter[l] = slot;
-                b->h_delay[slot] = b->delay[l];
-                const size_t pi = ((size_t)c * NP + s / 2) * NL + ln;
-                float2 *ar = &b->h_are[pi], *ai = &b->h_aim[pi], *br = &b->h_bre[pi], *bi = &b->h_bim[pi];
-                if (s % 2 == 0) {
-                    ar->x = b->a1[2 * l]; ai->x = b->a1[2 * l + 1];
-                    br->x = b->b0[2 * l]; bi->x = b->b0[2 * l + 1];
-                } else {
-                    ar->y = b->a1[2 * l]; ai->y = b->a1[2 * l + 1];
-                    br->y = b->b0[2 * l]; bi->y = b->b0[2 * l + 1];
-                }
-            }
+            for (int j = 0; j < lanes[t]; ++j) lane_t[lane0 + j] = t;
             b->h_segs.push_back(make_int4(t, lane0, lane0 + lanes[t], 0));
             lane0 += lanes[t];
         }
         b->h_active[c] = lane0;
+        assign_cells(b, c, lane_t, members[c]);
         const int s0 = b->h_seg_off[c];
         const int ns = (int)b->h_segs.size() - s0;
-        for (int w = 0; w < kBankWarps; ++w) {
+        for (int w = 0; w < NW; ++w) {
             for (int sg = 0; sg < ns; ++sg) {
                 const int4 g = b->h_segs[s0 + sg];
                 if (g.z > w * 32 && g.y < w * 32 + 32) {
-                    b->h_wfirst[c * kBankWarps + w] = sg;
+                    b->h_wfirst[c * NW + w] = sg;
                     break;
                 }
             }
         }
     }
     b->h_seg_off[n_cta] = (int)b->h_segs.size();
+    for (int64_t l = 0; l < b->F; ++l)
+        if (b->slot_of_filter[l] < 0) return fail(SPIIR_EUNSUPPORTED, "internal: filter %lld was not placed", (long long)l);
     return SPIIR_OK;
 }
 
@@ -294,6 +389,17 @@ static int upload(void **dst, const void *src, size_t bytes, const char *what) {
     SPIIR_TRY(dev_alloc(dst, bytes, what));
     if (bytes) SPIIR_CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
     return SPIIR_OK;
+}
+
+static void bank_free_packed(spiir_bank_s *b) {
+    dev_free(b->are); dev_free(b->aim); dev_free(b->bre); dev_free(b->bim);
+    dev_free(b->dly); dev_free(b->state); dev_free(b->segs); dev_free(b->seg_off);
+    dev_free(b->wfirst); dev_free(b->active);
+    b->are = b->aim = b->bre = b->bim = nullptr;
+    b->dly = nullptr;
+    b->state = nullptr;
+    b->segs = nullptr;
+    b->seg_off = b->wfirst = b->active = nullptr;
 }
 
 static void bank_free(spiir_bank_s *b) {
@@ -319,7 +425,7 @@ static int bank_alloc_device(spiir_bank_s *b) {
     SPIIR_TRY(upload((void **)&b->seg_off, b->h_seg_off.data(), b->h_seg_off.size() * sizeof(int), "segment offsets"));
     SPIIR_TRY(upload((void **)&b->wfirst, b->h_wfirst.data(), b->h_wfirst.size() * sizeof(int), "warp segments"));
     SPIIR_TRY(upload((void **)&b->active, b->h_active.data(), b->h_active.size() * sizeof(int), "active lanes"));
-    b->state_det_stride = (int64_t)b->n_cta * (b->S / 2) * kBankLanes;
+    b->state_det_stride = (int64_t)b->n_cta * (b->S / 2) * b->NL;
     SPIIR_TRY(dev_alloc((void **)&b->state, sizeof(float4) * b->state_det_stride * b->n_det, "IIR states"));
     SPIIR_CUDA_TRY(cudaMemset(b->state, 0, sizeof(float4) * b->state_det_stride * b->n_det));
     return SPIIR_OK;
@@ -374,16 +480,12 @@ int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int6
     a.n_det = b->n_det;
     a.status = device_status_word();
     a.red_offset = (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
-    a.bar_offset = a.red_offset + (size_t)kBankLanes * (kBankSteps + 1) * sizeof(float2);
-    const size_t smem = a.bar_offset + 16;
+    a.bar_offset = a.red_offset + (size_t)b->NL * (b->R + 1) * sizeof(float2);
+    const size_t smem = bank_smem_bytes(b);
     if (smem > (size_t)kBankMaxSmem)
         return fail(SPIIR_EUNSUPPORTED, "strain window of %d + %d samples does not fit in shared memory",
                     b->D_pad, b->c_tile);
-    if (b->S == 8) {
-        SPIIR_TRY(launch_bank<8>(a, b->n_cta, b->n_det, smem, stream));
-    } else {
-        SPIIR_TRY(launch_bank<16>(a, b->n_cta, b->n_det, smem, stream));
-    }
+    SPIIR_TRY(launch_bank_any(b, a, smem, stream));
     // the last D_pad samples become the history of the next call
     const int nxt = 1 - b->cur;
     if (b->D_pad > 0)
@@ -439,12 +541,17 @@ extern "C" int spiir_bank_create(int n_det, int n_templates, const int64_t *off,
     b->delay.assign(delay, delay + F);
     int64_t fmax = 0;
     for (int t = 0; t < n_templates; ++t) fmax = std::max(fmax, off[t + 1] - off[t]);
-    b->S = fmax <= (int64_t)8 * kBankLanes ? 8 : 16;
+    // default launch shape (fastest measured on the online-sized bank): 8 filters per lane,
+    // 128 lanes per block; larger blocks, then 16 filters per lane, for big templates
+    b->S = 8;
+    b->NL = 128;
+    b->R = 32;
+    if (fmax > (int64_t)b->S * b->NL) b->NL = 256;
+    if (fmax > (int64_t)b->S * b->NL) b->S = 16;
     b->c_tile = kBankTile;
     int rc = bank_pack(b);
     if (rc == SPIIR_OK) {
-        const size_t smem = (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128 +
-                            (size_t)kBankLanes * (kBankSteps + 1) * sizeof(float2) + 16;
+        const size_t smem = bank_smem_bytes(b);
         if (smem > (size_t)kBankMaxSmem)
             rc = fail(SPIIR_EUNSUPPORTED, "maximum delay %d needs a %zu-byte window; limit %d", dmax, smem,
                       kBankMaxSmem);
@@ -498,8 +605,8 @@ extern "C" int spiir_bank_get_state(spiir_bank_t b, void *host, size_t bytes) {
     for (int d = 0; d < b->n_det; ++d)
         for (int64_t l = 0; l < b->F; ++l) {
             const int64_t slot = b->slot_of_filter[l];
-            const int64_t ln = slot % kBankLanes, cs = slot / kBankLanes, s = cs % b->S, c = cs / b->S;
-            const float4 v = st[(size_t)d * b->state_det_stride + ((size_t)c * NP + s / 2) * kBankLanes + ln];
+            const int64_t ln = slot % b->NL, cs = slot / b->NL, s = cs % b->S, c = cs / b->S;
+            const float4 v = st[(size_t)d * b->state_det_stride + ((size_t)c * NP + s / 2) * b->NL + ln];
             o[((size_t)d * b->F + l) * 2] = (s % 2 == 0) ? v.x : v.y;
             o[((size_t)d * b->F + l) * 2 + 1] = (s % 2 == 0) ? v.z : v.w;
         }
@@ -523,8 +630,8 @@ extern "C" int spiir_bank_set_state(spiir_bank_t b, const void *host, size_t byt
     for (int d = 0; d < b->n_det; ++d)
         for (int64_t l = 0; l < b->F; ++l) {
             const int64_t slot = b->slot_of_filter[l];
-            const int64_t ln = slot % kBankLanes, cs = slot / kBankLanes, s = cs % b->S, c = cs / b->S;
-            float4 &v = st[(size_t)d * b->state_det_stride + ((size_t)c * NP + s / 2) * kBankLanes + ln];
+            const int64_t ln = slot % b->NL, cs = slot / b->NL, s = cs % b->S, c = cs / b->S;
+            float4 &v = st[(size_t)d * b->state_det_stride + ((size_t)c * NP + s / 2) * b->NL + ln];
             const float re = in[((size_t)d * b->F + l) * 2], im = in[((size_t)d * b->F + l) * 2 + 1];
             if (s % 2 == 0) { v.x = re; v.z = im; } else { v.y = re; v.w = im; }
         }
@@ -550,4 +657,59 @@ extern "C" int spiir_filter_chunk(spiir_bank_t b, const float *strain, int64_t s
     if (((uintptr_t)snr) % 8 != 0) return fail(SPIIR_EINVAL, "snr pointer is not 8-byte aligned");
     return bank_filter(b, strain, strain_pitch, n, reinterpret_cast<float2 *>(snr), snr_pitch,
                        (cudaStream_t)stream);
+}
+
+extern "C" int spiir_bank_set_shape(spiir_bank_t b, int filters_per_lane, int lanes_per_block, int steps_per_reduce,
+                                    int tile) {
+    clear_error();
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (filters_per_lane != 4 && filters_per_lane != 8 && filters_per_lane != 16)
+        return fail(SPIIR_EINVAL, "filters_per_lane must be 4, 8 or 16");
+    if (lanes_per_block != 128 && lanes_per_block != 256) return fail(SPIIR_EINVAL, "lanes_per_block must be 128 or 256");
+    if (steps_per_reduce != 16 && steps_per_reduce != 32) return fail(SPIIR_EINVAL, "steps_per_reduce must be 16 or 32");
+    if (tile < steps_per_reduce || tile > 8192 || tile % steps_per_reduce != 0)
+        return fail(SPIIR_EINVAL, "tile must be a multiple of steps_per_reduce in [steps_per_reduce, 8192]");
+    int64_t fmax = 0;
+    for (int t = 0; t < b->T; ++t) fmax = std::max(fmax, b->offsets[t + 1] - b->offsets[t]);
+    if (fmax > (int64_t)filters_per_lane * lanes_per_block)
+        return fail(SPIIR_EUNSUPPORTED, "a template has %lld filters, more than %d lanes x %d", (long long)fmax,
+                    lanes_per_block, filters_per_lane);
+    size_t nb = 0;
+    SPIIR_TRY(spiir_bank_state_bytes(b, &nb));
+    std::vector<char> saved(nb);
+    SPIIR_TRY(spiir_bank_get_state(b, saved.data(), nb));
+    const int oS = b->S, oNL = b->NL, oR = b->R, oT = b->c_tile;
+    b->S = filters_per_lane;
+    b->NL = lanes_per_block;
+    b->R = steps_per_reduce;
+    b->c_tile = tile;
+    int rc = bank_smem_bytes(b) <= (size_t)kBankMaxSmem ? SPIIR_OK
+                                                         : fail(SPIIR_EUNSUPPORTED, "shape needs too much shared memory");
+    if (rc == SPIIR_OK) {
+        bank_free_packed(b);
+        rc = bank_pack(b);
+        if (rc == SPIIR_OK) rc = bank_alloc_device(b);
+        if (rc == SPIIR_OK) rc = spiir_bank_set_state(b, saved.data(), nb);
+        if (rc != SPIIR_OK) {
+            // restore the previous shape so that the bank stays usable
+            const std::string msg = [] { char m[512]; spiir_last_error(m, sizeof m); return std::string(m); }();
+            bank_free_packed(b);
+            b->S = oS; b->NL = oNL; b->R = oR; b->c_tile = oT;
+            if (bank_pack(b) == SPIIR_OK && bank_alloc_device(b) == SPIIR_OK) spiir_bank_set_state(b, saved.data(), nb);
+            return fail(rc, "%s", msg.c_str());
+        }
+    } else {
+        b->S = oS; b->NL = oNL; b->R = oR; b->c_tile = oT;
+    }
+    return rc;
+}
+
+extern "C" int spiir_bank_get_shape(spiir_bank_t b, int *filters_per_lane, int *lanes_per_block,
+                                    int *steps_per_reduce, int *tile) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (filters_per_lane) *filters_per_lane = b->S;
+    if (lanes_per_block) *lanes_per_block = b->NL;
+    if (steps_per_reduce) *steps_per_reduce = b->R;
+    if (tile) *tile = b->c_tile;
+    return SPIIR_OK;
 }

@@ -7,10 +7,7 @@
 
 namespace spiir {
 
-constexpr int kBankLanes = 256;                // threads (lanes) per block
-constexpr int kBankWarps = kBankLanes / 32;
-constexpr int kBankSteps = 32;                 // time steps per reduction block (R)
-constexpr int kBankTile = 1024;                // time steps per staged strain window
+constexpr int kBankTile = 1024;                // default time steps per staged strain window
 constexpr int kBankMaxSmem = 227 * 1024;       // dynamic shared memory limit per block
 constexpr int kBankMaxDelay = 32768;           // largest delay whose window fits
 
@@ -43,7 +40,9 @@ struct spiir_bank_s {
     int64_t F = 0;
     int32_t dmax = 0;
     int D_pad = 0;
-    int S = 8;
+    int S = 8;        // filters per lane
+    int NL = 256;     // lanes (threads) per block
+    int R = 32;       // time steps per reduction block
     int c_tile = 1024;
     int n_cta = 0;
     std::vector<int64_t> offsets;
@@ -68,6 +67,7 @@ struct spiir_bank_s {
 };
 
 namespace spiir {
+size_t bank_smem_bytes(const spiir_bank_s *b);
 int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int64_t n, float2 *z,
                 int64_t zpitch, cudaStream_t stream);
 }

@@ -13,6 +13,7 @@
 // attains it.  The null stream is evaluated once per sample at the winning pixel.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "coherent.cuh"
@@ -116,26 +117,269 @@ __global__ void __launch_bounds__(kCohThreads) k_coherent(const __grid_constant_
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Grouped scan for 2 and 3 detectors.
+//
+// For N_d = 3 the signal plane and the unit null vector n(p) complete each other
+// (U_s U_s^T + n n^T = I), so rho_C^2 = |w|^2 - |n.w|^2 and the null stream at p is
+// |n.w|^2 (App. A, Eq. (null_def)).  For N_d = 2 rho_C^2 = |w|^2 and the null is 0.
+// Pixels are visited sorted by (Delta_0, Delta_1, Delta_2), grouped by Delta_0, so the SNR of
+// detector 0 and its power are loaded once per group.  The SNR tile is kept in shared memory as
+// separate real and imaginary planes, each twice (shifted by one sample), so a thread loads
+// the pair (z[k + off], z[k + 1 + off]) for any offset with one aligned 8-byte access and
+// evaluates two samples with packed f32x2 arithmetic.  The inner loop keeps only a running
+// maximum per group; after all groups, each sample rescans its winning group with the same
+// arithmetic in scalar form to find the lowest pixel index that attains the maximum (a full
+// rescan if two groups tie exactly).
+
+__device__ __forceinline__ u64 lds64(const float *p) { return *reinterpret_cast<const u64 *>(p); }
+
+template <int ND>
+__device__ __forceinline__ void stat_pair(const float *pl, int W, int i0, int i1, int i2, u64 s0, u64 w0r, u64 w0i,
+                                          float n0, float n1, float n2, int k, u64 &v, u64 &t) {
+    const u64 w1r = lds64(pl + i1 + k), w1i = lds64(pl + i1 + 2 * W + k);
+    u64 S = fma2(w1i, w1i, fma2(w1r, w1r, s0));
+    if (ND == 3) {
+        const u64 w2r = lds64(pl + i2 + k), w2i = lds64(pl + i2 + 2 * W + k);
+        const u64 N0 = pack2(n0, n0), N1 = pack2(n1, n1), N2 = pack2(n2, n2);
+        const u64 nr = fma2(N2, w2r, fma2(N1, w1r, mul2(N0, w0r)));
+        const u64 ni = fma2(N2, w2i, fma2(N1, w1i, mul2(N0, w0i)));
+        S = fma2(w2i, w2i, fma2(w2r, w2r, S));
+        t = fma2(ni, ni, mul2(nr, nr));
+        v = fma2(t, pack2(-1.f, -1.f), S);
+    } else {
+        t = 0;
+        v = S;
+    }
+}
+
+// scalar form of stat_pair for one sample: the same IEEE operations in the same order
+template <int ND>
+__device__ __forceinline__ void stat_one(const float *pl, int W, int i0, int i1, int i2, float n0, float n1, float n2,
+                                         int k, float &v, float &t) {
+    const float w0r = pl[i0 + k], w0i = pl[i0 + 2 * W + k];
+    const float w1r = pl[i1 + k], w1i = pl[i1 + 2 * W + k];
+    const float s0 = __fmaf_rn(w0r, w0r, __fmul_rn(w0i, w0i));
+    float S = __fmaf_rn(w1i, w1i, __fmaf_rn(w1r, w1r, s0));
+    if (ND == 3) {
+        const float w2r = pl[i2 + k], w2i = pl[i2 + 2 * W + k];
+        const float nr = __fmaf_rn(n2, w2r, __fmaf_rn(n1, w1r, __fmul_rn(n0, w0r)));
+        const float ni = __fmaf_rn(n2, w2i, __fmaf_rn(n1, w1i, __fmul_rn(n0, w0i)));
+        S = __fmaf_rn(w2i, w2i, __fmaf_rn(w2r, w2r, S));
+        t = __fmaf_rn(ni, ni, __fmul_rn(nr, nr));
+        v = __fmaf_rn(t, -1.f, S);
+    } else {
+        t = 0.f;
+        v = S;
+    }
+}
+
+template <int ND, bool TAB_SMEM, bool MAP, int TPB, int PPT>
+__global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant__ GroupedArgs a) {
+    constexpr int KT = 2 * TPB * PPT;   // output samples per work item
+    constexpr int NQ = 2 * PPT;         // samples per thread
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const int P = a.n_pix, G = a.n_grp, W = a.W;
+    size_t off = 0;
+    const float4 *ent;
+    if (TAB_SMEM) {
+        float4 *e = reinterpret_cast<float4 *>(smem);
+        for (int i = tid; i < P; i += TPB) e[i] = a.ent[i];
+        ent = e;
+        off = (size_t)P * sizeof(float4);
+    } else {
+        ent = a.ent;
+    }
+    uint16_t *orig = reinterpret_cast<uint16_t *>(smem + off);
+    for (int i = tid; i < P; i += TPB) orig[i] = a.orig[i];
+    off += ((size_t)P * sizeof(uint16_t) + 15) / 16 * 16;
+    int4 *grp = reinterpret_cast<int4 *>(smem + off);
+    for (int i = tid; i < G; i += TPB) grp[i] = a.grp[i];
+    off += (size_t)G * sizeof(int4);
+    float *pl = reinterpret_cast<float *>(smem + off);
+
+    const int ntiles = (int)((a.n + KT - 1) / KT);
+    const int64_t n_items = (int64_t)a.n_templates * ntiles;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int t = (int)(item / ntiles);
+        const int64_t k0 = (item % ntiles) * (int64_t)KT;
+        __syncthreads();
+        for (int I = 0; I < ND; ++I) {
+            const float2 *row = a.snr + ((int64_t)t * ND + I) * a.pitch + k0;
+            const int64_t lim = a.n + 2 * a.H - k0;
+            float *b = pl + I * 4 * W;
+            for (int j = tid; j < W; j += TPB) {
+                const float2 v = (j < lim) ? row[j] : make_float2(0.f, 0.f);
+                b[j] = v.x;
+                b[2 * W + j] = v.y;
+                if (j > 0) {
+                    b[W + j - 1] = v.x;
+                    b[3 * W + j - 1] = v.y;
+                } else {
+                    b[2 * W - 1] = 0.f;
+                    b[4 * W - 1] = 0.f;
+                }
+            }
+        }
+        __syncthreads();
+        float best[NQ];
+        int bg[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            best[q] = -INFINITY;
+            bg[q] = 0;
+        }
+        unsigned tie = 0;
+        for (int g = 0; g < G; ++g) {
+            const int4 gr = grp[g];
+            u64 w0r[PPT], w0i[PPT], s0[PPT];
+            float gm[NQ];
+#pragma unroll
+            for (int h = 0; h < PPT; ++h) {
+                const int k = 2 * tid + h * 2 * TPB;
+                w0r[h] = lds64(pl + gr.x + k);
+                w0i[h] = lds64(pl + gr.x + 2 * W + k);
+                s0[h] = fma2(w0r[h], w0r[h], mul2(w0i[h], w0i[h]));
+                gm[2 * h] = -INFINITY;
+                gm[2 * h + 1] = -INFINITY;
+            }
+#pragma unroll 2
+            for (int p = gr.y; p < gr.z; ++p) {
+                const float4 e = ent[p];
+                const unsigned o = __float_as_uint(e.w);
+                const int i1 = (int)(o & 0xFFFFu), i2 = (int)(o >> 16);
+#pragma unroll
+                for (int h = 0; h < PPT; ++h) {
+                    const int k = 2 * tid + h * 2 * TPB;
+                    u64 v, tt;
+                    stat_pair<ND>(pl, W, gr.x, i1, i2, s0[h], w0r[h], w0i[h], e.x, e.y, e.z, k, v, tt);
+                    const float2 f = unpack2(v);
+                    if (MAP) {
+                        float *mrow = a.skymap + ((int64_t)t * P + orig[p]) * a.n + k0;
+                        if (k0 + k < a.n) mrow[k] = f.x;
+                        if (k0 + k + 1 < a.n) mrow[k + 1] = f.y;
+                    }
+                    gm[2 * h] = fmaxf(gm[2 * h], f.x);
+                    gm[2 * h + 1] = fmaxf(gm[2 * h + 1], f.y);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if (gm[q] > best[q]) {
+                    best[q] = gm[q];
+                    bg[q] = g;
+                    tie &= ~(1u << q);
+                } else if (gm[q] == best[q]) {
+                    tie |= 1u << q;
+                }
+            }
+        }
+        // resolve the argmax (lowest original pixel index among equal maxima) and the null
+        for (int q = 0; q < NQ; ++q) {
+            const int k = 2 * tid + (q >> 1) * 2 * TPB + (q & 1);
+            if (k0 + k >= a.n) continue;
+            int arg = 0x7fffffff;
+            float nul = 0.f;
+            int g_lo = bg[q], g_hi = bg[q] + 1;
+            if (tie >> q & 1u) {
+                // equal maxima in different groups: pixel 0, the lowest index, wins if it
+                // attains the maximum (the all-zero window); otherwise rescan every group
+                const float4 e = ent[a.q0];
+                const unsigned o = __float_as_uint(e.w);
+                float v, tt;
+                stat_one<ND>(pl, W, grp[a.g0].x, (int)(o & 0xFFFFu), (int)(o >> 16), e.x, e.y, e.z, k, v, tt);
+                if (v == best[q]) {
+                    arg = 0;
+                    nul = tt;
+                    g_hi = g_lo;
+                } else {
+                    g_lo = 0;
+                    g_hi = G;
+                }
+            }
+            for (int g = g_lo; g < g_hi; ++g) {
+                const int4 gr = grp[g];
+                for (int p = gr.y; p < gr.z; ++p) {
+                    const float4 e = ent[p];
+                    const unsigned o = __float_as_uint(e.w);
+                    float v, tt;
+                    stat_one<ND>(pl, W, gr.x, (int)(o & 0xFFFFu), (int)(o >> 16), e.x, e.y, e.z, k, v, tt);
+                    const int op = orig[p];
+                    if (v == best[q] && op < arg) {
+                        arg = op;
+                        nul = tt;
+                    }
+                }
+            }
+            if (arg == 0x7fffffff) arg = 0;  // only when every statistic is NaN
+            const int64_t o = (int64_t)t * a.n + k0 + k;
+            a.max_stat[o] = best[q];
+            a.argmax[o] = arg;
+            a.null_stat[o] = nul;
+        }
+    }
+}
+
+template <int ND, bool TAB_SMEM, bool MAP, int TPB, int PPT>
+static int launch_grouped(const GroupedArgs &a, size_t smem, cudaStream_t stream) {
+    auto kern = k_coherent_grouped<ND, TAB_SMEM, MAP, TPB, PPT>;
+    static int blocks_per_sm = -1;
+    static size_t smem_seen = 0;
+    if (blocks_per_sm < 0 || smem_seen != smem) {
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        int nb = 0;
+        SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TPB, smem));
+        blocks_per_sm = std::max(1, nb);
+        smem_seen = smem;
+    }
+    int dev = 0, n_sm = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int KT = 2 * TPB * PPT;
+    const int64_t items = (int64_t)a.n_templates * ((a.n + KT - 1) / KT);
+    const int grid = (int)std::min<int64_t>(items, (int64_t)n_sm * blocks_per_sm);
+    kern<<<grid, TPB, smem, stream>>>(a);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+template <int ND, int TPB, int PPT>
+static int dispatch_grouped3(const GroupedArgs &a, bool tab_smem, bool map, size_t smem, cudaStream_t s) {
+    if (tab_smem)
+        return map ? launch_grouped<ND, true, true, TPB, PPT>(a, smem, s)
+                   : launch_grouped<ND, true, false, TPB, PPT>(a, smem, s);
+    return map ? launch_grouped<ND, false, true, TPB, PPT>(a, smem, s)
+               : launch_grouped<ND, false, false, TPB, PPT>(a, smem, s);
+}
+
+template <int ND>
+static int dispatch_grouped(const GroupedArgs &a, int tpb, int ppt, bool tab_smem, bool map, size_t smem,
+                            cudaStream_t s) {
+    if (tpb == 512 && ppt == 1) return dispatch_grouped3<ND, 512, 1>(a, tab_smem, map, smem, s);
+    if (tpb == 256 && ppt == 1) return dispatch_grouped3<ND, 256, 1>(a, tab_smem, map, smem, s);
+    if (tpb == 512 && ppt == 2) return dispatch_grouped3<ND, 512, 2>(a, tab_smem, map, smem, s);
+    return dispatch_grouped3<ND, 256, 2>(a, tab_smem, map, smem, s);
+}
+
 template <int ND, bool SMEM_TAB, bool MAP>
 static int launch_coh(const CohArgs &a, size_t smem, cudaStream_t stream) {
     auto kern = k_coherent<ND, SMEM_TAB, MAP>;
-    static int blocks_per_sm[2] = {-1, -1};
-    static size_t smem_seen[2] = {0, 0};
-    int dev = 0;
-    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
-    const int slot = 0;
-    if (blocks_per_sm[slot] < 0 || smem_seen[slot] != smem) {
+    static int blocks_per_sm = -1;
+    static size_t smem_seen = 0;
+    if (blocks_per_sm < 0 || smem_seen != smem) {
         SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         int nb = 0;
         SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kCohThreads, smem));
-        blocks_per_sm[slot] = std::max(1, nb);
-        smem_seen[slot] = smem;
+        blocks_per_sm = std::max(1, nb);
+        smem_seen = smem;
     }
-    int n_sm = 0;
+    int dev = 0, n_sm = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int KT = kCohThreads * kCohQ;
     const int64_t items = (int64_t)a.n_templates * ((a.n + KT - 1) / KT);
-    const int grid = (int)std::min<int64_t>(items, (int64_t)n_sm * blocks_per_sm[slot]);
+    const int grid = (int)std::min<int64_t>(items, (int64_t)n_sm * blocks_per_sm);
     kern<<<grid, kCohThreads, smem, stream>>>(a);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
@@ -149,6 +393,36 @@ static int dispatch_nd(const CohArgs &a, bool smem_tab, bool map, size_t smem, c
 
 int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int64_t n, float *max_stat,
                   int32_t *argmax, float *null_stat, float *skymap, cudaStream_t stream) {
+    if (sky->grouped) {
+        GroupedArgs g{};
+        g.snr = snr;
+        g.pitch = pitch;
+        g.n_templates = T;
+        g.n = n;
+        g.H = sky->halo;
+        g.n_pix = sky->n_pix;
+        g.ent = sky->g_ent;
+        g.orig = sky->g_orig;
+        g.grp = sky->g_grp;
+        g.n_grp = sky->n_grp;
+        g.q0 = sky->g_q0;
+        g.g0 = sky->g_g0;
+        g.W = sky->g_W;
+        g.max_stat = max_stat;
+        g.argmax = argmax;
+        g.null_stat = null_stat;
+        g.skymap = skymap;
+        const int tpb = sky->scan_threads, ppt = sky->scan_pairs;
+        g.W = 2 * tpb * ppt + 2 * sky->halo + 2;
+        if (g.W != sky->g_W) return fail(SPIIR_EINVAL, "internal: plane length mismatch");
+        const size_t fixed = ((size_t)sky->n_pix * sizeof(uint16_t) + 15) / 16 * 16 + (size_t)sky->n_grp * sizeof(int4) +
+                             (size_t)sky->n_det * 4 * g.W * sizeof(float);
+        const size_t tab = (size_t)sky->n_pix * sizeof(float4);
+        const bool tab_smem = fixed + tab <= (size_t)kCohSmemTableLimit;
+        const size_t smem = fixed + (tab_smem ? tab : 0);
+        if (sky->n_det == 3) return dispatch_grouped<3>(g, tpb, ppt, tab_smem, skymap != nullptr, smem, stream);
+        return dispatch_grouped<2>(g, tpb, ppt, tab_smem, skymap != nullptr, smem, stream);
+    }
     CohArgs a{};
     a.snr = snr;
     a.pitch = pitch;
@@ -200,7 +474,82 @@ static void sky_free(spiir_sky_s *s) {
     if (!s) return;
     dev_free(s->table);
     dev_free(s->u_null);
+    dev_free(s->g_ent);
+    dev_free(s->g_orig);
+    dev_free(s->g_grp);
     delete s;
+}
+
+// Grouped tables for 2 or 3 detectors, when the supplied U is an orthonormal basis whose
+// signal plane has rank 2 (the null-vector form needs it); otherwise the general kernel runs.
+static int build_grouped(spiir_sky_s *s, const int32_t *delays, const float *u_sig, const float *u_null) {
+    const int nd = s->n_det, P = s->n_pix, H = s->halo;
+    if (nd != 2 && nd != 3) return SPIIR_OK;
+    if (P > 65535) return SPIIR_OK;
+    for (int p = 0; p < P; ++p) {
+        double U[3][3] = {{0}};
+        for (int I = 0; I < nd; ++I) {
+            U[I][0] = u_sig[((int64_t)p * nd + I) * 2];
+            U[I][1] = u_sig[((int64_t)p * nd + I) * 2 + 1];
+            if (nd == 3) U[I][2] = u_null[(int64_t)p * nd + I];
+        }
+        for (int i = 0; i < nd; ++i)
+            for (int j = 0; j < nd; ++j) {
+                double d = 0;
+                for (int I = 0; I < nd; ++I) d += U[I][i] * U[I][j];
+                if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-5) return SPIIR_OK;
+            }
+    }
+    const int W = 2 * s->scan_threads * s->scan_pairs + 2 * H + 2;
+    if (nd * 4 * W > 65535) return SPIIR_OK;
+    std::vector<int> order(P);
+    for (int p = 0; p < P; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        for (int I = 0; I < nd; ++I) {
+            const int dx = delays[(int64_t)x * nd + I], dy = delays[(int64_t)y * nd + I];
+            if (dx != dy) return dx < dy;
+        }
+        return x < y;
+    });
+    auto plane_index = [&](int I, int delay) {
+        const int o = H + delay, par = o & 1;
+        return I * 4 * W + par * W + (o - par);
+    };
+    std::vector<float4> ent(P);
+    std::vector<uint16_t> orig(P);
+    std::vector<int4> grp;
+    for (int q = 0; q < P; ++q) {
+        const int p = order[q];
+        const int d0 = delays[(int64_t)p * nd];
+        if (grp.empty() || grp.back().w != d0) {
+            if (!grp.empty()) grp.back().z = q;
+            grp.push_back(make_int4(plane_index(0, d0), q, P, d0));
+        }
+        const unsigned i1 = (unsigned)plane_index(1, delays[(int64_t)p * nd + 1]);
+        const unsigned i2 = nd == 3 ? (unsigned)plane_index(2, delays[(int64_t)p * nd + 2]) : 0u;
+        float4 e;
+        e.x = nd == 3 ? u_null[(int64_t)p * nd + 0] : 0.f;
+        e.y = nd == 3 ? u_null[(int64_t)p * nd + 1] : 0.f;
+        e.z = nd == 3 ? u_null[(int64_t)p * nd + 2] : 0.f;
+        unsigned packed = i1 | (i2 << 16);
+        memcpy(&e.w, &packed, 4);
+        ent[q] = e;
+        orig[q] = (uint16_t)p;
+        if (p == 0) {
+            s->g_q0 = q;
+            s->g_g0 = (int)grp.size() - 1;
+        }
+    }
+    SPIIR_TRY(dev_alloc((void **)&s->g_ent, sizeof(float4) * P, "grouped sky table"));
+    SPIIR_TRY(dev_alloc((void **)&s->g_orig, sizeof(uint16_t) * P, "pixel order"));
+    SPIIR_TRY(dev_alloc((void **)&s->g_grp, sizeof(int4) * grp.size(), "pixel groups"));
+    SPIIR_CUDA_TRY(cudaMemcpy(s->g_ent, ent.data(), sizeof(float4) * P, cudaMemcpyHostToDevice));
+    SPIIR_CUDA_TRY(cudaMemcpy(s->g_orig, orig.data(), sizeof(uint16_t) * P, cudaMemcpyHostToDevice));
+    SPIIR_CUDA_TRY(cudaMemcpy(s->g_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice));
+    s->n_grp = (int)grp.size();
+    s->g_W = W;
+    s->grouped = true;
+    return SPIIR_OK;
 }
 
 extern "C" int spiir_sky_create(int n_det, int n_pix, const int32_t *delays, const float *u_sig,
@@ -242,6 +591,12 @@ extern "C" int spiir_sky_create(int n_det, int n_pix, const int32_t *delays, con
         if (rc == SPIIR_OK && cudaMemcpy(s->u_null, u_null, nb, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = fail(SPIIR_ECUDA, "copy of the null-space table failed");
     }
+    if (rc == SPIIR_OK) {
+        s->h_delays.assign(delays, delays + (size_t)n_pix * n_det);
+        s->h_usig.assign(u_sig, u_sig + (size_t)n_pix * n_det * 2);
+        if (n_det > 2) s->h_unull.assign(u_null, u_null + (size_t)n_pix * n_det * (n_det - 2));
+        rc = build_grouped(s, delays, u_sig, u_null);
+    }
     if (rc != SPIIR_OK) {
         sky_free(s);
         return rc;
@@ -272,4 +627,42 @@ extern "C" int spiir_coherent_scan(spiir_sky_t s, const float *snr, int64_t pitc
     if (((uintptr_t)snr) % 8 != 0) return fail(SPIIR_EINVAL, "snr pointer is not 8-byte aligned");
     return coherent_scan(s, reinterpret_cast<const float2 *>(snr), pitch, T, n, max_stat, argmax, null_stat,
                          skymap, (cudaStream_t)stream);
+}
+
+extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs) {
+    clear_error();
+    if (!s) return fail(SPIIR_EINVAL, "sky is NULL");
+    if ((threads != 256 && threads != 512) || (pairs != 1 && pairs != 2))
+        return fail(SPIIR_EINVAL, "threads must be 256 or 512 and pairs 1 or 2");
+    if (!s->grouped) {
+        s->scan_threads = threads;
+        s->scan_pairs = pairs;
+        return SPIIR_OK;
+    }
+    const int ot = s->scan_threads, op = s->scan_pairs;
+    SPIIR_CUDA_TRY(cudaDeviceSynchronize());
+    dev_free(s->g_ent);
+    dev_free(s->g_orig);
+    dev_free(s->g_grp);
+    s->g_ent = nullptr;
+    s->g_orig = nullptr;
+    s->g_grp = nullptr;
+    s->grouped = false;
+    s->scan_threads = threads;
+    s->scan_pairs = pairs;
+    int rc = build_grouped(s, s->h_delays.data(), s->h_usig.data(), s->n_det > 2 ? s->h_unull.data() : nullptr);
+    if (rc != SPIIR_OK || !s->grouped) {
+        s->scan_threads = ot;
+        s->scan_pairs = op;
+        build_grouped(s, s->h_delays.data(), s->h_usig.data(), s->n_det > 2 ? s->h_unull.data() : nullptr);
+    }
+    return rc;
+}
+
+extern "C" int spiir_sky_get_scan_shape(spiir_sky_t s, int *threads, int *pairs, int *grouped) {
+    if (!s) return fail(SPIIR_EINVAL, "sky is NULL");
+    if (threads) *threads = s->scan_threads;
+    if (pairs) *pairs = s->scan_pairs;
+    if (grouped) *grouped = s->grouped ? 1 : 0;
+    return SPIIR_OK;
 }

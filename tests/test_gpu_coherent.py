@@ -131,3 +131,50 @@ def test_streaming_pipeline_matches_oracle(host):
     zp = np.concatenate([np.zeros((bank.n_templates, 3, 2 * H)), z_or], axis=2)
     ms_or, am_or, nl_or, sm_or = oracle.coherent(zp, G, d_or, H, N, skymap=True)
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+
+
+@pytest.mark.parametrize("shape", [(256, 1), (256, 2), (512, 1), (512, 2)])
+@pytest.mark.parametrize("n_det", [2, 3])
+def test_every_scan_shape_matches_oracle(shape, n_det):
+    sky, G, d_or = _sky(1, n_det, 8, (0.5, 2.0))
+    sky.set_scan_shape(*shape)
+    assert sky.get_scan_shape() == shape + (1,)
+    H = sky.halo
+    n = 2500
+    z = synth.complex_gaussian_snr(1, (3, n_det, n + 2 * H), sub=11)
+    ms, am, nl, _ = _scan(sky, z, n)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    ms2, am2, nl2, mp = _scan(sky, z, n, skymap=True)
+    np.testing.assert_array_equal(ms2, ms)
+    np.testing.assert_array_equal(am2, am)
+    mp = np.transpose(mp, (0, 2, 1))
+    assert np.all(np.abs(mp - sm_or) <= 1e-4 * sm_or.max(axis=-1, keepdims=True))
+
+
+def test_general_kernel_for_non_orthonormal_tables():
+    import paper_2011_06787_b300 as sp
+    sky, G, d_or = _sky(1, 3, 4, (0.5, 2.0))
+    det = synth.detectors(1, 3)
+    sigma = synth.noise_weights(1, 3, 0.5, 2.0)
+    d, us, un = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 4, 2048.0)
+    un2 = un * 1.5  # not a unit null vector: the grouped null-vector form does not apply
+    sky2 = sp.Sky(d, us, un2)
+    assert sky2.get_scan_shape()[2] == 0
+    H = sky2.halo
+    z = synth.complex_gaussian_snr(1, (2, 3, 600 + 2 * H), sub=12)
+    ms, am, nl, _ = _scan(sky2, z, 600)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, 600, skymap=True)
+    # the statistic uses U_s only; the null uses the (scaled) table as given
+    assert_coherent_close(ms, am, nl / 2.25, ms_or, am_or, nl_or, sm_or)
+
+
+def test_all_zero_window_ties_resolve_to_pixel_zero():
+    sky, G, d_or = _sky(1, 3, 16, (0.5, 2.0))
+    H = sky.halo
+    z = np.zeros((2, 3, 1500 + 2 * H), np.complex64)
+    z[1, :, 700:] = synth.complex_gaussian_snr(1, (3, z.shape[2] - 700), sub=13)
+    ms, am, nl, _ = _scan(sky, z, 1500)
+    assert np.all(ms[0] == 0) and np.all(am[0] == 0) and np.all(nl[0] == 0)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, 1500, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)

@@ -159,3 +159,36 @@ def test_online_full_size_sampled_templates():
     z_or, _, _ = oracle.filter_bank(x, sub.offsets, sub.a1, sub.b0, sub.delay)
     assert_snr_close(z[pick], z_or)
     assert np.isfinite(z).all()
+
+
+@pytest.mark.parametrize("shape", [(4, 128, 16, 512), (8, 128, 32, 1024), (8, 256, 16, 2048), (16, 256, 32, 1024),
+                                   (16, 128, 16, 64)])
+def test_every_launch_shape_matches_oracle(shape):
+    torch = _torch()
+    import paper_2011_06787_b300 as sp
+    g = synth.rng(0, "misc", 6)
+    bank = synth.random_bank(g, [3, 200, 500, 57, 1, 440], d_max=3000)
+    x = synth.white_noise(0, 3, 3100, sub=10)
+    b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+    # change the shape in the middle of the stream: the state must carry over
+    z1 = torch.zeros((6, 3, 1000), dtype=torch.complex64, device="cuda")
+    b.filter_chunk(torch.from_numpy(np.ascontiguousarray(x[:, :1000])).cuda(), z1)
+    b.set_shape(*shape)
+    assert b.get_shape() == shape
+    z2 = torch.zeros((6, 3, 2100), dtype=torch.complex64, device="cuda")
+    b.filter_chunk(torch.from_numpy(np.ascontiguousarray(x[:, 1000:])).cuda(), z2)
+    z = np.concatenate([z1.cpu().numpy(), z2.cpu().numpy()], axis=2)
+    z_or, _, _ = oracle.filter_bank(x, bank.offsets, bank.a1, bank.b0, bank.delay)
+    assert_snr_close(z, z_or)
+
+
+def test_shape_rejections_keep_the_bank_usable():
+    import paper_2011_06787_b300 as sp
+    g = synth.rng(0, "misc", 7)
+    bank = synth.random_bank(g, [700], d_max=100)
+    b = sp.Bank(1, bank.offsets, bank.a1, bank.b0, bank.delay)
+    with pytest.raises(sp.SpiirError):
+        b.set_shape(4, 128, 16, 1024)   # 700 filters > 4 x 128
+    with pytest.raises(sp.SpiirError):
+        b.set_shape(8, 100, 16, 1024)
+    assert b.get_shape() == (8, 256, 32, 1024)  # 700 filters need 256 lanes of 8
