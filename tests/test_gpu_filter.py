@@ -191,4 +191,4 @@ def test_shape_rejections_keep_the_bank_usable():
         b.set_shape(4, 128, 16, 1024)   # 700 filters > 4 x 128
     with pytest.raises(sp.SpiirError):
         b.set_shape(8, 100, 16, 1024)
-    assert b.get_shape() == (8, 256, 32, 1024)  # 700 filters need 256 lanes of 8
+    assert b.get_shape() == (8, 128, 32, 1024)  # the default for templates of up to 1024 filters
