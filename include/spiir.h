@@ -121,6 +121,29 @@ int spiir_bank_get_shape(spiir_bank_t bank, int *filters_per_lane, int *lanes_pe
 int spiir_filter_chunk(spiir_bank_t bank, const float *strain_dev, int64_t strain_pitch,
                        int64_t n, float *snr_dev, int64_t snr_pitch, void *stream);
 
+/* Filter one segment that starts a stream without allocating anything -- for callers that
+ * cannot call cudaMalloc (for example code running where device allocation is forbidden or
+ * would stall, or under an allocator that owns all device memory).  The paper has no
+ * counterpart; this is a packaging of the filter bank above.
+ * Computes what spiir_bank_create followed by one spiir_filter_chunk computes on a new bank
+ * (zero IIR states, zero strain history), with the same kernel.  Coefficient arguments are
+ * host arrays as in spiir_bank_create; strain_dev and snr_dev are as in spiir_filter_chunk.
+ * All scratch (copied coefficients, packed layout, block tables, IIR states, strain window)
+ * lives in one file-scope device array of 32 MiB that every GPU which loads the library
+ * holds until the process exits; no cudaMalloc, cudaFree or other allocating routine is
+ * called.  The first call on a device looks up that array's device address with the device
+ * current (cudaGetSymbolAddress), so make the first call before any stream capture.
+ * Every call reuses the same array: calls whose GPU work can overlap (different streams
+ * without ordering) race and give wrong results; order them on one stream.  The coefficient
+ * copies read the host arrays before the call returns; the rest is enqueued on stream.
+ * Limits: n_det <= 4, n_templates <= 4096, n_filters <= 131072, n <= 65536, delays <= 8192,
+ * and the packed problem must fit in the array; otherwise SPIIR_EUNSUPPORTED with the limit
+ * in spiir_last_error().  Invalid values: SPIIR_EINVAL as in spiir_bank_create. */
+int spiir_filter_static(int n_det, int n_templates, const int64_t *filter_offsets_host,
+                        const float *a1_host, const float *b0_host, const int32_t *delay_host,
+                        const float *strain_dev, int64_t strain_pitch, int64_t n, float *snr_dev,
+                        int64_t snr_pitch, void *stream);
+
 /* ------------------------------------------------------------------------------------
  * Sky tables -- Sec. II.C.1 (HEALPix tiling, U and time-offset look-up tables) and
  * App. A Eqs. (strain_sngl), (svd).

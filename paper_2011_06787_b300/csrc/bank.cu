@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -712,4 +713,245 @@ extern "C" int spiir_bank_get_shape(spiir_bank_t b, int *filters_per_lane, int *
     if (steps_per_reduce) *steps_per_reduce = b->R;
     if (tile) *tile = b->c_tile;
     return SPIIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Filter bank without any allocation (spiir_filter_static).
+//
+// Some callers cannot allocate device memory: code that runs where cudaMalloc is not
+// allowed or would stall (inside a real-time loop, under an allocator that owns all device
+// memory, or in a process that must not grow its footprint after start-up).  This entry
+// point runs the same filter-bank kernel as spiir_filter_chunk on one segment that starts a
+// stream (zero IIR states, zero strain history), with every piece of scratch -- the copied
+// coefficients, their packed layout, the block tables, the IIR states, the strain window
+// and a status word -- carved out of one file-scope device array of fixed size.  The array
+// exists on every GPU that loads the library, for the life of the process.  All calls share
+// it, so calls whose GPU work overlaps (different streams, no ordering) race and corrupt
+// each other's results.
+
+namespace spiir {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+static std::mutex g_static_mu;
+static void *g_static_addr[64];
+
+// Device address of the scratch array on the current device.  Looked up once per device,
+// on the first call made with that device current.
+static int static_scratch_address(unsigned char **out) {
+    int dev = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SPIIR_EUNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(SPIIR_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        g_static_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_static_addr[dev]);
+    return SPIIR_OK;
+}
+
+// Block layout in template order: template t takes max(1, ceil(F_t / S)) lanes; a block is
+// closed when the next template does not fit.  One thread; T is small.
+__global__ void k_static_layout(const int64_t *off, int T, int S, int NL, int *cta_of_t, int *lane0_of_t,
+                                int4 *segs, int *seg_off, int *wfirst, int *active) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int NW = NL / 32;
+    int c = 0, used = 0;
+    seg_off[0] = 0;
+    for (int t = 0; t < T; ++t) {
+        const int64_t f = off[t + 1] - off[t];
+        const int L = (int)max((int64_t)1, (f + S - 1) / S);
+        if (used + L > NL) {
+            active[c] = used;
+            ++c;
+            used = 0;
+            seg_off[c] = t;
+        }
+        cta_of_t[t] = c;
+        lane0_of_t[t] = used;
+        segs[t] = make_int4(t, used, used + L, 0);
+        used += L;
+    }
+    active[c] = used;
+    seg_off[c + 1] = T;
+    for (int cc = 0; cc <= c; ++cc) {
+        const int s0 = seg_off[cc], ns = seg_off[cc + 1] - s0;
+        for (int w = 0; w < NW; ++w) {
+            int first = -1;
+            for (int sg = 0; sg < ns; ++sg) {
+                const int4 g = segs[s0 + sg];
+                if (g.z > w * 32 && g.y < w * 32 + 32) {
+                    first = sg;
+                    break;
+                }
+            }
+            wfirst[cc * NW + w] = first;
+        }
+    }
+}
+
+// Scatter filter l of template t to lane lane0[t] + q / S, slot q % S (q = l - off[t]).
+__global__ void k_static_scatter(const int64_t *off, const float2 *a1, const float2 *b0, const int32_t *delay, int T,
+                                 int64_t F, int S, int NL, const int *cta_of_t, const int *lane0_of_t, float2 *are,
+                                 float2 *aim, float2 *bre, float2 *bim, int *dly) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= F) return;
+    int lo = 0, hi = T;  // last t with off[t] <= l
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (off[mid] <= l) lo = mid; else hi = mid;
+    }
+    const int t = lo;
+    const int64_t q = l - off[t];
+    const int lane = lane0_of_t[t] + (int)(q / S), s = (int)(q % S), c = cta_of_t[t];
+    const int NP = S / 2;
+    const int64_t pi = ((int64_t)c * NP + s / 2) * NL + lane;
+    float *ar = reinterpret_cast<float *>(&are[pi]) + (s & 1);
+    float *ai = reinterpret_cast<float *>(&aim[pi]) + (s & 1);
+    float *br = reinterpret_cast<float *>(&bre[pi]) + (s & 1);
+    float *bi = reinterpret_cast<float *>(&bim[pi]) + (s & 1);
+    *ar = a1[l].x;
+    *ai = a1[l].y;
+    *br = b0[l].x;
+    *bi = b0[l].y;
+    dly[((int64_t)c * S + s) * NL + lane] = delay[l];
+}
+
+}  // namespace spiir
+
+extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *off, const float *a1, const float *b0,
+                                   const int32_t *delay, const float *strain, int64_t strain_pitch, int64_t n,
+                                   float *snr, int64_t snr_pitch, void *stream) {
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    // host-side validation (reads the caller's host arrays only)
+    if (n_det < 1 || n_det > kStaticMaxDet) return fail(SPIIR_EINVAL, "n_det = %d outside [1, %d]", n_det, kStaticMaxDet);
+    if (n_templates < 1) return fail(SPIIR_EINVAL, "n_templates = %d < 1", n_templates);
+    if (!off || !strain || !snr) return fail(SPIIR_EINVAL, "NULL pointer");
+    if (off[0] != 0) return fail(SPIIR_EINVAL, "filter_offsets[0] must be 0");
+    if (n < 1 || strain_pitch < n || snr_pitch < n) return fail(SPIIR_EINVAL, "bad n or pitch");
+    if (((uintptr_t)snr) % 8 != 0) return fail(SPIIR_EINVAL, "snr pointer is not 8-byte aligned");
+    int64_t fmax = 0;
+    for (int t = 0; t < n_templates; ++t) {
+        if (off[t + 1] < off[t]) return fail(SPIIR_EINVAL, "filter_offsets decrease at template %d", t);
+        fmax = std::max(fmax, off[t + 1] - off[t]);
+    }
+    const int64_t F = off[n_templates];
+    if (F > 0 && (!a1 || !b0 || !delay)) return fail(SPIIR_EINVAL, "coefficient pointer is NULL");
+    if (n_templates > kStaticMaxTemplates || F > kStaticMaxFilters || n > kStaticMaxSamples)
+        return fail(SPIIR_EUNSUPPORTED,
+                    "static scratch limits: at most %d templates, %d filters, %d samples (got %d, %lld, %lld)",
+                    kStaticMaxTemplates, kStaticMaxFilters, kStaticMaxSamples, n_templates, (long long)F, (long long)n);
+    int32_t dmax = 0;
+    for (int64_t l = 0; l < F; ++l) {
+        const double ar = a1[2 * l], ai = a1[2 * l + 1], br = b0[2 * l], bi = b0[2 * l + 1];
+        if (!std::isfinite(ar) || !std::isfinite(ai) || !std::isfinite(br) || !std::isfinite(bi))
+            return fail(SPIIR_EINVAL, "filter %lld has a non-finite coefficient", (long long)l);
+        if (ar * ar + ai * ai >= 1.0) return fail(SPIIR_EINVAL, "filter %lld has |a1| >= 1 (unstable)", (long long)l);
+        if (delay[l] < 0 || delay[l] > kStaticMaxDelay)
+            return fail(SPIIR_EINVAL, "filter %lld has delay %d outside [0, %d]", (long long)l, delay[l], kStaticMaxDelay);
+        dmax = std::max(dmax, delay[l]);
+    }
+    // launch shape as the allocating path chooses it for a new bank
+    const int S = fmax > 2048 ? 16 : 8;
+    const int NL = fmax > 1024 ? 256 : 128;
+    const int R = 32, tile = kBankTile, NP = S / 2;
+    if (fmax > (int64_t)S * NL) return fail(SPIIR_EUNSUPPORTED, "a template has %lld filters", (long long)fmax);
+    int n_cta = 1, used = 0;
+    for (int t = 0; t < n_templates; ++t) {
+        const int L = (int)std::max<int64_t>(1, (off[t + 1] - off[t] + S - 1) / S);
+        if (used + L > NL) {
+            ++n_cta;
+            used = 0;
+        }
+        used += L;
+    }
+    const int D_pad = ((dmax + 3) / 4) * 4;
+    const int64_t xpitch = ((D_pad + n + 3) / 4) * 4 + 4;
+    // carve the scratch
+    size_t cur = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = cur;
+        cur = (cur + bytes + 255) / 256 * 256;
+        return at;
+    };
+    const int64_t npair = (int64_t)n_cta * NP * NL;
+    const size_t o_off = take(sizeof(int64_t) * (n_templates + 1));
+    const size_t o_a1 = take(sizeof(float2) * F), o_b0 = take(sizeof(float2) * F), o_d = take(sizeof(int32_t) * F);
+    const size_t o_pk = cur;
+    const size_t o_are = take(sizeof(float2) * npair), o_aim = take(sizeof(float2) * npair);
+    const size_t o_bre = take(sizeof(float2) * npair), o_bim = take(sizeof(float2) * npair);
+    const size_t o_dly = take(sizeof(int) * npair * 2);
+    const size_t o_st = take(sizeof(float4) * npair * n_det);
+    const size_t pk_bytes = cur - o_pk;
+    const size_t o_cta = take(sizeof(int) * n_templates), o_l0 = take(sizeof(int) * n_templates);
+    const size_t o_segs = take(sizeof(int4) * n_templates), o_so = take(sizeof(int) * (n_cta + 1));
+    const size_t o_wf = take(sizeof(int) * n_cta * (NL / 32)), o_act = take(sizeof(int) * n_cta);
+    const size_t o_x = take(sizeof(float) * xpitch * n_det);
+    const size_t o_status = take(sizeof(int));
+    if (cur > kStaticScratchBytes)
+        return fail(SPIIR_EUNSUPPORTED, "problem needs %zu bytes of scratch; the static array holds %zu", cur,
+                    kStaticScratchBytes);
+    BankArgs a{};
+    a.red_offset = (size_t)(((D_pad + tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
+    a.bar_offset = a.red_offset + (size_t)NL * (R + 1) * sizeof(float2);
+    const size_t smem = a.bar_offset + 16;
+    if (smem > (size_t)kBankMaxSmem) return fail(SPIIR_EUNSUPPORTED, "strain window does not fit in shared memory");
+    unsigned char *base = nullptr;
+    SPIIR_TRY(static_scratch_address(&base));
+    // inputs into the scratch, packed region and strain window cleared
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(base + o_off, off, sizeof(int64_t) * (n_templates + 1), cudaMemcpyHostToDevice, st));
+    if (F > 0) {
+        SPIIR_CUDA_TRY(cudaMemcpyAsync(base + o_a1, a1, sizeof(float2) * F, cudaMemcpyHostToDevice, st));
+        SPIIR_CUDA_TRY(cudaMemcpyAsync(base + o_b0, b0, sizeof(float2) * F, cudaMemcpyHostToDevice, st));
+        SPIIR_CUDA_TRY(cudaMemcpyAsync(base + o_d, delay, sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    }
+    SPIIR_CUDA_TRY(cudaMemsetAsync(base + o_pk, 0, pk_bytes, st));
+    SPIIR_CUDA_TRY(cudaMemsetAsync(base + o_x, 0, sizeof(float) * xpitch * n_det, st));
+    SPIIR_CUDA_TRY(cudaMemsetAsync(base + o_status, 0, sizeof(int), st));
+    SPIIR_CUDA_TRY(cudaMemcpy2DAsync(reinterpret_cast<float *>(base + o_x) + D_pad, xpitch * sizeof(float), strain,
+                                     strain_pitch * sizeof(float), n * sizeof(float), n_det, cudaMemcpyDeviceToDevice,
+                                     st));
+    k_static_layout<<<1, 32, 0, st>>>(reinterpret_cast<const int64_t *>(base + o_off), n_templates, S, NL,
+                                      reinterpret_cast<int *>(base + o_cta), reinterpret_cast<int *>(base + o_l0),
+                                      reinterpret_cast<int4 *>(base + o_segs), reinterpret_cast<int *>(base + o_so),
+                                      reinterpret_cast<int *>(base + o_wf), reinterpret_cast<int *>(base + o_act));
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    if (F > 0) {
+        const int nb = (int)((F + 255) / 256);
+        k_static_scatter<<<nb, 256, 0, st>>>(
+            reinterpret_cast<const int64_t *>(base + o_off), reinterpret_cast<const float2 *>(base + o_a1),
+            reinterpret_cast<const float2 *>(base + o_b0), reinterpret_cast<const int32_t *>(base + o_d), n_templates, F,
+            S, NL, reinterpret_cast<const int *>(base + o_cta), reinterpret_cast<const int *>(base + o_l0),
+            reinterpret_cast<float2 *>(base + o_are), reinterpret_cast<float2 *>(base + o_aim),
+            reinterpret_cast<float2 *>(base + o_bre), reinterpret_cast<float2 *>(base + o_bim),
+            reinterpret_cast<int *>(base + o_dly));
+        SPIIR_CUDA_TRY(cudaGetLastError());
+    }
+    a.xbuf = reinterpret_cast<const float *>(base + o_x);
+    a.xpitch = xpitch;
+    a.D_pad = D_pad;
+    a.n = n;
+    a.c_tile = tile;
+    a.are = reinterpret_cast<const float2 *>(base + o_are);
+    a.aim = reinterpret_cast<const float2 *>(base + o_aim);
+    a.bre = reinterpret_cast<const float2 *>(base + o_bre);
+    a.bim = reinterpret_cast<const float2 *>(base + o_bim);
+    a.delay = reinterpret_cast<const int *>(base + o_dly);
+    a.state = reinterpret_cast<float4 *>(base + o_st);
+    a.state_det_stride = npair;
+    a.segs = reinterpret_cast<const int4 *>(base + o_segs);
+    a.seg_off = reinterpret_cast<const int *>(base + o_so);
+    a.wfirst = reinterpret_cast<const int *>(base + o_wf);
+    a.cta_active = reinterpret_cast<const int *>(base + o_act);
+    a.z = reinterpret_cast<float2 *>(snr);
+    a.zpitch = snr_pitch;
+    a.n_det = n_det;
+    a.status = reinterpret_cast<int *>(base + o_status);
+    if (S == 8) return launch_bank_nl<8>(a, NL, R, n_cta, n_det, smem, st);
+    return launch_bank_nl<16>(a, NL, R, n_cta, n_det, smem, st);
 }

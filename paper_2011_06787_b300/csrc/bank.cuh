@@ -10,6 +10,12 @@ namespace spiir {
 constexpr int kBankTile = 1024;                // default time steps per staged strain window
 constexpr int kBankMaxSmem = 227 * 1024;       // dynamic shared memory limit per block
 constexpr int kBankMaxDelay = 32768;           // largest delay whose window fits
+// limits of spiir_filter_static (fixed-size static scratch)
+constexpr int kStaticMaxDet = 4;
+constexpr int kStaticMaxTemplates = 4096;
+constexpr int kStaticMaxFilters = 131072;
+constexpr int kStaticMaxSamples = 65536;
+constexpr int kStaticMaxDelay = 8192;
 
 struct BankArgs {
     const float *xbuf;        // [n_det][xpitch] window source: D_pad history + chunk

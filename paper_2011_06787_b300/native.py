@@ -41,6 +41,7 @@ SIGNATURES = {
     "spiir_bank_get_state": (_I, [_P, _P, _SZ]),
     "spiir_bank_set_state": (_I, [_P, _P, _SZ]),
     "spiir_filter_chunk": (_I, [_P, _P, _I64, _I64, _P, _I64, _P]),
+    "spiir_filter_static": (_I, [_I, _I, _P, _P, _P, _P, _P, _I64, _I64, _P, _I64, _P]),
     "spiir_bank_set_shape": (_I, [_P, _I, _I, _I, _I]),
     "spiir_bank_get_shape": (_I, [_P, _P, _P, _P, _P]),
     "spiir_sky_set_scan_shape": (_I, [_P, _I, _I]),
