@@ -181,3 +181,94 @@ def online_chunk(chunk_index: int) -> np.ndarray:
     """1 s chunk number ``chunk_index`` of the online-sized strain, [3][2048] float32."""
     c = ONLINE
     return white_noise(c["index"], c["n_det"], c["chunk"], sub=1000 + chunk_index)
+
+
+# ----------------------------------------------------------------------------------------------
+# Chirp targets and initial IIR coefficients for the adjoint workload
+
+G_MSUN_S = 4.925490947641267e-06   # G M_sun / c^3 in seconds
+CHIRP = dict(index=3, n_templates=256, n_filters=300, rate=2048.0, f_lo=30.0, f_hi=1024.0, mc=(1.0, 3.0))
+
+
+def newtonian_chirp(mc_msun: float, rate: float = 2048.0, f_lo: float = 30.0, f_hi: float = 1024.0):
+    """Leading-order (Newtonian) complex chirp, time-reversed so that sample 0 is the
+    high-frequency end.  tau is the time to coalescence, M = G Mc / c^3:
+        f(tau) = (1/pi) (5 / (256 tau))^(3/8) M^(-5/8),   phi(tau) = -2 (tau / (5 M))^(5/8),
+        amplitude proportional to f^(2/3).
+    Sample j is at tau_j = tau(f_hi) + j / rate, up to tau(f_lo).  Returns complex128 h[j]."""
+    M = mc_msun * G_MSUN_S
+    tau_of_f = lambda f: (5.0 / 256.0) * (math.pi * f) ** (-8.0 / 3.0) * M ** (-5.0 / 3.0)
+    t_hi, t_lo = tau_of_f(f_hi), tau_of_f(f_lo)
+    n = int(math.floor((t_lo - t_hi) * rate)) + 1
+    tau = t_hi + np.arange(n) / rate
+    f = (1.0 / math.pi) * (5.0 / (256.0 * tau)) ** (3.0 / 8.0) * M ** (-5.0 / 8.0)
+    phi = -2.0 * (tau / (5.0 * M)) ** (5.0 / 8.0)
+    amp = (f / f_hi) ** (2.0 / 3.0)
+    return amp * np.exp(1j * phi)
+
+
+def segment_fit(h: np.ndarray, n_filters: int):
+    """Per-frequency-segment first-order IIR fit of a complex waveform h[k].
+
+    The phase is approximated linearly on each segment (the SPIIR construction: a = e^(gamma +
+    i omega), b = the waveform at the segment start).  Segment lengths follow an equal
+    share of the integral of |phi''|^(1/2), so that the quadratic phase error is about the same
+    on every segment.  omega is the mean phase slope over the segment and gamma = -1 / length.
+    Returns (a1, b0, delay) as complex128, complex128, int32 arrays of n_filters entries."""
+    n = h.size
+    ph = np.unwrap(np.angle(h))
+    d2 = np.abs(np.gradient(np.gradient(ph)))
+    w = np.sqrt(d2 + 1e-12)
+    cum = np.concatenate([[0.0], np.cumsum(w)])
+    edges = np.searchsorted(cum, np.linspace(0.0, cum[-1], n_filters + 1))
+    edges = np.clip(edges, 0, n)
+    edges[0], edges[-1] = 0, n
+    for i in range(1, edges.size):           # strictly increasing, at least one sample each
+        edges[i] = max(edges[i], edges[i - 1] + 1)
+    edges = np.minimum(edges, n)
+    a1 = np.empty(n_filters, dtype=np.complex128)
+    b0 = np.empty(n_filters, dtype=np.complex128)
+    d = np.empty(n_filters, dtype=np.int32)
+    for m in range(n_filters):
+        lo, hi = int(min(edges[m], n - 1)), int(max(min(edges[m + 1], n), min(edges[m], n - 1) + 1))
+        L = max(hi - lo, 1)
+        omega = (ph[hi - 1] - ph[lo]) / max(L - 1, 1) if L > 1 else (ph[min(lo + 1, n - 1)] - ph[lo])
+        a1[m] = np.exp(-1.0 / L + 1j * omega)
+        b0[m] = h[lo]
+        d[m] = lo
+    return a1, b0, d
+
+
+def chirp_workload(n_templates: int = CHIRP["n_templates"], n_filters: int = CHIRP["n_filters"],
+                   mc=None, max_len: int = None):
+    """Adjoint workload: chirp targets and perturbed IIR fits.
+
+    Chirp masses are uniform in [1, 3] solar masses (or the given list).  The fit
+    coefficients are perturbed by +-5%: the decay rate gamma and |b0| by a factor 1 + 0.05 u,
+    the phase of b0 by 0.05 pi u, and the frequency omega by 0.05 u (2 pi / length) -- a drift of
+    at most 5% of a cycle over the segment -- with u uniform in [-1, 1].  Targets are padded
+    with zeros to the longest chirp (or truncated to max_len).  Returns dict with h [T][n]
+    complex128, a1, b0 [T][F] complex64, delay [T][F] int32, s0 [T][F] complex64 (zeros), mc."""
+    g = rng(CHIRP["index"], "chirp")
+    if mc is None:
+        mc = g.uniform(CHIRP["mc"][0], CHIRP["mc"][1], n_templates)
+    mc = np.asarray(mc, dtype=np.float64)
+    hs = [newtonian_chirp(float(m)) for m in mc]
+    if max_len is not None:
+        hs = [h[:max_len] for h in hs]
+    n = max(h.size for h in hs)
+    H = np.zeros((len(hs), n), dtype=np.complex128)
+    A = np.empty((len(hs), n_filters), dtype=np.complex64)
+    B = np.empty_like(A)
+    D = np.empty((len(hs), n_filters), dtype=np.int32)
+    for t, h in enumerate(hs):
+        H[t, : h.size] = h
+        a1, b0, d = segment_fit(h, n_filters)
+        L = np.diff(np.concatenate([d, [h.size]])).clip(min=1)
+        u = g.uniform(-1.0, 1.0, (4, n_filters))
+        gam = np.log(np.abs(a1)) * (1.0 + 0.05 * u[0])
+        om = np.angle(a1) + 0.05 * u[1] * 2.0 * math.pi / L
+        A[t] = np.exp(gam + 1j * om).astype(np.complex64)
+        B[t] = (b0 * (1.0 + 0.05 * u[2]) * np.exp(1j * 0.05 * math.pi * u[3])).astype(np.complex64)
+        D[t] = d
+    return dict(h=H, a1=A, b0=B, delay=D, s0=np.zeros_like(A), mc=mc)
