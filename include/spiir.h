@@ -41,6 +41,7 @@ extern "C" {
 typedef struct spiir_bank_s *spiir_bank_t;
 typedef struct spiir_sky_s *spiir_sky_t;
 typedef struct spiir_pipeline_s *spiir_pipeline_t;
+typedef struct spiir_batch_s *spiir_batch_t;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int spiir_version(void);
@@ -259,6 +260,51 @@ int spiir_pipeline_run(spiir_pipeline_t pipe, const float *strain_dev, int64_t s
 int spiir_pipeline_run_host(spiir_pipeline_t pipe, const float *strain_host, int64_t n,
                             float *max_stat_host, int32_t *argmax_host,
                             float *null_stat_host, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Batched multirate banks.  Several template banks of uneven size share one strain stream.
+ * Every filter runs in one band b at the rate 1 / M_b of the strain (M_b a power of two;
+ * M = 1 is the full rate); its delay is in samples of its band.  Per chunk of strain:
+ *   x_b[j]  = sum_{i<32} h_b[i] x[j M_b - i]   (Hann-windowed sinc, cutoff 0.8 x the band's
+ *             Nyquist, unit DC gain; M = 1 passes x through)
+ *   z_b     = the band-b filters of each template on x_b (Eq. (zk), Sec. II.B.1)
+ *   z[k]    = sum_b (1 - w) z_b[m-1] + w z_b[m],  m = floor(k / M_b), w = (k mod M_b) / M_b
+ *   coherent scan of z over all templates of all banks (Sec. II.C.1), one H-sample lag as in
+ *   the streaming pipeline.
+ * The paper filters one rate only (its front end downsamples 16 kHz to 2 kHz by FIR); the
+ * band split, the decimation filter and the upsampling rule are this library's definitions.
+ * ---------------------------------------------------------------------------------- */
+
+/* templates_per_bank [n_banks]; filter_offsets [T+1] over all templates of all banks in
+ * bank order (T = sum of templates_per_bank); a1, b0 [2 F]; delay [F]; band [F] in
+ * [0, n_bands); band_factor [n_bands] (powers of two <= 64).  chunk: full-rate samples per
+ * call, >= 32 and a multiple of every band factor.  sky must outlive the batch.  All host
+ * arrays.  Builds both the per-band banks of the batched path and the per-(bank, band)
+ * banks of the plain path. */
+int spiir_batch_create(int n_det, int n_banks, const int32_t *templates_per_bank,
+                       const int64_t *filter_offsets_host, const float *a1_host,
+                       const float *b0_host, const int32_t *delay_host, const int32_t *band_host,
+                       int n_bands, const int32_t *band_factor, spiir_sky_t sky, int64_t chunk,
+                       spiir_batch_t *out);
+void spiir_batch_destroy(spiir_batch_t batch);
+int spiir_batch_info(spiir_batch_t batch, int *n_templates, int64_t *n_filters, int *n_work_items);
+/* Zero all streaming state of both paths. */
+int spiir_batch_reset(spiir_batch_t batch, void *stream);
+/* Launch shape of the persistent filter launch (a tuning knob): filters_per_lane,
+ * lanes_per_block, steps_per_reduce as in spiir_bank_set_shape; blocks_per_sm 0 = as many as
+ * fit.  Keeps the streaming state; drops a captured graph.  Synchronises the device. */
+int spiir_batch_set_shape(spiir_batch_t batch, int filters_per_lane, int lanes_per_block,
+                          int steps_per_reduce, int blocks_per_sm);
+/* Process one chunk.  strain_dev [n_det][chunk] (contiguous); outputs [T][chunk] as in
+ * spiir_coherent_scan (templates in bank order).
+ *   mode 0: plain path, separate launches per bank and band;
+ *   mode 1: batched path, one persistent filter launch, launched eagerly;
+ *   mode 2: batched path replayed from a CUDA graph, captured on the first call (and again
+ *           whenever the buffer pointers change).
+ * A batch streams in one path: switching between mode 0 and modes 1/2 needs
+ * spiir_batch_reset (SPIIR_EINVAL otherwise).  Enqueued on stream. */
+int spiir_batch_run(spiir_batch_t batch, int mode, const float *strain_dev, float *max_stat_dev,
+                    int32_t *argmax_dev, float *null_stat_dev, void *stream);
 
 #ifdef __cplusplus
 }

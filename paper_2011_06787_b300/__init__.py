@@ -13,7 +13,7 @@ import numpy as np
 from . import native
 from .native import SpiirError, check
 
-__all__ = ["Bank", "Sky", "Pipeline", "sky_tables", "SpiirError", "device_status", "version"]
+__all__ = ["Bank", "Sky", "Pipeline", "Batch", "sky_tables", "SpiirError", "device_status", "version"]
 
 
 def _stream_ptr(stream=None):
@@ -250,3 +250,69 @@ class Pipeline:
         n = strain.shape[1]
         check(native.lib().spiir_pipeline_run_host(self._h, _host_ptr(strain), n, _host_ptr(max_stat),
                                                    _host_ptr(argmax), _host_ptr(null_stat), _stream_ptr(stream)))
+
+
+class Batch:
+    """Batched multirate banks (spiir_batch_*).  banks: list of (offsets, a1, b0, delay, band)
+    host arrays, one per bank; band_factor: decimation factor of each band."""
+
+    PLAIN, BATCHED, GRAPH = 0, 1, 2
+
+    def __init__(self, n_det: int, banks, band_factor, sky: Sky, chunk: int):
+        offs, a1s, b0s, ds, bs, tpb = [np.zeros(1, np.int64)], [], [], [], [], []
+        for off, a1, b0, d, band in banks:
+            off = np.asarray(off, np.int64)
+            offs.append(offs[-1][-1] + off[1:])
+            a1s.append(np.asarray(a1, np.complex64))
+            b0s.append(np.asarray(b0, np.complex64))
+            ds.append(np.asarray(d, np.int32))
+            bs.append(np.asarray(band, np.int32))
+            tpb.append(off.size - 1)
+        off = np.ascontiguousarray(np.concatenate(offs))
+        a1 = np.ascontiguousarray(np.concatenate(a1s)).view(np.float32)
+        b0 = np.ascontiguousarray(np.concatenate(b0s)).view(np.float32)
+        d = np.ascontiguousarray(np.concatenate(ds))
+        band = np.ascontiguousarray(np.concatenate(bs))
+        tpb = np.ascontiguousarray(tpb, np.int32)
+        bf = np.ascontiguousarray(band_factor, np.int32)
+        h = ctypes.c_void_p()
+        check(native.lib().spiir_batch_create(int(n_det), len(tpb), _host_ptr(tpb), _host_ptr(off), _host_ptr(a1),
+                                              _host_ptr(b0), _host_ptr(d), _host_ptr(band), int(bf.size), _host_ptr(bf),
+                                              sky.handle, int(chunk), ctypes.byref(h)))
+        self._h = h
+        self.sky = sky
+        self.n_det = int(n_det)
+        self.chunk = int(chunk)
+        self.n_templates = int(off.size - 1)
+        self.templates_per_bank = tpb
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            native.lib().spiir_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        T, F, I = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        check(native.lib().spiir_batch_info(self._h, ctypes.byref(T), ctypes.byref(F), ctypes.byref(I)))
+        return T.value, F.value, I.value
+
+    def reset(self, stream=None):
+        check(native.lib().spiir_batch_reset(self._h, _stream_ptr(stream)))
+
+    def set_shape(self, filters_per_lane=8, lanes_per_block=128, steps_per_reduce=32, blocks_per_sm=0):
+        check(native.lib().spiir_batch_set_shape(self._h, int(filters_per_lane), int(lanes_per_block),
+                                                 int(steps_per_reduce), int(blocks_per_sm)))
+
+    def run(self, strain, max_stat, argmax, null_stat, mode=GRAPH, stream=None):
+        import torch
+        _require_cuda(strain, torch.float32, "strain")
+        if not strain.is_contiguous() or tuple(strain.shape) != (self.n_det, self.chunk):
+            raise ValueError("strain must be a contiguous [n_det][chunk] tensor")
+        check(native.lib().spiir_batch_run(self._h, int(mode), _dev_ptr(strain), _dev_ptr(max_stat),
+                                           _dev_ptr(argmax), _dev_ptr(null_stat), _stream_ptr(stream)))

@@ -30,18 +30,21 @@ namespace spiir {
 // ---------------------------------------------------------------------------------------
 // Kernel
 
+// Shared-memory layout of one block: the mbarrier at offset 0, the strain window at
+// kBankSmemHead, the reduction buffer at a.red_offset.
+
+// One block's work: template block `cta` of bank `a` for detector `det` over the whole call.
+// Returns false when a bounded wait ran out (every thread of the block returns false).
 template <int S, int NL, int R>
-__global__ void __launch_bounds__(NL, 1) k_filter_bank(const __grid_constant__ BankArgs a) {
+__device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, const int det, unsigned char *smem,
+                                           uint64_t *bar, uint32_t &phase) {
     constexpr int NP = S / 2;
     constexpr int NW = NL / 32;
-    extern __shared__ __align__(128) unsigned char smem[];
-    float *xw = reinterpret_cast<float *>(smem);
+    float *xw = reinterpret_cast<float *>(smem + kBankSmemHead);
     float2 *red = reinterpret_cast<float2 *>(smem + a.red_offset);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_offset);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int cta = blockIdx.x, det = blockIdx.y;
     const int active = a.cta_active[cta];
     const bool busy = (warp * 32) < active;
 
@@ -73,10 +76,6 @@ __global__ void __launch_bounds__(NL, 1) k_filter_bank(const __grid_constant__ B
     const int seg0 = a.seg_off[cta];
     const int nseg = a.seg_off[cta + 1] - seg0;
     const int wfirst = a.wfirst[cta * NW + warp];
-
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
-    uint32_t phase = 0;
     const float *xsrc = a.xbuf + (int64_t)det * a.xpitch;
 
     for (int64_t k0 = 0; k0 < a.n; k0 += a.c_tile) {
@@ -91,7 +90,7 @@ __global__ void __launch_bounds__(NL, 1) k_filter_bank(const __grid_constant__ B
                 report_timeout(a.status);
                 mbar_wait(bar, phase);
             }
-            return;
+            return false;
         }
         phase ^= 1u;
 
@@ -176,6 +175,39 @@ __global__ void __launch_bounds__(NL, 1) k_filter_bank(const __grid_constant__ B
         const float2 r = unpack2(yre[p]), i = unpack2(yim[p]);
         st[(int64_t)p * NL] = make_float4(r.x, r.y, i.x, i.y);
     }
+    return true;
+}
+
+template <int S, int NL, int R>
+__global__ void __launch_bounds__(NL, 1) k_filter_bank(const __grid_constant__ BankArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    bank_block<S, NL, R>(a, blockIdx.x, blockIdx.y, smem, bar, phase);
+}
+
+// Persistent form: a grid of resident blocks takes (bank, block, detector) work items from a
+// shared counter (atomic fetch-and-add, no waiting) in the order of the item list, so that
+// banks of uneven size and different rates share one launch.
+template <int S, int NL, int R>
+__global__ void __launch_bounds__(NL, 1) k_filter_bank_persistent(const __grid_constant__ PersistArgs p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int item_s;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= p.n_items) break;
+        const int4 it = p.items[item];
+        if (!bank_block<S, NL, R>(p.banks[it.x], it.y, it.z, smem, bar, phase)) break;
+    }
 }
 
 template <int S, int NL, int R>
@@ -209,9 +241,12 @@ static int launch_bank_any(const spiir_bank_s *b, const BankArgs &a, size_t smem
     }
 }
 
+size_t bank_red_offset(const spiir_bank_s *b) {
+    return kBankSmemHead + (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
+}
+
 size_t bank_smem_bytes(const spiir_bank_s *b) {
-    const size_t win = (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
-    return win + (size_t)b->NL * (b->R + 1) * sizeof(float2) + 16;
+    return bank_red_offset(b) + (size_t)b->NL * (b->R + 1) * sizeof(float2);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -459,6 +494,59 @@ static int bank_reserve(spiir_bank_s *b, int64_t ncap, cudaStream_t stream) {
     return SPIIR_OK;
 }
 
+int bank_prepare(spiir_bank_s *b, int64_t ncap, cudaStream_t stream) { return bank_reserve(b, ncap, stream); }
+
+BankArgs bank_args(spiir_bank_s *b, float2 *z, int64_t zpitch, int64_t n) {
+    BankArgs a{};
+    a.xbuf = b->xbuf[b->cur];
+    a.xpitch = b->xpitch;
+    a.D_pad = b->D_pad;
+    a.n = n;
+    a.c_tile = b->c_tile;
+    a.are = b->are; a.aim = b->aim; a.bre = b->bre; a.bim = b->bim;
+    a.delay = b->dly;
+    a.state = b->state;
+    a.state_det_stride = b->state_det_stride;
+    a.segs = b->segs; a.seg_off = b->seg_off; a.wfirst = b->wfirst; a.cta_active = b->active;
+    a.z = z;
+    a.zpitch = zpitch;
+    a.n_det = b->n_det;
+    a.status = device_status_word();
+    a.red_offset = bank_red_offset(b);
+    return a;
+}
+
+template <int S, int NL, int R>
+static int launch_persist(const PersistArgs &p, int blocks_per_sm, size_t smem, cudaStream_t s) {
+    auto kern = k_filter_bank_persistent<S, NL, R>;
+    cudaFuncAttributes fa{};
+    SPIIR_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const int dyn_max = kBankMaxSmem - (int)fa.sharedSizeBytes;
+    if ((int)smem > dyn_max) return fail(SPIIR_EUNSUPPORTED, "persistent filter kernel needs %zu bytes of shared memory", smem);
+    SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+    int nb = 0, dev = 0, n_sm = 0;
+    SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NL, smem));
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    if (nb < 1) return fail(SPIIR_EUNSUPPORTED, "persistent filter kernel does not fit on an SM");
+    const int per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, nb) : nb;
+    const int grid = std::max(1, std::min(p.n_items, n_sm * per_sm));
+    kern<<<grid, NL, smem, s>>>(p);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+int bank_launch_persistent(const PersistArgs &p, int S, int NL, int R, int blocks_per_sm, size_t smem,
+                           cudaStream_t s) {
+#define SPIIR_PERSIST(S_, NL_, R_) \
+    if (S == S_ && NL == NL_ && R == R_) return launch_persist<S_, NL_, R_>(p, blocks_per_sm, smem, s);
+    SPIIR_PERSIST(8, 128, 32) SPIIR_PERSIST(8, 256, 32) SPIIR_PERSIST(8, 128, 16) SPIIR_PERSIST(8, 256, 16)
+    SPIIR_PERSIST(16, 128, 32) SPIIR_PERSIST(16, 256, 32) SPIIR_PERSIST(16, 128, 16) SPIIR_PERSIST(16, 256, 16)
+    SPIIR_PERSIST(4, 128, 32) SPIIR_PERSIST(4, 256, 32) SPIIR_PERSIST(4, 128, 16) SPIIR_PERSIST(4, 256, 16)
+#undef SPIIR_PERSIST
+    return fail(SPIIR_EINVAL, "unsupported persistent shape");
+}
+
 int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int64_t n, float2 *z,
                 int64_t zpitch, cudaStream_t stream) {
     SPIIR_TRY(bank_reserve(b, std::max<int64_t>(n, 2048), stream));
@@ -480,8 +568,7 @@ int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int6
     a.zpitch = zpitch;
     a.n_det = b->n_det;
     a.status = device_status_word();
-    a.red_offset = (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
-    a.bar_offset = a.red_offset + (size_t)b->NL * (b->R + 1) * sizeof(float2);
+    a.red_offset = bank_red_offset(b);
     const size_t smem = bank_smem_bytes(b);
     if (smem > (size_t)kBankMaxSmem)
         return fail(SPIIR_EUNSUPPORTED, "strain window of %d + %d samples does not fit in shared memory",
@@ -897,9 +984,8 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
         return fail(SPIIR_EUNSUPPORTED, "problem needs %zu bytes of scratch; the static array holds %zu", cur,
                     kStaticScratchBytes);
     BankArgs a{};
-    a.red_offset = (size_t)(((D_pad + tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
-    a.bar_offset = a.red_offset + (size_t)NL * (R + 1) * sizeof(float2);
-    const size_t smem = a.bar_offset + 16;
+    a.red_offset = kBankSmemHead + (size_t)(((D_pad + tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
+    const size_t smem = a.red_offset + (size_t)NL * (R + 1) * sizeof(float2);
     if (smem > (size_t)kBankMaxSmem) return fail(SPIIR_EUNSUPPORTED, "strain window does not fit in shared memory");
     unsigned char *base = nullptr;
     SPIIR_TRY(static_scratch_address(&base));

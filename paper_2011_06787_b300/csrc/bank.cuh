@@ -8,6 +8,8 @@
 namespace spiir {
 
 constexpr int kBankTile = 1024;                // default time steps per staged strain window
+constexpr int kBankSmemHead = 128;             // bytes before the strain window (mbarrier)
+constexpr int kMaxBands = 4;                   // banks per persistent launch
 constexpr int kBankMaxSmem = 227 * 1024;       // dynamic shared memory limit per block
 constexpr int kBankMaxDelay = 32768;           // largest delay whose window fits
 // limits of spiir_filter_static (fixed-size static scratch)
@@ -35,7 +37,14 @@ struct BankArgs {
     int64_t zpitch;
     int n_det;
     int *status;
-    size_t red_offset, bar_offset;
+    size_t red_offset;        // byte offset of the reduction buffer in shared memory
+};
+
+struct PersistArgs {
+    BankArgs banks[kMaxBands];
+    const int4 *items;        // (bank, block, detector, 0), in the order blocks take them
+    int n_items;
+    int *counter;             // zero before the launch
 };
 
 }  // namespace spiir
@@ -74,6 +83,11 @@ struct spiir_bank_s {
 
 namespace spiir {
 size_t bank_smem_bytes(const spiir_bank_s *b);
+size_t bank_red_offset(const spiir_bank_s *b);
+int bank_prepare(spiir_bank_s *b, int64_t ncap, cudaStream_t stream);
+BankArgs bank_args(spiir_bank_s *b, float2 *z, int64_t zpitch, int64_t n);
+int bank_launch_persistent(const PersistArgs &p, int S, int NL, int R, int blocks_per_sm, size_t smem,
+                           cudaStream_t s);
 int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int64_t n, float2 *z,
                 int64_t zpitch, cudaStream_t stream);
 }

@@ -272,3 +272,48 @@ def chirp_workload(n_templates: int = CHIRP["n_templates"], n_filters: int = CHI
         B[t] = (b0 * (1.0 + 0.05 * u[2]) * np.exp(1j * 0.05 * math.pi * u[3])).astype(np.complex64)
         D[t] = d
     return dict(h=H, a1=A, b0=B, delay=D, s0=np.zeros_like(A), mc=mc)
+
+
+# ----------------------------------------------------------------------------------------------
+# Multirate batched workload
+
+MULTIRATE = dict(index=2, n_det=3, rate=2048, chunk=512, n_banks=8, t_range=(64, 2048), f_range=(100, 1200),
+                 factors=(1, 4, 16), band_p=(0.4, 0.35, 0.25), d_max_s=2.0, nside=16, sigma=(0.5, 2.0))
+
+
+def multirate_banks(n_banks=None, t_range=None, f_range=None, seed_sub=0):
+    """Banks of the batched workload: template counts log-uniform in t_range, filters per
+    template uniform in f_range, each filter in band b with probability band_p[b].  In band b
+    (decimation M_b) the delay is uniform in [0, 2 s x 2048 / M_b] band samples, |a1| uniform in
+    [0.9, 0.999] and arg a1 uniform in [-0.8 pi, 0.8 pi] for decimated bands (inside the
+    decimation filter's passband) or [0, 2 pi) at the full rate; b0 complex normal / sqrt(F).
+    Returns a list of (offsets, a1, b0, delay, band)."""
+    c = MULTIRATE
+    n_banks = c["n_banks"] if n_banks is None else n_banks
+    t_range = c["t_range"] if t_range is None else t_range
+    f_range = c["f_range"] if f_range is None else f_range
+    g = rng(c["index"], "bands", seed_sub)
+    out = []
+    for _ in range(n_banks):
+        T = int(round(math.exp(g.uniform(math.log(t_range[0]), math.log(t_range[1])))))
+        counts = g.integers(f_range[0], f_range[1] + 1, T)
+        off = np.zeros(T + 1, dtype=np.int64)
+        np.cumsum(counts, out=off[1:])
+        F = int(off[-1])
+        band = g.choice(len(c["factors"]), size=F, p=c["band_p"]).astype(np.int32)
+        M = np.asarray(c["factors"])[band]
+        r = g.uniform(0.9, 0.999, F)
+        ph_full = g.uniform(0.0, 2.0 * math.pi, F)
+        ph_dec = g.uniform(-0.8 * math.pi, 0.8 * math.pi, F)
+        ph = np.where(M == 1, ph_full, ph_dec)
+        a1 = (r * np.exp(1j * ph)).astype(np.complex64)
+        scale = np.repeat(1.0 / np.sqrt(counts), counts)
+        b0 = ((g.standard_normal(F) + 1j * g.standard_normal(F)) / math.sqrt(2.0) * scale).astype(np.complex64)
+        dmax = (c["d_max_s"] * c["rate"] / M).astype(np.int64)
+        d = np.floor(g.uniform(0.0, 1.0, F) * (dmax + 1)).astype(np.int32)
+        out.append((off, a1, b0, d, band))
+    return out
+
+
+def multirate_chunk(chunk_index: int, n_det: int = 3, chunk: int = 512) -> np.ndarray:
+    return white_noise(MULTIRATE["index"], n_det, chunk, sub=2000 + chunk_index)

@@ -71,3 +71,21 @@ def test_sky_tables_rejects_bad_geometry():
         sp.sky_tables(pos, arms, arms, np.array([1.0, -1.0, 1.0]), 4, 2048.0)  # negative sigma
     with pytest.raises(sp.SpiirError):
         sp.sky_tables(pos, arms, arms, np.ones(3), 0, 2048.0)
+
+
+def test_batch_create_rejects_invalid_arguments():
+    import synth
+    banks = synth.multirate_banks(n_banks=2, t_range=(2, 4), f_range=(5, 10), seed_sub=9)
+
+    class FakeSky:  # any handle; validation of the band layout happens before the sky is used
+        handle = None
+
+    for factors, chunk, msg in (((1, 3, 16), 512, "power of two"), ((1, 4, 16), 520, "multiple"),
+                                ((1, 4, 16), 16, "multiple"), ((1, 4, 16), 512, "sky is NULL")):
+        with pytest.raises(sp.SpiirError) as e:
+            sp.Batch(3, banks, factors, FakeSky(), chunk)
+        assert e.value.code == native.EINVAL and msg in str(e.value)
+    bad = [(o, a, b, d, np.full_like(bb, 3)) for o, a, b, d, bb in banks]
+    with pytest.raises(sp.SpiirError) as e:
+        sp.Batch(3, bad, (1, 4, 16), FakeSky(), 512)
+    assert "band 3" in str(e.value)

@@ -174,5 +174,5 @@ def test_gradient_descent_improves_the_overlap():
         loss = overlap_loss(h, impulse_response(a1, b0, s0, d, n, 1024)).sum()
         loss.backward()
         opt.step()
-        first = float(loss) if first is None else first
-    assert float(loss) < 0.95 * first
+        first = loss.item() if first is None else first
+    assert loss.item() < 0.95 * first
