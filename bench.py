@@ -169,7 +169,7 @@ def run_reference(args):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    T_f, T_c = 16, 2
+    T_f, T_c = 128, 16
     vals = []
     last = None
     for i in range(args.warmup + args.steps):
@@ -209,7 +209,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     # each rank filters its own 1024-template bank (weak scaling over template shards)
-    w = synth.online_workload()
+    w = synth.online_workload(args.templates)
     bank, det, sigma = w["bank"], w["det"], w["sigma"]
     n_det, T, n = 3, bank.n_templates, 2048
     tabs = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 16, 2048.0)
@@ -224,7 +224,7 @@ def run_gpu(args):
     ms = torch.empty((T, n), dtype=torch.float32, device=dev)
     am = torch.empty((T, n), dtype=torch.int32, device=dev)
     nl = torch.empty((T, n), dtype=torch.float32, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(max(1, args.flush_mib * 1024 * 1024 // 4), dtype=torch.float32, device=dev)
 
     def barrier():
         if world > 1:
@@ -284,6 +284,93 @@ def run_gpu(args):
     traffic = recorded_traffic(kern, source_hash(*src))
 
     # end to end through the host-buffer C entry point: pinned strain in, results out
+    e2e_value = None
+    if not args.no_e2e:
+        e2e_value = e2e_rate(args, pipe, T, n, flush, updates_per_step, world, dev, barrier)
+
+    batched = None
+    if not args.no_batched:
+        batched = batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r = oracle_sample(1024, 128, threads)
+        cpu = {"value": r["step_updates_per_s"], "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "filter bank on all 1024 templates and coherent scan on 128 templates over one 2048-sample "
+                         "chunk (FP64 C oracle, OpenMP over templates); whole-step rate from the per-template times",
+               "filter_updates_per_s": r["updates_per_s"], "coherent_pixel_samples_per_s": r["pixel_samples_per_s"],
+               "seconds": r["t_filter"] + r["t_coh"]}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "templates_per_gpu": T, "filters_per_gpu": int(bank.n_filters),
+                       "chunk_samples": n, "n_pix": P, "parallelism": f"template shards x{world}",
+                       "l2": f"flushed before every timed step ({args.flush_mib} MiB write)"},
+            "coherent_pixel_samples_per_s": pix_rate,
+            "kernel_ms": {"k_filter_bank": k1, "k_coherent": k2},
+            "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+                         "frac": achieved / peak_max, "frac_at_run_clock": achieved / peak_run,
+                         "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
+                         "traffic": traffic},
+            "batched_vs_plain": batched,
+            "cpu_baseline": cpu,
+            "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
+                                                   "h2d_bytes_per_step": n_det * n * 4,
+                                                   "d2h_bytes_per_step": T * n * 12},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma):
+    """Multirate workload: 8 banks of uneven size over bands at 2048/512/128 Hz, 0.25 s chunks.
+    Times per-bank plain launches against one persistent launch (eager and graph-replayed)."""
+    from paper_2011_06787_b300 import autotune
+    c = synth.MULTIRATE
+    banks = synth.multirate_banks()
+    sky = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, c["nside"], 2048.0))
+    chunk = c["chunk"]
+    batch = sp.Batch(3, banks, c["factors"], sky, chunk)
+    T, F, items = batch.info()
+    updates = sum(int(np.sum(3 * (chunk // np.asarray(c["factors"])[b[4]]))) for b in banks)
+    ms = torch.empty((T, chunk), device=dev)
+    am = torch.empty((T, chunk), dtype=torch.int32, device=dev)
+    nl = torch.empty((T, chunk), device=dev)
+    xs = [torch.from_numpy(synth.multirate_chunk(i, 3, chunk)).to(dev) for i in range(args.warmup + args.steps)]
+    x = torch.empty((3, chunk), device=dev)
+    tuned = autotune.tune_batch(batch, x, ms, am, nl)
+    out = {"workload": f"{len(banks)} banks, {T} templates, {F} filters over bands 2048/512/128 Hz, "
+                       f"3 det, {chunk}-sample chunks, nside {c['nside']}",
+           "updates_per_chunk": updates, "pixel_samples_per_chunk": T * chunk * sky.n_pix,
+           "persistent_work_items": items, "tuned_shape": tuned["shape"]}
+    for mode, name in ((0, "plain"), (1, "batched"), (2, "batched_graph")):
+        batch.reset()
+        for i in range(args.warmup):
+            x.copy_(xs[i])
+            batch.run(x, ms, am, nl, mode=mode)
+
+        def step(i, mode=mode):
+            x.copy_(xs[args.warmup + i])
+            batch.run(x, ms, am, nl, mode=mode)
+        t = timed_loop(step, args.steps)
+        tot = float(np.sum(t))
+        out[name] = {"ms_per_chunk": tot / args.steps, "updates_per_s": updates * args.steps / (tot * 1e-3)}
+    sp.device_status()
+    out["speedup_graph_vs_plain"] = out["plain"]["ms_per_chunk"] / out["batched_graph"]["ms_per_chunk"]
+    out["kernel_launches_per_chunk"] = {"plain": 1 + sum(1 for b in banks for k in range(3) if np.any(b[4] == k)) +
+                                        2 * len(banks), "batched": 4}
+    return out
+
+
+def e2e_rate(args, pipe, T, n, flush, updates_per_step, world, dev, barrier):
+    import torch
     hs = [torch.from_numpy(synth.online_chunk(i)).pin_memory() for i in range(args.warmup + args.steps)]
     h_ms = torch.empty((T, n), dtype=torch.float32).pin_memory()
     h_am = torch.empty((T, n), dtype=torch.int32).pin_memory()
@@ -303,42 +390,7 @@ def run_gpu(args):
         t = torch.tensor([e2e_s], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * updates_per_step * args.steps / e2e_s
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        r = oracle_sample(16, 2, threads)
-        cpu = {"value": r["step_updates_per_s"], "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "filter bank on 16 of 1024 templates and coherent scan on 2 templates over one 2048-sample "
-                         "chunk (FP64 C oracle, OpenMP over templates); whole-step rate scaled per template",
-               "filter_updates_per_s": r["updates_per_s"], "coherent_pixel_samples_per_s": r["pixel_samples_per_s"]}
-
-    if rank == 0:
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "templates_per_gpu": T, "filters_per_gpu": int(bank.n_filters),
-                       "chunk_samples": n, "n_pix": P, "parallelism": f"template shards x{world}",
-                       "l2": "flushed before every timed step (512 MiB write)"},
-            "coherent_pixel_samples_per_s": pix_rate,
-            "kernel_ms": {"k_filter_bank": k1, "k_coherent": k2},
-            "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
-                         "frac": achieved / peak_max, "frac_at_run_clock": achieved / peak_run,
-                         "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
-                         "traffic": traffic},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_det * n * 4,
-                    "d2h_bytes_per_step": T * n * 12},
-            "gpu_launches": 2 * args.steps,
-            "clocks": clocks,
-            "wall_s_timed_region": wall,
-        }
-        print(json.dumps(out))
-    if world > 1:
-        torch.distributed.destroy_process_group()
-
+    return world * updates_per_step * args.steps / e2e_s
 
 def main():
     ap = argparse.ArgumentParser()
@@ -347,6 +399,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
+    ap.add_argument("--templates", type=int, default=1024, help="templates per GPU (1024 = the workload)")
+    ap.add_argument("--flush-mib", type=int, default=512, help="L2 flush buffer written before each timed step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

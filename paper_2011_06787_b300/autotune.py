@@ -111,3 +111,26 @@ def tune_scan(sky, snr, n, max_stat, argmax, null_stat, reps=3, shapes=SCAN_SHAP
     _cache[key] = rec
     _store(cache_path, key, rec)
     return rec
+
+
+BATCH_SHAPES = [(8, 128, 32, 0), (8, 256, 32, 0), (8, 128, 16, 0), (8, 128, 32, 1), (16, 128, 32, 0), (4, 128, 16, 0)]
+
+
+def tune_batch(batch, strain, max_stat, argmax, null_stat, reps=4, shapes=BATCH_SHAPES, verbose=False):
+    """Pick the persistent-launch shape of a Batch by timing graph replays of one chunk.  The
+    batch is reset afterwards (the timing calls advance its stream state)."""
+    results = []
+    for shp in shapes:
+        try:
+            batch.set_shape(*shp)
+        except Exception:
+            continue
+        batch.reset()
+        ms = _time_ms(lambda: batch.run(strain, max_stat, argmax, null_stat, mode=2), reps)
+        results.append((ms, shp))
+        if verbose:
+            print(f"batch shape {shp}: {ms:.3f} ms")
+    best = min(results)
+    batch.set_shape(*best[1])
+    batch.reset()
+    return {"shape": list(best[1]), "ms": best[0], "tried": [[m, list(s)] for m, s in results]}

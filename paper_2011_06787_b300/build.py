@@ -34,15 +34,19 @@ def _stale(target: str) -> bool:
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale(LIB_PATH):
-        return LIB_PATH
+def build(force: bool = False, verbose: bool = False, checked: bool = False, out: str = None) -> str:
+    """checked=True defines SPIIR_CHECKED: kernels verify their indices against the buffer sizes
+    they were given, record violations in the device status word and skip the access, and the
+    batched path synchronises after every stage.  A debugging build, written to ``out``."""
+    lib_path = out or LIB_PATH
+    if not force and not checked and not _stale(lib_path):
+        return lib_path
     os.makedirs(BUILD_DIR, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [NVCC] + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + (".checked.o" if checked else ".o"))
+        cmd = [NVCC] + FLAGS + (["-DSPIIR_CHECKED"] if checked else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,13 +58,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    os.makedirs(os.path.dirname(os.path.abspath(lib_path)), exist_ok=True)
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    if "--checked" in sys.argv:
+        print(build(force=True, checked=True, out=sys.argv[sys.argv.index("--checked") + 1]))
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <climits>
 #include <map>
 #include <mutex>
 #include <numeric>
@@ -45,6 +46,18 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+#ifdef SPIIR_CHECKED
+    {
+        int bad = 0;
+        if (cta < 0 || cta >= a.n_cta_total) bad = 1;
+        else if (((int64_t)cta * (S / 2) + S / 2) * NL > a.n_pairs_total) bad = 2;
+        else if (a.seg_off && (a.seg_off[cta] < 0 || a.seg_off[cta + 1] > a.n_segs_total)) bad = 3;
+        if (__syncthreads_or(bad)) {
+            if (bad) report_bounds(a.status, bad);
+            return false;
+        }
+    }
+#endif
     const int active = a.cta_active[cta];
     const bool busy = (warp * 32) < active;
 
@@ -81,6 +94,19 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
     for (int64_t k0 = 0; k0 < a.n; k0 += a.c_tile) {
         const int nt = (int)min((int64_t)a.c_tile, a.n - k0);
         const uint32_t bytes = (uint32_t)(a.D_pad + ((nt + 3) & ~3)) * 4u;
+#ifdef SPIIR_CHECKED
+        {
+            int bad = 0;
+            if ((int64_t)det * a.xpitch + k0 + bytes / 4 > a.x_elems) bad = 4;
+            if (kBankSmemHead + bytes > a.red_offset) bad = 5;
+            for (int s = 0; s < S; ++s)
+                if (dof[s] < 0 || dof[s] > a.D_pad) bad = 6;
+            if (__syncthreads_or(bad)) {
+                if (bad) report_bounds(a.status, bad);
+                return false;
+            }
+        }
+#endif
         __syncthreads();  // all reads of the previous window are done
         if (tid == 0) bulk_load(xw, xsrc + k0, bytes, bar);
         const bool ok = mbar_wait(bar, phase);
@@ -133,8 +159,9 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
             }
             __syncthreads();
             // pass 1: each warp sums its own rows per column, split at template boundaries;
-            // piece j of the warp overwrites row 32*warp + j (a row it has already read)
-            if (busy && wfirst >= 0) {
+            // piece j of the warp overwrites row 32*warp + j (a row it has already read).
+            // Lane r owns column r; with R < 32 the remaining lanes have no column.
+            if (busy && wfirst >= 0 && lane < R) {
                 int j = 0;
                 for (int sg = wfirst; sg < nseg; ++sg) {
                     const int4 g = a.segs[seg0 + sg];
@@ -142,6 +169,12 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                     const int hi = min(g.z, warp * 32 + 32) - warp * 32;
                     if (hi <= lo) break;
                     float2 acc = make_float2(0.f, 0.f);
+#ifdef SPIIR_CHECKED
+                    if ((warp * 32 + hi - 1) * (R + 1) + lane >= NL * (R + 1)) {
+                        report_bounds(a.status, 8);
+                        break;
+                    }
+#endif
                     for (int i = lo; i < hi; ++i) {
                         const float2 v = red[(warp * 32 + i) * (R + 1) + lane];
                         acc.x += v.x;
@@ -164,6 +197,12 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                     acc.y += v.y;
                 }
                 float2 *zrow = a.z + ((int64_t)g.x * a.n_det + det) * a.zpitch;
+#ifdef SPIIR_CHECKED
+                if (((int64_t)g.x * a.n_det + det) * a.zpitch + k0 + kb + r >= a.z_elems) {
+                    report_bounds(a.status, 7);
+                    continue;
+                }
+#endif
                 zrow[k0 + kb + r] = acc;
             }
             __syncthreads();
@@ -513,6 +552,11 @@ BankArgs bank_args(spiir_bank_s *b, float2 *z, int64_t zpitch, int64_t n) {
     a.n_det = b->n_det;
     a.status = device_status_word();
     a.red_offset = bank_red_offset(b);
+    a.n_cta_total = b->n_cta;
+    a.n_pairs_total = (int64_t)b->n_cta * (b->S / 2) * b->NL;
+    a.x_elems = b->xpitch * b->n_det;
+    a.z_elems = INT64_MAX;
+    a.n_segs_total = (int64_t)b->h_segs.size();
     return a;
 }
 
@@ -569,6 +613,11 @@ int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int6
     a.n_det = b->n_det;
     a.status = device_status_word();
     a.red_offset = bank_red_offset(b);
+    a.n_cta_total = b->n_cta;
+    a.n_pairs_total = (int64_t)b->n_cta * (b->S / 2) * b->NL;
+    a.x_elems = b->xpitch * b->n_det;
+    a.z_elems = INT64_MAX;
+    a.n_segs_total = (int64_t)b->h_segs.size();
     const size_t smem = bank_smem_bytes(b);
     if (smem > (size_t)kBankMaxSmem)
         return fail(SPIIR_EUNSUPPORTED, "strain window of %d + %d samples does not fit in shared memory",
@@ -1038,6 +1087,11 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     a.zpitch = snr_pitch;
     a.n_det = n_det;
     a.status = reinterpret_cast<int *>(base + o_status);
+    a.n_cta_total = n_cta;
+    a.n_pairs_total = npair;
+    a.x_elems = xpitch * n_det;
+    a.z_elems = INT64_MAX;
+    a.n_segs_total = n_templates;
     if (S == 8) return launch_bank_nl<8>(a, NL, R, n_cta, n_det, smem, st);
     return launch_bank_nl<16>(a, NL, R, n_cta, n_det, smem, st);
 }

@@ -38,6 +38,9 @@ struct BankArgs {
     int n_det;
     int *status;
     size_t red_offset;        // byte offset of the reduction buffer in shared memory
+    // buffer sizes, used by the bounds-checked debug build (SPIIR_CHECKED)
+    int n_cta_total;
+    int64_t n_pairs_total, x_elems, z_elems, n_segs_total;
 };
 
 struct PersistArgs {

@@ -17,6 +17,7 @@
 // and replayed per chunk.  Plain path: one bank per (bank, band) with its own launches, one
 // upsampling and one coherent launch per bank.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -39,6 +40,8 @@ struct UpArgs {
     int64_t n;                     // full-rate samples
     float2 *z;                     // [nT][n_det][zpitch], written at zoff + k
     int64_t zpitch, zoff;
+    int rows[kMaxBands];           // rows of each zb (bounds-checked debug build)
+    int *status;
 };
 
 __global__ void k_upsample_sum(const __grid_constant__ UpArgs a) {
@@ -49,6 +52,12 @@ __global__ void k_upsample_sum(const __grid_constant__ UpArgs a) {
     for (int b = 0; b < a.n_bands; ++b) {
         const int row = a.rowmap[b][t];
         if (row < 0) continue;
+#ifdef SPIIR_CHECKED
+        if (row >= a.rows[b]) {
+            report_bounds(a.status, 20 + b);
+            continue;
+        }
+#endif
         const float2 *r = a.zb[b] + ((int64_t)row * a.n_det + det) * a.pitch[b];
         const int M = a.M[b];
         float2 v;
@@ -289,15 +298,36 @@ static int run_upsample(spiir_batch_s *B, float2 *const *zb, const int *const *r
     u.z = B->zpad + (int64_t)t0 * B->n_det * B->zpitch;
     u.zpitch = B->zpitch;
     u.zoff = 2 * B->H;
+    u.status = device_status_word();
+    for (int b = 0; b < B->n_bands; ++b) u.rows[b] = (t0 == 0 && nT == B->T) ? B->zb_rows[b] : 1 << 30;
     const unsigned rows = (unsigned)nT * B->n_det;
     k_upsample_sum<<<dim3((unsigned)((B->chunk + 255) / 256), rows), 256, 0, s>>>(u);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }
 
+#ifdef SPIIR_CHECKED
+#define SPIIR_DEBUG_SYNC(what)                                                                   \
+    do {                                                                                         \
+        cudaStreamCaptureStatus cs_ = cudaStreamCaptureStatusNone;                               \
+        cudaStreamIsCapturing(s, &cs_);                                                          \
+        if (cs_ == cudaStreamCaptureStatusNone) {                                                \
+            const cudaError_t e_ = cudaStreamSynchronize(s);                                     \
+            int st_ = 0;                                                                         \
+            cudaMemcpy(&st_, device_status_word(), sizeof(int), cudaMemcpyDeviceToHost);         \
+            fprintf(stderr, "[checked] %s: %s status=0x%x\n", what, cudaGetErrorString(e_), st_); \
+        }                                                                                        \
+    } while (0)
+#else
+#define SPIIR_DEBUG_SYNC(what) \
+    do {                       \
+    } while (0)
+#endif
+
 // Bands without filters anywhere still need a valid (all -1) row map; their zb is unused.
 static int batched_chunk(spiir_batch_s *B, const float *strain, float *ms, int32_t *am, float *nl, cudaStream_t s) {
     SPIIR_TRY(stage_and_decimate(B, strain, s));
+    SPIIR_DEBUG_SYNC("decimate");
     PersistArgs p{};
     size_t smem = 0;
     for (int b = 0; b < B->n_bands; ++b) {
@@ -309,6 +339,7 @@ static int batched_chunk(spiir_batch_s *B, const float *strain, float *ms, int32
                                          (B->M[b] == 1 ? B->chunk : nb) * 4, nb * 4, B->n_det,
                                          cudaMemcpyDeviceToDevice, s));
         p.banks[b] = bank_args(k, B->zb[b] + 1, zb_pitch(B, b), nb);
+        p.banks[b].z_elems = zb_pitch(B, b) * B->zb_rows[b] * B->n_det - 1;
         smem = std::max(smem, bank_smem_bytes(k));
     }
     p.items = B->items;
@@ -316,6 +347,7 @@ static int batched_chunk(spiir_batch_s *B, const float *strain, float *ms, int32
     p.counter = B->counter;
     SPIIR_CUDA_TRY(cudaMemsetAsync(B->counter, 0, sizeof(int), s));
     if (B->n_items > 0) SPIIR_TRY(bank_launch_persistent(p, B->shape_S, B->shape_NL, B->shape_R, B->blocks_per_sm, smem, s));
+    SPIIR_DEBUG_SYNC("persistent filter");
     for (int b = 0; b < B->n_bands; ++b) {
         spiir_bank_s *k = B->band_bank[b];
         if (!k || k->D_pad == 0) continue;
@@ -327,11 +359,17 @@ static int batched_chunk(spiir_batch_s *B, const float *strain, float *ms, int32
         SPIIR_CUDA_TRY(cudaMemcpy2DAsync(x, k->xpitch * 4, tmp, k->xpitch * 4, k->D_pad * 4, B->n_det,
                                          cudaMemcpyDeviceToDevice, s));
     }
+    SPIIR_DEBUG_SYNC("history moves");
     SPIIR_TRY(run_upsample(B, B->zb, B->rowmap, 0, B->T, s));
+    SPIIR_DEBUG_SYNC("upsample");
     for (int b = 0; b < B->n_bands; ++b)
         if (B->band_bank[b]) SPIIR_TRY(band_history(B->zb[b], B->zb_rows[b], B->n_det, band_len(B, b), zb_pitch(B, b), s));
+    SPIIR_DEBUG_SYNC("band history");
     SPIIR_TRY(coherent_scan(B->sky, B->zpad, B->zpitch, B->T, B->chunk, ms, am, nl, nullptr, s));
-    return zpad_history(B, s);
+    SPIIR_DEBUG_SYNC("coherent");
+    const int rz = zpad_history(B, s);
+    SPIIR_DEBUG_SYNC("zpad history");
+    return rz;
 }
 
 static int plain_chunk(spiir_batch_s *B, const float *strain, float *ms, int32_t *am, float *nl, cudaStream_t s) {
@@ -517,10 +555,20 @@ extern "C" int spiir_batch_set_shape(spiir_batch_t B, int filters_per_lane, int 
         spiir_bank_get_shape(k, &oS, &oNL, &oR, &oT);
         const int rc = spiir_bank_set_shape(k, filters_per_lane, lanes_per_block, steps_per_reduce, oT);
         if (rc != SPIIR_OK) {
-            // put back the banks already changed
+            char msg[512];
+            spiir_last_error(msg, sizeof msg);
+            // put back the banks already changed; their device arrays moved, so the work
+            // list is rebuilt and a captured graph dropped
             for (int c = 0; c < b; ++c)
                 if (B->band_bank[c]) spiir_bank_set_shape(B->band_bank[c], B->shape_S, B->shape_NL, B->shape_R, oT);
-            return rc;
+            if (b > 0) {
+                build_items(B);
+                if (B->gexec) {
+                    cudaGraphExecDestroy(B->gexec);
+                    B->gexec = nullptr;
+                }
+            }
+            return fail(rc, "%s", msg);
         }
     }
     B->shape_S = filters_per_lane;

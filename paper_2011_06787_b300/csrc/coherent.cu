@@ -210,6 +210,12 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
             const int64_t lim = a.n + 2 * a.H - k0;
             float *b = pl + I * 4 * W;
             for (int j = tid; j < W; j += TPB) {
+#ifdef SPIIR_CHECKED
+                if (j < lim && k0 + j >= a.pitch) {
+                    report_bounds(a.status, 30);
+                    continue;
+                }
+#endif
                 const float2 v = (j < lim) ? row[j] : make_float2(0.f, 0.f);
                 b[j] = v.x;
                 b[2 * W + j] = v.y;
@@ -314,6 +320,12 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
             }
             if (arg == 0x7fffffff) arg = 0;  // only when every statistic is NaN
             const int64_t o = (int64_t)t * a.n + k0 + k;
+#ifdef SPIIR_CHECKED
+            if (o >= (int64_t)a.n_templates * a.n || arg < 0 || arg >= P) {
+                report_bounds(a.status, 31);
+                continue;
+            }
+#endif
             a.max_stat[o] = best[q];
             a.argmax[o] = arg;
             a.null_stat[o] = nul;
@@ -412,6 +424,7 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         g.argmax = argmax;
         g.null_stat = null_stat;
         g.skymap = skymap;
+        g.status = device_status_word();
         const int tpb = sky->scan_threads, ppt = sky->scan_pairs;
         g.W = 2 * tpb * ppt + 2 * sky->halo + 2;
         if (g.W != sky->g_W) return fail(SPIIR_EINVAL, "internal: plane length mismatch");

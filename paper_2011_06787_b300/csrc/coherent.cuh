@@ -31,6 +31,7 @@ struct GroupedArgs {
     int32_t *argmax;
     float *null_stat;
     float *skymap;
+    int *status;            // bounds-checked debug build only
 };
 
 struct CohArgs {

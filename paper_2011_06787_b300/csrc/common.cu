@@ -117,5 +117,6 @@ extern "C" int spiir_device_status(int clear) {
     SPIIR_CUDA_TRY(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
     if (clear) SPIIR_CUDA_TRY(cudaMemset(w, 0, sizeof(int)));
     if (v & kStatusTimeout) return fail(SPIIR_ETIMEOUT, "a bounded device-side wait gave up");
+    if (v & kStatusBounds) return fail(SPIIR_ECUDA, "bounds check failed (codes 0x%x, checked build)", v >> 8);
     return SPIIR_OK;
 }

@@ -118,4 +118,10 @@ __device__ __forceinline__ void report_timeout(int *status) {
     if (status) atomicOr(status, kStatusTimeout);
 }
 
+// Debug build only: record the first out-of-range index (code in the status word's upper bits).
+constexpr int kStatusBounds = 4;
+__device__ __forceinline__ void report_bounds(int *status, int code) {
+    if (status) atomicOr(status, kStatusBounds | (code << 8));
+}
+
 }  // namespace spiir

@@ -9,7 +9,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libspiir.so")
+# SPIIR_LIB_PATH selects another build of the library (for example a bounds-checked debug build)
+LIB_PATH = os.environ.get("SPIIR_LIB_PATH") or os.path.join(HERE, "_lib", "libspiir.so")
 
 OK, EINVAL, ECUDA, ENOMEM, EUNSUPPORTED, ETIMEOUT = 0, -1, -2, -3, -4, -5
 _NAMES = {EINVAL: "EINVAL", ECUDA: "ECUDA", ENOMEM: "ENOMEM", EUNSUPPORTED: "EUNSUPPORTED", ETIMEOUT: "ETIMEOUT"}

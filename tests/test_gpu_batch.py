@@ -104,3 +104,11 @@ def test_switching_paths_needs_a_reset():
     b.reset()
     b.run(x, ms, am, nl, mode=0)
     assert torch.equal(first, ms)
+
+
+def test_persistent_launch_with_full_blocks_and_short_reduction_blocks():
+    sp, sky, G, d_or, _ = _setup(sub=5)
+    banks = synth.multirate_banks(n_banks=4, t_range=(60, 90), f_range=(60, 70), seed_sub=6)
+    ms, am, nl = _run(sp, sky, banks, 2, 2, shape=(8, 128, 16, 0))
+    ms_or, am_or, nl_or, sm_or = _oracle(banks, G, d_or, sky.halo, 2)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)

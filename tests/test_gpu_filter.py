@@ -192,3 +192,22 @@ def test_shape_rejections_keep_the_bank_usable():
     with pytest.raises(sp.SpiirError):
         b.set_shape(8, 100, 16, 1024)
     assert b.get_shape() == (8, 128, 32, 1024)  # the default for templates of up to 1024 filters
+
+
+@pytest.mark.parametrize("shape", [(8, 128, 16, 1024), (4, 256, 16, 512), (16, 128, 16, 1024)])
+def test_full_blocks_with_short_reduction_blocks(shape):
+    # templates of 8 lanes fill every warp of every block, so the last warp reduces too
+    torch = _torch()
+    import paper_2011_06787_b300 as sp
+    g = synth.rng(0, "misc", 8)
+    S = shape[0]
+    bank = synth.random_bank(g, [8 * S] * 40, d_max=700)
+    x = synth.white_noise(0, 2, 1500, sub=11)
+    b = sp.Bank(2, bank.offsets, bank.a1, bank.b0, bank.delay)
+    b.set_shape(*shape)
+    z = torch.zeros((40, 2, 1500), dtype=torch.complex64, device="cuda")
+    b.filter_chunk(torch.from_numpy(x).cuda(), z)
+    torch.cuda.synchronize()
+    sp.device_status()
+    z_or, _, _ = oracle.filter_bank(x, bank.offsets, bank.a1, bank.b0, bank.delay)
+    assert_snr_close(z.cpu().numpy(), z_or)
