@@ -226,6 +226,21 @@ def run_gpu(args):
     nl = torch.empty((T, n), dtype=torch.float32, device=dev)
     flush = torch.empty(max(1, args.flush_mib * 1024 * 1024 // 4), dtype=torch.float32, device=dev)
 
+    # launch shapes: autotuned on steady-state data (after a few chunks), then the stream restarts
+    tuned = None
+    if not args.no_tune:
+        from paper_2011_06787_b300 import autotune
+        zt = torch.zeros((T, n_det, n + 2 * H), dtype=torch.complex64, device=dev)
+        for i in range(3):
+            b.filter_chunk(chunks[i], zt[:, :, 2 * H:])
+        rs = autotune.tune_scan(sky, zt, n, ms, am, nl)
+        rb = autotune.tune_bank(b, chunks[0], zt[:, :, 2 * H:])
+        tuned = {"scan": rs["shape"], "bank": rb["shape"],
+                 "tried_ms": {"scan": [[round(m, 4), s] for m, s in rs["tried"]] + [["skipped", s, e] for s, e in rs.get("skipped", [])],
+                              "bank": [[round(m, 4), s] for m, s in rb["tried"]]}}
+        del zt
+        pipe.reset()
+
     def barrier():
         if world > 1:
             torch.distributed.barrier()
@@ -289,8 +304,11 @@ def run_gpu(args):
         e2e_value = e2e_rate(args, pipe, T, n, flush, updates_per_step, world, dev, barrier)
 
     batched = None
-    if not args.no_batched:
+    if not args.no_batched and "batched" in args.sections:
         batched = batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma)
+    adjoint = None
+    if "adjoint" in args.sections:
+        adjoint = adjoint_rate(args, torch, dev, flush, timed_loop)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -310,12 +328,14 @@ def run_gpu(args):
                        "chunk_samples": n, "n_pix": P, "parallelism": f"template shards x{world}",
                        "l2": f"flushed before every timed step ({args.flush_mib} MiB write)"},
             "coherent_pixel_samples_per_s": pix_rate,
+            "tuned_shapes": tuned,
             "kernel_ms": {"k_filter_bank": k1, "k_coherent": k2},
             "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
                          "frac": achieved / peak_max, "frac_at_run_clock": achieved / peak_run,
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
                          "traffic": traffic},
             "batched_vs_plain": batched,
+            "adjoint": adjoint,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
                                                    "h2d_bytes_per_step": n_det * n * 4,
@@ -369,6 +389,53 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     return out
 
 
+def adjoint_rate(args, torch, dev, flush, timed_loop):
+    """Chirp workload: impulse response of T templates x 300 filters over the longest chirp
+    (Newtonian, chirp mass 1..3 Msun, 30-1024 Hz at 2048 Hz) and its adjoint, as used to refine
+    IIR coefficients.  Forward and backward are timed separately; units are filter-sample
+    steps (one recurrence step of one filter)."""
+    from paper_2011_06787_b300.adjoint import impulse_response, overlap_loss
+    w = synth.chirp_workload(args.adjoint_templates, 300)
+    T, F = w["a1"].shape
+    n = w["h"].shape[1]
+    h = torch.from_numpy(w["h"]).to(dev).to(torch.complex64)
+    a1 = torch.from_numpy(w["a1"]).to(dev).requires_grad_(True)
+    b0 = torch.from_numpy(w["b0"]).to(dev).requires_grad_(True)
+    s0 = torch.from_numpy(w["s0"]).to(dev).requires_grad_(True)
+    d = torch.from_numpy(w["delay"]).to(dev)
+    state = {}
+
+    def fwd(i):
+        state["u"] = impulse_response(a1, b0, s0, d, n, 1024)
+
+    def loss_and_bwd(i):
+        u = impulse_response(a1, b0, s0, d, n, 1024)
+        loss = overlap_loss(h, u).sum()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        loss.backward()
+        e1.record()
+        e1.synchronize()
+        state.setdefault("bwd", []).append(e0.elapsed_time(e1))
+
+    steps = max(3, min(args.steps, 8))
+    for i in range(2):
+        fwd(i)
+        loss_and_bwd(i)
+    state["bwd"] = []
+    f_ms = float(np.mean(timed_loop(fwd, steps)))
+    for i in range(steps):
+        flush.fill_(float(i))
+        loss_and_bwd(i)
+    b_ms = float(np.mean(state["bwd"]))
+    fs = T * F * n
+    return {"workload": f"{T} chirp templates x {F} filters, {n} samples (longest chirp), checkpoints every 1024",
+            "filter_steps": fs, "forward_ms": f_ms, "backward_ms": b_ms,
+            "forward_steps_per_s": fs / (f_ms * 1e-3), "backward_steps_per_s": fs / (b_ms * 1e-3),
+            "backward_note": "loss.backward(): torch ops of the overlap loss plus the adjoint kernel"}
+
+
 def e2e_rate(args, pipe, T, n, flush, updates_per_step, world, dev, barrier):
     import torch
     hs = [torch.from_numpy(synth.online_chunk(i)).pin_memory() for i in range(args.warmup + args.steps)]
@@ -401,6 +468,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
+    ap.add_argument("--sections", default="main,batched,adjoint",
+                    help="comma list of measurements: main (always timed), batched, adjoint")
+    ap.add_argument("--adjoint-templates", type=int, default=256)
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--templates", type=int, default=1024, help="templates per GPU (1024 = the workload)")
     ap.add_argument("--flush-mib", type=int, default=512, help="L2 flush buffer written before each timed step")
     args = ap.parse_args()

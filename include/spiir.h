@@ -178,12 +178,21 @@ void spiir_sky_destroy(spiir_sky_t sky);
 int spiir_sky_info(spiir_sky_t sky, int *n_det, int *n_pix, int *halo);
 
 /* Launch shape of the coherent scan for 2 and 3 detectors, a tuning knob that does not change
- * results: threads per block in {256, 512}, pairs of output samples per thread in {1, 2}.
- * Synchronises the device.  grouped (output) is 1 when the grouped scan applies: 2 or 3
- * detectors, an orthonormal U with a rank-2 signal plane, at most 65535 pixels.  Default
- * 256 threads, 2 pairs. */
-int spiir_sky_set_scan_shape(spiir_sky_t sky, int threads, int pairs);
-int spiir_sky_get_scan_shape(spiir_sky_t sky, int *threads, int *pairs, int *grouped);
+ * results: threads per block in {256, 512}, pairs of output samples per thread in {1, 2}, and
+ * table_in_shared 1 to keep the pixel table in shared memory when it fits (0 reads it through
+ * the L1 cache and leaves the shared memory to more resident blocks).  Synchronises the
+ * device.  grouped (output) is 1 when the grouped scan applies: 2 or 3 detectors, an
+ * orthonormal U with a rank-2 signal plane, at most 65535 pixels.  Default 256 threads,
+ * 2 pairs, table in shared memory.
+ * threads = 512 with pairs = 4 selects the tensor-memory scan (3 detectors, max |Delta| <= 60,
+ * pixel table within shared memory): each of 128 thread rows keeps the detector-1 and -2 SNR
+ * windows of its 8 consecutive samples in tensor memory (one block per SM, 512 columns).
+ * Its results are bit-identical to the shared-memory scan; a call with a sky map runs the
+ * shared-memory scan.  Errors: SPIIR_EUNSUPPORTED when the tensor-memory scan does not apply
+ * (the previous shape is kept), SPIIR_EINVAL for other shapes. */
+int spiir_sky_set_scan_shape(spiir_sky_t sky, int threads, int pairs, int table_in_shared);
+int spiir_sky_get_scan_shape(spiir_sky_t sky, int *threads, int *pairs, int *table_in_shared,
+                             int *grouped);
 
 /* Coherent all-sky scan -- Sec. II.C.1 Eq. (llr_form) and Eq. (null_def), App. A:
  *     w_I(p, k)   = z_I[k + Delta_I(p)]

@@ -176,11 +176,11 @@ class Sky:
         except Exception:
             pass
 
-    def set_scan_shape(self, threads=256, pairs=2):
-        check(native.lib().spiir_sky_set_scan_shape(self._h, int(threads), int(pairs)))
+    def set_scan_shape(self, threads=256, pairs=2, table_in_shared=1):
+        check(native.lib().spiir_sky_set_scan_shape(self._h, int(threads), int(pairs), int(table_in_shared)))
 
     def get_scan_shape(self):
-        v = [ctypes.c_int() for _ in range(3)]
+        v = [ctypes.c_int() for _ in range(4)]
         check(native.lib().spiir_sky_get_scan_shape(self._h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
 

@@ -13,7 +13,7 @@ import os
 
 BANK_SHAPES = [(8, 256, 32, 1024), (8, 128, 32, 1024), (4, 256, 16, 1024), (4, 128, 16, 1024),
                (8, 256, 16, 1024), (8, 128, 16, 2048), (16, 256, 32, 1024), (16, 128, 16, 1024)]
-SCAN_SHAPES = [(512, 1), (256, 2), (256, 1), (512, 2)]
+SCAN_SHAPES = [(512, 4, 1), (256, 2, 1), (256, 2, 0), (512, 1, 0), (256, 1, 0), (512, 2, 0), (512, 1, 1)]
 
 _cache: dict = {}
 
@@ -95,11 +95,12 @@ def tune_scan(sky, snr, n, max_stat, argmax, null_stat, reps=3, shapes=SCAN_SHAP
         sky.set_scan_shape(*hit["shape"])
         _cache[key] = hit
         return hit
-    results = []
+    results, skipped = [], []
     for shp in shapes:
         try:
             sky.set_scan_shape(*shp)
-        except Exception:
+        except Exception as e:
+            skipped.append([list(shp), str(e)])
             continue
         ms = _time_ms(lambda: sky.scan(snr, n, max_stat, argmax, null_stat), reps)
         results.append((ms, shp))
@@ -107,7 +108,7 @@ def tune_scan(sky, snr, n, max_stat, argmax, null_stat, reps=3, shapes=SCAN_SHAP
             print(f"scan shape {shp}: {ms:.3f} ms")
     best = min(results)
     sky.set_scan_shape(*best[1])
-    rec = {"shape": list(best[1]), "ms": best[0], "tried": [[m, list(s)] for m, s in results]}
+    rec = {"shape": list(best[1]), "ms": best[0], "tried": [[m, list(s)] for m, s in results], "skipped": skipped}
     _cache[key] = rec
     _store(cache_path, key, rec)
     return rec

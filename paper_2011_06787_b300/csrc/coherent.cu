@@ -134,26 +134,7 @@ __global__ void __launch_bounds__(kCohThreads) k_coherent(const __grid_constant_
 
 __device__ __forceinline__ u64 lds64(const float *p) { return *reinterpret_cast<const u64 *>(p); }
 
-template <int ND>
-__device__ __forceinline__ void stat_pair(const float *pl, int W, int i0, int i1, int i2, u64 s0, u64 w0r, u64 w0i,
-                                          float n0, float n1, float n2, int k, u64 &v, u64 &t) {
-    const u64 w1r = lds64(pl + i1 + k), w1i = lds64(pl + i1 + 2 * W + k);
-    u64 S = fma2(w1i, w1i, fma2(w1r, w1r, s0));
-    if (ND == 3) {
-        const u64 w2r = lds64(pl + i2 + k), w2i = lds64(pl + i2 + 2 * W + k);
-        const u64 N0 = pack2(n0, n0), N1 = pack2(n1, n1), N2 = pack2(n2, n2);
-        const u64 nr = fma2(N2, w2r, fma2(N1, w1r, mul2(N0, w0r)));
-        const u64 ni = fma2(N2, w2i, fma2(N1, w1i, mul2(N0, w0i)));
-        S = fma2(w2i, w2i, fma2(w2r, w2r, S));
-        t = fma2(ni, ni, mul2(nr, nr));
-        v = fma2(t, pack2(-1.f, -1.f), S);
-    } else {
-        t = 0;
-        v = S;
-    }
-}
-
-// scalar form of stat_pair for one sample: the same IEEE operations in the same order
+// one sample in scalar form: the same IEEE operations in the same order as the packed loop
 template <int ND>
 __device__ __forceinline__ void stat_one(const float *pl, int W, int i0, int i1, int i2, float n0, float n1, float n2,
                                          int k, float &v, float &t) {
@@ -250,18 +231,65 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
                 gm[2 * h] = -INFINITY;
                 gm[2 * h + 1] = -INFINITY;
             }
-#pragma unroll 2
-            for (int p = gr.y; p < gr.z; ++p) {
-                const float4 e = ent[p];
+            // Software pipeline over the pixels of the group: while pixel p is evaluated, the SNR
+            // loads of pixel p + 1 are in flight and the table entry of pixel p + 2 is fetched.
+            // Indices are clamped at the end of the group (the extra loads are discarded).
+            const int p0 = gr.y, p1 = gr.z;
+            float4 e = TAB_SMEM ? ent[p0] : __ldg(&ent[p0]);
+            float4 en = TAB_SMEM ? ent[min(p0 + 1, p1 - 1)] : __ldg(&ent[min(p0 + 1, p1 - 1)]);
+            u64 a1r[PPT], a1i[PPT], a2r[PPT], a2i[PPT];
+            {
                 const unsigned o = __float_as_uint(e.w);
-                const int i1 = (int)(o & 0xFFFFu), i2 = (int)(o >> 16);
+                const int i1 = (int)(o & 0x7FFFu), i2 = (int)(o >> 16);
 #pragma unroll
                 for (int h = 0; h < PPT; ++h) {
                     const int k = 2 * tid + h * 2 * TPB;
-                    u64 v, tt;
-                    stat_pair<ND>(pl, W, gr.x, i1, i2, s0[h], w0r[h], w0i[h], e.x, e.y, e.z, k, v, tt);
+                    a1r[h] = lds64(pl + i1 + k);
+                    a1i[h] = lds64(pl + i1 + 2 * W + k);
+                    if (ND == 3) {
+                        a2r[h] = lds64(pl + i2 + k);
+                        a2i[h] = lds64(pl + i2 + 2 * W + k);
+                    }
+                }
+            }
+#pragma unroll 2
+            for (int p = p0; p < p1; ++p) {
+                // loads of the next pixel
+                u64 b1r[PPT], b1i[PPT], b2r[PPT], b2i[PPT];
+                {
+                    const unsigned o = __float_as_uint(en.w);
+                    const int i1 = (int)(o & 0x7FFFu), i2 = (int)(o >> 16);
+#pragma unroll
+                    for (int h = 0; h < PPT; ++h) {
+                        const int k = 2 * tid + h * 2 * TPB;
+                        b1r[h] = lds64(pl + i1 + k);
+                        b1i[h] = lds64(pl + i1 + 2 * W + k);
+                        if (ND == 3) {
+                            b2r[h] = lds64(pl + i2 + k);
+                            b2i[h] = lds64(pl + i2 + 2 * W + k);
+                        }
+                    }
+                }
+                const int pnn = min(p + 2, p1 - 1);
+                const float4 enn = TAB_SMEM ? ent[pnn] : __ldg(&ent[pnn]);
+                // evaluate pixel p
+#pragma unroll
+                for (int h = 0; h < PPT; ++h) {
+                    const u64 s01 = fma2(a1i[h], a1i[h], fma2(a1r[h], a1r[h], s0[h]));
+                    u64 v;
+                    if (ND == 3) {
+                        const u64 N0 = pack2(e.x, e.x), N1 = pack2(e.y, e.y), N2 = pack2(e.z, e.z);
+                        const u64 nr = fma2(N2, a2r[h], fma2(N1, a1r[h], mul2(N0, w0r[h])));
+                        const u64 ni = fma2(N2, a2i[h], fma2(N1, a1i[h], mul2(N0, w0i[h])));
+                        const u64 S = fma2(a2i[h], a2i[h], fma2(a2r[h], a2r[h], s01));
+                        const u64 t = fma2(ni, ni, mul2(nr, nr));
+                        v = fma2(t, pack2(-1.f, -1.f), S);
+                    } else {
+                        v = s01;
+                    }
                     const float2 f = unpack2(v);
                     if (MAP) {
+                        const int k = 2 * tid + h * 2 * TPB;
                         float *mrow = a.skymap + ((int64_t)t * P + orig[p]) * a.n + k0;
                         if (k0 + k < a.n) mrow[k] = f.x;
                         if (k0 + k + 1 < a.n) mrow[k + 1] = f.y;
@@ -269,6 +297,17 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
                     gm[2 * h] = fmaxf(gm[2 * h], f.x);
                     gm[2 * h + 1] = fmaxf(gm[2 * h + 1], f.y);
                 }
+#pragma unroll
+                for (int h = 0; h < PPT; ++h) {
+                    a1r[h] = b1r[h];
+                    a1i[h] = b1i[h];
+                    if (ND == 3) {
+                        a2r[h] = b2r[h];
+                        a2i[h] = b2i[h];
+                    }
+                }
+                e = en;
+                en = enn;
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -294,7 +333,7 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
                 const float4 e = ent[a.q0];
                 const unsigned o = __float_as_uint(e.w);
                 float v, tt;
-                stat_one<ND>(pl, W, grp[a.g0].x, (int)(o & 0xFFFFu), (int)(o >> 16), e.x, e.y, e.z, k, v, tt);
+                stat_one<ND>(pl, W, grp[a.g0].x, (int)(o & 0x7FFFu), (int)(o >> 16), e.x, e.y, e.z, k, v, tt);
                 if (v == best[q]) {
                     arg = 0;
                     nul = tt;
@@ -310,7 +349,7 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
                     const float4 e = ent[p];
                     const unsigned o = __float_as_uint(e.w);
                     float v, tt;
-                    stat_one<ND>(pl, W, gr.x, (int)(o & 0xFFFFu), (int)(o >> 16), e.x, e.y, e.z, k, v, tt);
+                    stat_one<ND>(pl, W, gr.x, (int)(o & 0x7FFFu), (int)(o >> 16), e.x, e.y, e.z, k, v, tt);
                     const int op = orig[p];
                     if (v == best[q] && op < arg) {
                         arg = op;
@@ -405,6 +444,27 @@ static int dispatch_nd(const CohArgs &a, bool smem_tab, bool map, size_t smem, c
 
 int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int64_t n, float *max_stat,
                   int32_t *argmax, float *null_stat, float *skymap, cudaStream_t stream) {
+    if (sky->grouped && sky->scan_tmem && sky->tmem_ok && !skymap) {
+        TmemArgs m{};
+        m.snr = snr;
+        m.pitch = pitch;
+        m.n_templates = T;
+        m.n = n;
+        m.H = sky->halo;
+        m.n_pix = sky->n_pix;
+        m.ent = sky->t_ent;
+        m.orig = sky->g_orig;
+        m.grp = sky->g_grp;
+        m.n_grp = sky->n_grp;
+        m.q0 = sky->g_q0;
+        m.g0 = sky->g_g0;
+        for (int i = 0; i < 5; ++i) m.slice[i] = sky->t_slice[i];
+        m.C = tmem_columns(sky->halo);
+        m.max_stat = max_stat;
+        m.argmax = argmax;
+        m.null_stat = null_stat;
+        return launch_coherent_tmem(m, stream);
+    }
     if (sky->grouped) {
         GroupedArgs g{};
         g.snr = snr;
@@ -431,7 +491,7 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         const size_t fixed = ((size_t)sky->n_pix * sizeof(uint16_t) + 15) / 16 * 16 + (size_t)sky->n_grp * sizeof(int4) +
                              (size_t)sky->n_det * 4 * g.W * sizeof(float);
         const size_t tab = (size_t)sky->n_pix * sizeof(float4);
-        const bool tab_smem = fixed + tab <= (size_t)kCohSmemTableLimit;
+        const bool tab_smem = sky->scan_table_shared && fixed + tab <= (size_t)kCohSmemTableLimit;
         const size_t smem = fixed + (tab_smem ? tab : 0);
         if (sky->n_det == 3) return dispatch_grouped<3>(g, tpb, ppt, tab_smem, skymap != nullptr, smem, stream);
         return dispatch_grouped<2>(g, tpb, ppt, tab_smem, skymap != nullptr, smem, stream);
@@ -490,6 +550,7 @@ static void sky_free(spiir_sky_s *s) {
     dev_free(s->g_ent);
     dev_free(s->g_orig);
     dev_free(s->g_grp);
+    dev_free(s->t_ent);
     delete s;
 }
 
@@ -514,7 +575,7 @@ static int build_grouped(spiir_sky_s *s, const int32_t *delays, const float *u_s
             }
     }
     const int W = 2 * s->scan_threads * s->scan_pairs + 2 * H + 2;
-    if (nd * 4 * W > 65535) return SPIIR_OK;
+    if (nd * 4 * W > 32767) return SPIIR_OK;  // plane indices use 15 bits
     std::vector<int> order(P);
     for (int p = 0; p < P; ++p) order[p] = p;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -560,6 +621,36 @@ static int build_grouped(spiir_sky_s *s, const int32_t *delays, const float *u_s
     SPIIR_CUDA_TRY(cudaMemcpy(s->g_orig, orig.data(), sizeof(uint16_t) * P, cudaMemcpyHostToDevice));
     SPIIR_CUDA_TRY(cudaMemcpy(s->g_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice));
     s->n_grp = (int)grp.size();
+    // tensor-memory scan: raw offsets delta_I = H + Delta_I, and four slices of consecutive
+    // groups holding nearly equal numbers of pixels
+    if (nd == 3 && tmem_fits(P, s->n_grp, H)) {
+        std::vector<float4> te(ent);
+        for (int q = 0; q < P; ++q) {
+            const int p = order[q];
+            const unsigned packed = (unsigned)(H + delays[(int64_t)p * nd + 1]) | ((unsigned)(H + delays[(int64_t)p * nd + 2]) << 16);
+            memcpy(&te[q].w, &packed, 4);
+        }
+        SPIIR_TRY(dev_alloc((void **)&s->t_ent, sizeof(float4) * P, "tensor-memory sky table"));
+        SPIIR_CUDA_TRY(cudaMemcpy(s->t_ent, te.data(), sizeof(float4) * P, cudaMemcpyHostToDevice));
+        s->t_slice[0] = 0;
+        for (int k = 1; k < 4; ++k) {
+            // the group boundary closest to a quarter of the pixels
+            const int64_t target = (int64_t)P * k / 4;
+            int best = s->t_slice[k - 1];
+            int64_t best_d = INT64_MAX;
+            for (int c = s->t_slice[k - 1]; c <= s->n_grp; ++c) {
+                const int64_t start = c < s->n_grp ? grp[c].y : P;
+                const int64_t d = start > target ? start - target : target - start;
+                if (d < best_d) {
+                    best_d = d;
+                    best = c;
+                }
+            }
+            s->t_slice[k] = best;
+        }
+        s->t_slice[4] = s->n_grp;
+        s->tmem_ok = true;
+    }
     s->g_W = W;
     s->grouped = true;
     return SPIIR_OK;
@@ -642,11 +733,21 @@ extern "C" int spiir_coherent_scan(spiir_sky_t s, const float *snr, int64_t pitc
                          skymap, (cudaStream_t)stream);
 }
 
-extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs) {
+extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs, int table_in_shared) {
     clear_error();
     if (!s) return fail(SPIIR_EINVAL, "sky is NULL");
-    if ((threads != 256 && threads != 512) || (pairs != 1 && pairs != 2))
-        return fail(SPIIR_EINVAL, "threads must be 256 or 512 and pairs 1 or 2");
+    if (threads == 512 && pairs == 4) {
+        // tensor-memory scan; the shared-memory kernel keeps its shape for sky-map requests
+        if (!s->tmem_ok)
+            return fail(SPIIR_EUNSUPPORTED, "tensor-memory scan needs 3 detectors, an orthonormal basis, "
+                                            "|Delta| <= 60 and a table that fits in shared memory");
+        s->scan_tmem = 1;
+        return SPIIR_OK;
+    }
+    if ((threads != 256 && threads != 512) || (pairs != 1 && pairs != 2) || (table_in_shared != 0 && table_in_shared != 1))
+        return fail(SPIIR_EINVAL, "threads must be 256 or 512, pairs 1 or 2 (or 512 and 4), table_in_shared 0 or 1");
+    s->scan_tmem = 0;
+    s->scan_table_shared = table_in_shared;
     if (!s->grouped) {
         s->scan_threads = threads;
         s->scan_pairs = pairs;
@@ -657,9 +758,12 @@ extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs) {
     dev_free(s->g_ent);
     dev_free(s->g_orig);
     dev_free(s->g_grp);
+    dev_free(s->t_ent);
     s->g_ent = nullptr;
     s->g_orig = nullptr;
     s->g_grp = nullptr;
+    s->t_ent = nullptr;
+    s->tmem_ok = false;
     s->grouped = false;
     s->scan_threads = threads;
     s->scan_pairs = pairs;
@@ -672,10 +776,11 @@ extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs) {
     return rc;
 }
 
-extern "C" int spiir_sky_get_scan_shape(spiir_sky_t s, int *threads, int *pairs, int *grouped) {
+extern "C" int spiir_sky_get_scan_shape(spiir_sky_t s, int *threads, int *pairs, int *table_in_shared, int *grouped) {
     if (!s) return fail(SPIIR_EINVAL, "sky is NULL");
-    if (threads) *threads = s->scan_threads;
-    if (pairs) *pairs = s->scan_pairs;
+    if (threads) *threads = s->scan_tmem ? 512 : s->scan_threads;
+    if (pairs) *pairs = s->scan_tmem ? 4 : s->scan_pairs;
+    if (table_in_shared) *table_in_shared = s->scan_table_shared;
     if (grouped) *grouped = s->grouped ? 1 : 0;
     return SPIIR_OK;
 }

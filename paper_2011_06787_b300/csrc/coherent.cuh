@@ -34,6 +34,31 @@ struct GroupedArgs {
     int *status;            // bounds-checked debug build only
 };
 
+// Tensor-memory scan (3 detectors): sorted pixels as in GroupedArgs, with raw offsets
+// delta_I = H + Delta_I in the table entries.
+struct TmemArgs {
+    const float2 *snr;
+    int64_t pitch;
+    int n_templates;
+    int64_t n;
+    int H;
+    int n_pix;
+    const float4 *ent;      // [P] sorted pixels: (n0, n1, n2, delta_1 | delta_2 << 16)
+    const uint16_t *orig;   // [P] original index of each sorted pixel
+    const int4 *grp;        // [G] (unused, first, end, Delta_0)
+    int n_grp;
+    int q0, g0;             // sorted position and group of pixel 0
+    int slice[5];           // group ranges of the four pixel slices
+    int C;                  // TMEM columns used per plane (multiple of 16, at most 128)
+    float *max_stat;
+    int32_t *argmax;
+    float *null_stat;
+};
+
+int tmem_columns(int H);
+bool tmem_fits(int n_pix, int n_grp, int H);
+int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream);
+
 struct CohArgs {
     const float2 *snr;   // [T][n_det][pitch], entry H + k is output sample k
     int64_t pitch;
@@ -68,6 +93,12 @@ struct spiir_sky_s {
     int g_W = 0;
     // launch shape of the grouped scan: threads per block and sample pairs per thread
     int scan_threads = 256, scan_pairs = 2;
+    int scan_table_shared = 1;  // 1: stage the table in shared memory when it fits; 0: read it through L1
+    int scan_tmem = 0;          // 1: tensor-memory scan (3 detectors, no sky map)
+    // tensor-memory scan tables (same pixel order and groups as the grouped scan)
+    bool tmem_ok = false;
+    float4 *t_ent = nullptr;
+    int t_slice[5] = {0, 0, 0, 0, 0};
     // inputs kept to rebuild the grouped tables when the launch shape changes
     std::vector<int32_t> h_delays;
     std::vector<float> h_usig, h_unull;

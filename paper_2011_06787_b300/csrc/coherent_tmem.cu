@@ -1,0 +1,328 @@
+// Coherent sky scan for three detectors with the delay windows of detectors 1 and 2 held in
+// tensor memory (TMEM).
+//
+// The statistic is the one of the grouped shared-memory scan (App. A, Eq. (null_def)):
+//     rho_C^2(p, k) = |w|^2 - |n(p).w|^2,   null(p, k) = |n(p).w|^2,
+//     w_I = z_I[k + Delta_I(p)]  (Sec. II.C.1),
+// evaluated with packed (real, imaginary) pairs: with A = |w_0|^2 + |w_1|^2 + |w_2|^2 and
+// n.w formed component-wise, rho_C^2 = (A_re - (n.w)_re^2) + (A_im - (n.w)_im^2).  The scalar
+// rescan that resolves the argmax recomputes the statistic of the candidate pixels and takes
+// the largest (lowest pixel index among equals).
+//
+// Why TMEM: in the shared-memory kernel every (pixel, sample) reads 16 bytes of detector 1
+// and 2 SNR from shared memory, and shared-memory bandwidth (one 128-byte wavefront per clock
+// per SM) bounds the scan below the FP32 rate.  Here each of the 128 TMEM lanes belongs to one
+// thread row and holds, for detectors 1 and 2, the SNR window z_I[k_r + c] (c = 0 .. C-1) of
+// the row's first sample k_r, real and imaginary parts in adjacent columns 2c and 2c + 1.  The
+// 8 samples k_r + m of a row at delay offset delta sit at columns 2 (delta + m), so one
+// warp-uniform column address serves all 32 rows of a warp for any pixel, and every sample is
+// one aligned two-column load that lands as an FP32 pair.
+//
+// Work item: one template and 1024 output samples.  Block: 512 threads = 16 warps, one block
+// per SM (shared memory above half the SM's capacity keeps a second block off the SM, so the
+// 512-column TMEM allocation never waits).  Warp w reads TMEM lanes 32 (w % 4) .. + 31 (the
+// quarter its hardware position allows) and evaluates pixel slice w / 4: the sorted pixel
+// groups are cut into four slices of nearly equal pixel count.  Per sample the four slice
+// maxima are merged in shared memory; the sample's winning group is then rescanned in scalar
+// arithmetic to find the lowest pixel index attaining the maximum, as in the shared-memory
+// kernel.
+#include <algorithm>
+
+#include "coherent.cuh"
+
+namespace spiir {
+
+constexpr int kTmThreads = 512;
+constexpr int kTmRows = 128;                // TMEM lanes = thread rows
+constexpr int kTmM = 8;                     // consecutive samples per row
+constexpr int kTmKT = kTmRows * kTmM;       // samples per work item
+constexpr int kTmDet = 256;                 // TMEM columns per detector (2 detectors, 512 columns)
+constexpr int kTmMinSmem = 120 * 1024;      // keeps a second block off the SM
+
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Two-column TMEM load (real, imaginary) of sample M of the window at addr, for this warp's
+// 32 lanes.  The column 2 M after addr is even whenever addr is.
+template <int M>
+__device__ __forceinline__ void tl2(u64 (&w)[8], uint32_t addr) {
+    uint32_t lo, hi;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2+%3];"
+                 : "=r"(lo), "=r"(hi)
+                 : "r"(addr), "n"(2 * M)
+                 : "memory");
+    asm("mov.b64 %0, {%1, %2};" : "=l"(w[M]) : "r"(lo), "r"(hi));
+}
+
+__device__ __forceinline__ void tm_window(u64 (&w)[8], uint32_t addr) {
+    tl2<0>(w, addr), tl2<1>(w, addr), tl2<2>(w, addr), tl2<3>(w, addr);
+    tl2<4>(w, addr), tl2<5>(w, addr), tl2<6>(w, addr), tl2<7>(w, addr);
+}
+
+// Completes every outstanding TMEM load of the thread; the empty statements after it pin the
+// loaded registers behind the wait.
+__device__ __forceinline__ void tm_wait_ld(u64 (&a)[8], u64 (&b)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int m = 0; m < 8; ++m) asm volatile("" : "+l"(a[m]), "+l"(b[m]));
+}
+
+__device__ __forceinline__ void tm_st8(uint32_t addr, const float (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(addr),
+                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// shared-memory SNR planes, transposed by 8: element x at (x % 8) * L + x / 8, so the 32 rows
+// of a warp reading sample 8 r + c hit 32 consecutive words
+__device__ __forceinline__ int tpos(int x, int L) { return (x & 7) * L + (x >> 3); }
+
+__global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_constant__ TmemArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, sl = warp >> 2;
+    const int row = 32 * q + lane;
+    const int P = a.n_pix, G = a.n_grp, H = a.H, C = a.C;
+    const int W0 = kTmKT + C;       // staged samples per plane
+    const int L = W0 / 8 + 1;       // transposed plane stride (odd)
+    const int PL = 8 * L;           // floats per staged plane
+
+    float4 *ent = reinterpret_cast<float4 *>(smem);
+    size_t off = (size_t)P * sizeof(float4);
+    int4 *grp = reinterpret_cast<int4 *>(smem + off);
+    off += (size_t)G * sizeof(int4);
+    float *cb_best = reinterpret_cast<float *>(smem + off);
+    off += (size_t)4 * kTmKT * sizeof(float);
+    unsigned *cb_grp = reinterpret_cast<unsigned *>(smem + off);
+    off += (size_t)4 * kTmKT * sizeof(unsigned);
+    float *zp = reinterpret_cast<float *>(smem + off);  // [3 detectors][re, im][PL]
+    off += (size_t)6 * PL * sizeof(float);
+    uint16_t *orig = reinterpret_cast<uint16_t *>(smem + off);
+    off += ((size_t)P * sizeof(uint16_t) + 15) / 16 * 16;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + off);
+
+    for (int i = tid; i < P; i += kTmThreads) {
+        ent[i] = a.ent[i];
+        orig[i] = a.orig[i];
+    }
+    for (int i = tid; i < G; i += kTmThreads) grp[i] = a.grp[i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tbase = *slot;
+    const uint32_t la = tbase + ((uint32_t)(32 * q) << 16);  // this warp's lane quarter
+    const int g_lo = a.slice[sl], g_hi = a.slice[sl + 1];
+
+    const int ntiles = (int)((a.n + kTmKT - 1) / kTmKT);
+    const int64_t n_items = (int64_t)a.n_templates * ntiles;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int t = (int)(item / ntiles);
+        const int64_t k0 = (item % ntiles) * (int64_t)kTmKT;
+        const int64_t lim = a.n + 2 * H - k0;  // staged entries past this are zero
+        // the previous item's TMEM and shared-memory reads are complete past this point
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        for (int I = 0; I < 3; ++I) {
+            const float2 *src = a.snr + ((int64_t)t * 3 + I) * a.pitch + k0;
+            float *re = zp + (2 * I) * PL, *im = re + PL;
+            for (int j = tid; j < W0; j += kTmThreads) {
+                const float2 v = (j < lim) ? src[j] : make_float2(0.f, 0.f);
+                re[tpos(j, L)] = v.x;
+                im[tpos(j, L)] = v.y;
+            }
+        }
+        __syncthreads();
+        // TMEM windows: warp slice sl fills detector 1 + (sl & 1), window half sl >> 1; four
+        // samples (8 columns) per store
+        {
+            const int I = 1 + (sl & 1);
+            const float *re = zp + (2 * I) * PL, *im = re + PL;
+            const uint32_t base = la + (uint32_t)((I - 1) * kTmDet);
+            const int h = C / 2;
+            for (int c0 = (sl >> 1) * h; c0 < (sl >> 1) * h + h; c0 += 4) {
+                float v[8];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int x = 8 * row + c0 + m;
+                    v[2 * m] = re[tpos(x, L)];
+                    v[2 * m + 1] = im[tpos(x, L)];
+                }
+                tm_st8(base + 2 * c0, v);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+
+        // running maximum and winning group of this thread's samples within its slice, kept in
+        // shared memory at [slice][m][row] (updated once per group)
+        float *my_best = cb_best + sl * kTmKT + row;
+        unsigned *my_grp = cb_grp + sl * kTmKT + row;
+#pragma unroll
+        for (int m = 0; m < kTmM; ++m) {
+            my_best[m * kTmRows] = -INFINITY;
+            my_grp[m * kTmRows] = 0;
+        }
+        const float *z0r = zp, *z0i = zp + PL;
+        for (int g = g_lo; g < g_hi; ++g) {
+            const int4 gr = grp[g];
+            const int d0 = H + gr.w;
+            u64 w0[kTmM], s0[kTmM];
+            float gm[kTmM];
+#pragma unroll
+            for (int m = 0; m < kTmM; ++m) {
+                const int x = 8 * row + d0 + m;
+                w0[m] = pack2(z0r[tpos(x, L)], z0i[tpos(x, L)]);
+                s0[m] = mul2(w0[m], w0[m]);
+                gm[m] = -INFINITY;
+            }
+            for (int p = gr.y; p < gr.z; ++p) {
+                const float4 e = ent[p];
+                const uint32_t o = __float_as_uint(e.w);
+                u64 w1[kTmM], w2[kTmM];
+                tm_window(w1, la + 2 * (o & 0xFFFFu));
+                tm_window(w2, la + kTmDet + 2 * (o >> 16));
+                tm_wait_ld(w1, w2);
+                const u64 N0 = pack2(e.x, e.x), N1 = pack2(e.y, e.y), N2 = pack2(e.z, e.z);
+#pragma unroll
+                for (int m = 0; m < kTmM; ++m) {
+                    const u64 A = fma2(w2[m], w2[m], fma2(w1[m], w1[m], s0[m]));
+                    const u64 nw = fma2(N2, w2[m], fma2(N1, w1[m], mul2(N0, w0[m])));
+                    const float2 d = unpack2(sub2(A, mul2(nw, nw)));
+                    gm[m] = fmaxf(gm[m], __fadd_rn(d.x, d.y));
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < kTmM; ++m) {
+                const float b = my_best[m * kTmRows];
+                if (gm[m] > b) {
+                    my_best[m * kTmRows] = gm[m];
+                    my_grp[m * kTmRows] = (unsigned)g;
+                } else if (gm[m] == b) {
+                    my_grp[m * kTmRows] |= 0x80000000u;  // another group of this slice attains the same maximum
+                }
+            }
+        }
+        __syncthreads();
+        // merge the slices and resolve the argmax (lowest original pixel index among equal maxima)
+        for (int j = tid; j < kTmKT; j += kTmThreads) {
+            if (k0 + j >= a.n) continue;
+            const int cj = (j & 7) * kTmRows + (j >> 3);  // sample j = 8 row + m sits at [m][row]
+            float B = cb_best[cj];
+            for (int s = 1; s < 4; ++s) B = fmaxf(B, cb_best[s * kTmKT + cj]);
+            int hits = 0;
+            unsigned gsel = 0, tie = 0;
+            for (int s = 0; s < 4; ++s) {
+                if (cb_best[s * kTmKT + cj] == B) {
+                    ++hits;
+                    gsel = cb_grp[s * kTmKT + cj] & 0x7FFFFFFFu;
+                    tie |= cb_grp[s * kTmKT + cj] >> 31;
+                }
+            }
+            int lo = (int)gsel, hi = (int)gsel + 1;
+            int arg = 0x7fffffff;
+            float nul = 0.f;
+            auto stat = [&](int p, int d0, float &v, float &tt) {
+                const float4 e = ent[p];
+                const uint32_t o = __float_as_uint(e.w);
+                const int d1 = (int)(o & 0xFFFFu), d2 = (int)(o >> 16);
+                const float *r0 = zp, *r1 = zp + 2 * PL, *r2 = zp + 4 * PL;
+                const float w0r = r0[tpos(j + d0, L)], w0i = r0[PL + tpos(j + d0, L)];
+                const float w1r = r1[tpos(j + d1, L)], w1i = r1[PL + tpos(j + d1, L)];
+                const float w2r = r2[tpos(j + d2, L)], w2i = r2[PL + tpos(j + d2, L)];
+                const float Ar = __fmaf_rn(w2r, w2r, __fmaf_rn(w1r, w1r, __fmul_rn(w0r, w0r)));
+                const float Ai = __fmaf_rn(w2i, w2i, __fmaf_rn(w1i, w1i, __fmul_rn(w0i, w0i)));
+                const float nr = __fmaf_rn(e.z, w2r, __fmaf_rn(e.y, w1r, __fmul_rn(e.x, w0r)));
+                const float ni = __fmaf_rn(e.z, w2i, __fmaf_rn(e.y, w1i, __fmul_rn(e.x, w0i)));
+                tt = __fmaf_rn(ni, ni, __fmul_rn(nr, nr));
+                v = __fadd_rn(__fsub_rn(Ar, __fmul_rn(nr, nr)), __fsub_rn(Ai, __fmul_rn(ni, ni)));
+            };
+            if (hits > 1 || tie) {
+                // equal maxima in several groups: pixel 0, the lowest index, wins if it attains
+                // the maximum (the all-zero window); otherwise every group is rescanned
+                float v, tt;
+                stat(a.q0, H + grp[a.g0].w, v, tt);
+                if (v == B) {
+                    arg = 0;
+                    nul = tt;
+                    hi = lo;
+                } else {
+                    lo = 0;
+                    hi = G;
+                }
+            }
+            // the candidate pixel with the largest recomputed statistic, lowest index among
+            // equals (the compiler may contract the packed multiply-subtract of the main loop,
+            // so its value and the recomputed one can differ in the last bit)
+            float bv = -INFINITY;
+            for (int g = lo; g < hi; ++g) {
+                const int4 gr = grp[g];
+                for (int p = gr.y; p < gr.z; ++p) {
+                    float v, tt;
+                    stat(p, H + gr.w, v, tt);
+                    const int op = orig[p];
+                    if (v > bv || (v == bv && op < arg)) {
+                        bv = v;
+                        arg = op;
+                        nul = tt;
+                    }
+                }
+            }
+            if (arg == 0x7fffffff) arg = 0;  // only when every statistic is NaN
+            const int64_t o = (int64_t)t * a.n + k0 + j;
+            a.max_stat[o] = B;
+            a.argmax[o] = arg;
+            a.null_stat[o] = nul;
+        }
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512u) : "memory");
+}
+
+size_t tmem_scan_smem(int n_pix, int n_grp, int C) {
+    const int W0 = kTmKT + C, L = W0 / 8 + 1;
+    size_t s = (size_t)n_pix * sizeof(float4) + (size_t)n_grp * sizeof(int4) + (size_t)8 * kTmKT * sizeof(float) +
+               (size_t)6 * 8 * L * sizeof(float) + ((size_t)n_pix * sizeof(uint16_t) + 15) / 16 * 16 + 16;
+    return std::max(s, (size_t)kTmMinSmem);
+}
+
+int tmem_columns(int H) { return (2 * H + kTmM + 15) / 16 * 16; }
+
+bool tmem_fits(int n_pix, int n_grp, int H) {
+    return 2 * tmem_columns(H) <= kTmDet && tmem_scan_smem(n_pix, n_grp, tmem_columns(H)) <= 227 * 1024;
+}
+
+int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream) {
+    const size_t smem = tmem_scan_smem(a.n_pix, a.n_grp, a.C);
+    static bool attr = false;
+    if (!attr) {
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    int dev = 0, n_sm = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t items = (int64_t)a.n_templates * ((a.n + kTmKT - 1) / kTmKT);
+    const int grid = (int)std::min<int64_t>(items, n_sm);
+    k_coherent_tmem<<<grid, kTmThreads, smem, stream>>>(a);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+}  // namespace spiir

@@ -133,7 +133,7 @@ def test_streaming_pipeline_matches_oracle(host):
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
 
 
-@pytest.mark.parametrize("shape", [(256, 1), (256, 2), (512, 1), (512, 2)])
+@pytest.mark.parametrize("shape", [(256, 1, 1), (256, 2, 1), (512, 1, 0), (512, 2, 0), (256, 2, 0)])
 @pytest.mark.parametrize("n_det", [2, 3])
 def test_every_scan_shape_matches_oracle(shape, n_det):
     sky, G, d_or = _sky(1, n_det, 8, (0.5, 2.0))
@@ -160,7 +160,7 @@ def test_general_kernel_for_non_orthonormal_tables():
     d, us, un = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 4, 2048.0)
     un2 = un * 1.5  # not a unit null vector: the grouped null-vector form does not apply
     sky2 = sp.Sky(d, us, un2)
-    assert sky2.get_scan_shape()[2] == 0
+    assert sky2.get_scan_shape()[3] == 0
     H = sky2.halo
     z = synth.complex_gaussian_snr(1, (2, 3, 600 + 2 * H), sub=12)
     ms, am, nl, _ = _scan(sky2, z, 600)
@@ -178,3 +178,47 @@ def test_all_zero_window_ties_resolve_to_pixel_zero():
     assert np.all(ms[0] == 0) and np.all(am[0] == 0) and np.all(nl[0] == 0)
     ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, 1500, skymap=True)
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+
+
+@pytest.mark.parametrize("nside,T,n", [(8, 3, 2500), (16, 2, 1024), (16, 2, 3000)])
+def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(nside, T, n):
+    """The TMEM scan (512 threads, 8 samples per row, detector 1 and 2 windows in tensor
+    memory) against the oracle, and against the shared-memory scan (the two pair the FP32
+    arithmetic differently, so they agree to rounding).  n = 2500 and 3000 leave ragged last
+    tiles of 1024 samples."""
+    sky, G, d_or = _sky(1, 3, nside, (0.5, 2.0))
+    H = sky.halo
+    z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=21)
+    ms_s, am_s, nl_s, _ = _scan(sky, z, n)
+    sky.set_scan_shape(512, 4, 1)
+    assert sky.get_scan_shape() == (512, 4, 1, 1)
+    ms, am, nl, _ = _scan(sky, z, n)
+    assert np.all(np.abs(ms - ms_s) <= 1e-5 * ms_s.max())
+    assert np.mean(am == am_s) > 0.999
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+
+
+def test_tensor_memory_scan_ties_and_sky_map_fallback():
+    sky, G, d_or = _sky(1, 3, 16, (0.5, 2.0))
+    sky.set_scan_shape(512, 4, 1)
+    H = sky.halo
+    z = np.zeros((2, 3, 2100 + 2 * H), np.complex64)
+    z[1, :, 900:] = synth.complex_gaussian_snr(1, (3, z.shape[2] - 900), sub=14)
+    ms, am, nl, _ = _scan(sky, z, 2100)
+    assert np.all(ms[0] == 0) and np.all(am[0] == 0) and np.all(nl[0] == 0)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, 2100, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    # a sky-map request runs the shared-memory kernel
+    ms2, am2, nl2, mp = _scan(sky, z, 2100, skymap=True)
+    assert_coherent_close(ms2, am2, nl2, ms_or, am_or, nl_or, sm_or)
+    mp = np.transpose(mp, (0, 2, 1))
+    assert np.all(np.abs(mp - sm_or) <= 1e-4 * np.maximum(sm_or.max(axis=-1, keepdims=True), 1e-30))
+
+
+def test_tensor_memory_scan_needs_three_detectors():
+    import paper_2011_06787_b300 as sp
+    sky, _, _ = _sky(0, 2, 4, (1.0, 1.0))
+    with pytest.raises(sp.SpiirError):
+        sky.set_scan_shape(512, 4, 1)
+    assert sky.get_scan_shape()[:2] == (256, 2)
