@@ -228,7 +228,13 @@ def run_gpu(args):
 
     # launch shapes: autotuned on steady-state data (after a few chunks), then the stream restarts
     tuned = None
-    if not args.no_tune:
+    if args.scan_shape:
+        sky.set_scan_shape(*[int(x) for x in args.scan_shape.split(",")])
+    if args.bank_shape:
+        b.set_shape(*[int(x) for x in args.bank_shape.split(",")])
+    if args.scan_shape or args.bank_shape:
+        tuned = {"scan": list(sky.get_scan_shape()[:3]), "bank": list(b.get_shape()), "fixed": True}
+    elif not args.no_tune:
         from paper_2011_06787_b300 import autotune
         zt = torch.zeros((T, n_det, n + 2 * H), dtype=torch.complex64, device=dev)
         for i in range(3):
@@ -290,8 +296,14 @@ def run_gpu(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_max = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12          # TFLOP/s at max clock
     peak_run = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    if tuple(sky.get_scan_shape()[:2]) == (512, 4):
+        coh_name, coh_src = "k_coherent_tmem", ["paper_2011_06787_b300/csrc/coherent_tmem.cu",
+                                                "paper_2011_06787_b300/csrc/coherent.cuh"]
+    else:
+        coh_name, coh_src = "k_coherent_grouped", ["paper_2011_06787_b300/csrc/coherent.cu",
+                                                   "paper_2011_06787_b300/csrc/coherent.cuh"]
     if k2 >= k1:
-        kern, src = "k_coherent", ["paper_2011_06787_b300/csrc/coherent.cu", "paper_2011_06787_b300/csrc/coherent.cuh"]
+        kern, src = coh_name, coh_src
         achieved = k2_flops_per_pixel_sample(n_det) * pix_per_step / (k2 * 1e-3) / 1e12
     else:
         kern, src = "k_filter_bank", ["paper_2011_06787_b300/csrc/bank.cu", "paper_2011_06787_b300/csrc/bank.cuh"]
@@ -309,6 +321,9 @@ def run_gpu(args):
     adjoint = None
     if "adjoint" in args.sections:
         adjoint = adjoint_rate(args, torch, dev, flush, timed_loop)
+    skymap = None
+    if "skymap" in args.sections:
+        skymap = skymap_rate(args, torch, sky, zbuf, n, ms, am, nl, timed_loop)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -329,13 +344,14 @@ def run_gpu(args):
                        "l2": f"flushed before every timed step ({args.flush_mib} MiB write)"},
             "coherent_pixel_samples_per_s": pix_rate,
             "tuned_shapes": tuned,
-            "kernel_ms": {"k_filter_bank": k1, "k_coherent": k2},
+            "kernel_ms": {"k_filter_bank": k1, coh_name: k2},
             "roofline": {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
                          "frac": achieved / peak_max, "frac_at_run_clock": achieved / peak_run,
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
                          "traffic": traffic},
             "batched_vs_plain": batched,
             "adjoint": adjoint,
+            "skymap": skymap,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
                                                    "h2d_bytes_per_step": n_det * n * 4,
@@ -387,6 +403,29 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     out["kernel_launches_per_chunk"] = {"plain": 1 + sum(1 for b in banks for k in range(3) if np.any(b[4] == k)) +
                                         2 * len(banks), "batched": 4}
     return out
+
+
+def skymap_rate(args, torch, sky, zbuf, n, ms, am, nl, timed_loop):
+    """Coherent scan in sky-map mode: the statistic of every (template, pixel, sample) is
+    written to HBM ([T][P][n] f32; 25.8 GB for the online workload), so the HBM roofline
+    applies.  Bytes per launch: the map, the SNR read and the three per-sample outputs."""
+    T, n_det, pitch = zbuf.shape
+    P = sky.n_pix
+    smap = torch.empty((T, P, n), dtype=torch.float32, device=zbuf.device)
+    steps = max(3, min(args.steps, 8))
+    sky.scan(zbuf, n, ms, am, nl, smap)
+    t = timed_loop(lambda i: sky.scan(zbuf, n, ms, am, nl, smap), steps)
+    t_ms = float(np.mean(t))
+    map_bytes = T * P * n * 4
+    total = map_bytes + T * n_det * pitch * 8 + T * n * 12
+    peak = measured_peaks().get("hbm_gbs")
+    gbs = total / (t_ms * 1e-3) / 1e9
+    del smap
+    torch.cuda.empty_cache()
+    return {"workload": f"{T} templates x {n} samples x {P} pixels, map [T][P][n] f32", "steps": steps,
+            "ms": t_ms, "pixel_samples_per_s": T * P * n / (t_ms * 1e-3), "map_bytes": map_bytes,
+            "bytes_per_launch": total, "achieved_gbs": gbs, "hbm_peak_gbs": peak,
+            "frac_of_measured_hbm": (gbs / peak) if peak else None}
 
 
 def adjoint_rate(args, torch, dev, flush, timed_loop):
@@ -468,10 +507,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
-    ap.add_argument("--sections", default="main,batched,adjoint",
-                    help="comma list of measurements: main (always timed), batched, adjoint")
+    ap.add_argument("--sections", default="main,batched,adjoint,skymap",
+                    help="comma list of measurements: main (always timed), batched, adjoint, skymap")
     ap.add_argument("--adjoint-templates", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--scan-shape", default="", help="fixed coherent-scan shape threads,pairs,table (no autotuning)")
+    ap.add_argument("--bank-shape", default="", help="fixed filter-bank shape S,NL,R,tile (no autotuning)")
     ap.add_argument("--templates", type=int, default=1024, help="templates per GPU (1024 = the workload)")
     ap.add_argument("--flush-mib", type=int, default=512, help="L2 flush buffer written before each timed step")
     args = ap.parse_args()

@@ -187,9 +187,10 @@ int spiir_sky_info(spiir_sky_t sky, int *n_det, int *n_pix, int *halo);
  * threads = 512 with pairs = 4 selects the tensor-memory scan (3 detectors, max |Delta| <= 60,
  * pixel table within shared memory): each of 128 thread rows keeps the detector-1 and -2 SNR
  * windows of its 8 consecutive samples in tensor memory (one block per SM, 512 columns).
- * Its results are bit-identical to the shared-memory scan; a call with a sky map runs the
- * shared-memory scan.  Errors: SPIIR_EUNSUPPORTED when the tensor-memory scan does not apply
- * (the previous shape is kept), SPIIR_EINVAL for other shapes. */
+ * It pairs the FP32 arithmetic differently from the shared-memory scan, so the two agree to
+ * rounding; with a sky map each thread writes its 8 samples of a pixel as one 32-byte segment.
+ * Errors: SPIIR_EUNSUPPORTED when the tensor-memory scan does not apply (the previous shape is
+ * kept), SPIIR_EINVAL for other shapes. */
 int spiir_sky_set_scan_shape(spiir_sky_t sky, int threads, int pairs, int table_in_shared);
 int spiir_sky_get_scan_shape(spiir_sky_t sky, int *threads, int *pairs, int *table_in_shared,
                              int *grouped);

@@ -444,7 +444,7 @@ static int dispatch_nd(const CohArgs &a, bool smem_tab, bool map, size_t smem, c
 
 int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int64_t n, float *max_stat,
                   int32_t *argmax, float *null_stat, float *skymap, cudaStream_t stream) {
-    if (sky->grouped && sky->scan_tmem && sky->tmem_ok && !skymap) {
+    if (sky->grouped && sky->scan_tmem && sky->tmem_ok) {
         TmemArgs m{};
         m.snr = snr;
         m.pitch = pitch;
@@ -463,6 +463,8 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         m.max_stat = max_stat;
         m.argmax = argmax;
         m.null_stat = null_stat;
+        m.skymap = skymap;
+        m.map_vec = (n % 4 == 0 && ((uintptr_t)skymap % 16) == 0) ? 1 : 0;
         return launch_coherent_tmem(m, stream);
     }
     if (sky->grouped) {

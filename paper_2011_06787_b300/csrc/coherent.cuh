@@ -53,6 +53,8 @@ struct TmemArgs {
     float *max_stat;
     int32_t *argmax;
     float *null_stat;
+    float *skymap;          // NULL or [T][P][n]
+    int map_vec;            // 1: n % 4 == 0 and skymap 16-byte aligned (vector stores)
 };
 
 int tmem_columns(int H);

@@ -25,7 +25,9 @@
 // groups are cut into four slices of nearly equal pixel count.  Per sample the four slice
 // maxima are merged in shared memory; the sample's winning group is then rescanned in scalar
 // arithmetic to find the lowest pixel index attaining the maximum, as in the shared-memory
-// kernel.
+// kernel.  In sky-map mode every row also writes its 8 statistics of each pixel to
+// map[t][p][k] (two 16-byte streaming stores), which overlaps the map's HBM writes with the
+// arithmetic.
 #include <algorithm>
 
 #include "coherent.cuh"
@@ -83,6 +85,7 @@ __device__ __forceinline__ u64 sub2(u64 a, u64 b) {
 // of a warp reading sample 8 r + c hit 32 consecutive words
 __device__ __forceinline__ int tpos(int x, int L) { return (x & 7) * L + (x >> 3); }
 
+template <bool MAP>
 __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_constant__ TmemArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -198,12 +201,28 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_co
                 tm_window(w2, la + kTmDet + 2 * (o >> 16));
                 tm_wait_ld(w1, w2);
                 const u64 N0 = pack2(e.x, e.x), N1 = pack2(e.y, e.y), N2 = pack2(e.z, e.z);
+                float v[kTmM];
 #pragma unroll
                 for (int m = 0; m < kTmM; ++m) {
                     const u64 A = fma2(w2[m], w2[m], fma2(w1[m], w1[m], s0[m]));
                     const u64 nw = fma2(N2, w2[m], fma2(N1, w1[m], mul2(N0, w0[m])));
                     const float2 d = unpack2(sub2(A, mul2(nw, nw)));
-                    gm[m] = fmaxf(gm[m], __fadd_rn(d.x, d.y));
+                    v[m] = __fadd_rn(d.x, d.y);
+                    gm[m] = fmaxf(gm[m], v[m]);
+                }
+                if (MAP) {
+                    // the row's 8 samples of this pixel: one contiguous 1 KB segment per warp,
+                    // written with the streaming (evict-first) hint
+                    const int64_t kr = k0 + 8 * row;
+                    float *mrow = a.skymap + ((int64_t)t * P + orig[p]) * a.n + kr;
+                    if (a.map_vec && kr + kTmM <= a.n) {
+                        __stcs(reinterpret_cast<float4 *>(mrow), make_float4(v[0], v[1], v[2], v[3]));
+                        __stcs(reinterpret_cast<float4 *>(mrow) + 1, make_float4(v[4], v[5], v[6], v[7]));
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < kTmM; ++m)
+                            if (kr + m < a.n) __stcs(mrow + m, v[m]);
+                    }
                 }
             }
 #pragma unroll
@@ -312,7 +331,8 @@ int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream) {
     const size_t smem = tmem_scan_smem(a.n_pix, a.n_grp, a.C);
     static bool attr = false;
     if (!attr) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
     int dev = 0, n_sm = 0;
@@ -320,7 +340,10 @@ int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream) {
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int64_t items = (int64_t)a.n_templates * ((a.n + kTmKT - 1) / kTmKT);
     const int grid = (int)std::min<int64_t>(items, n_sm);
-    k_coherent_tmem<<<grid, kTmThreads, smem, stream>>>(a);
+    if (a.skymap)
+        k_coherent_tmem<true><<<grid, kTmThreads, smem, stream>>>(a);
+    else
+        k_coherent_tmem<false><<<grid, kTmThreads, smem, stream>>>(a);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }

@@ -133,9 +133,11 @@ def test_streaming_pipeline_matches_oracle(host):
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
 
 
-@pytest.mark.parametrize("shape", [(256, 1, 1), (256, 2, 1), (512, 1, 0), (512, 2, 0), (256, 2, 0)])
+@pytest.mark.parametrize("shape", [(256, 1, 1), (256, 2, 1), (512, 1, 0), (512, 2, 0), (256, 2, 0), (512, 4, 1)])
 @pytest.mark.parametrize("n_det", [2, 3])
 def test_every_scan_shape_matches_oracle(shape, n_det):
+    if shape[1] == 4 and n_det == 2:
+        pytest.skip("the tensor-memory scan is for three detectors")
     sky, G, d_or = _sky(1, n_det, 8, (0.5, 2.0))
     sky.set_scan_shape(*shape)
     assert sky.get_scan_shape() == shape + (1,)
@@ -199,7 +201,7 @@ def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(nside, T, n):
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
 
 
-def test_tensor_memory_scan_ties_and_sky_map_fallback():
+def test_tensor_memory_scan_ties_and_sky_map():
     sky, G, d_or = _sky(1, 3, 16, (0.5, 2.0))
     sky.set_scan_shape(512, 4, 1)
     H = sky.halo
@@ -209,7 +211,7 @@ def test_tensor_memory_scan_ties_and_sky_map_fallback():
     assert np.all(ms[0] == 0) and np.all(am[0] == 0) and np.all(nl[0] == 0)
     ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, 2100, skymap=True)
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
-    # a sky-map request runs the shared-memory kernel
+    # with a sky map (n = 2100: vector stores, a ragged last tile)
     ms2, am2, nl2, mp = _scan(sky, z, 2100, skymap=True)
     assert_coherent_close(ms2, am2, nl2, ms_or, am_or, nl_or, sm_or)
     mp = np.transpose(mp, (0, 2, 1))
@@ -222,3 +224,53 @@ def test_tensor_memory_scan_needs_three_detectors():
     with pytest.raises(sp.SpiirError):
         sky.set_scan_shape(512, 4, 1)
     assert sky.get_scan_shape()[:2] == (256, 2)
+
+
+def test_online_full_size_pipeline_sampled_templates():
+    """The full online workload (1024 templates, 3 detectors, nside 16) streamed through the
+    pipeline in the benchmark's launch configuration (tensor-memory scan, 8 filters x 128
+    lanes); the oracle recomputes a sample of templates, which are independent."""
+    import torch
+    import paper_2011_06787_b300 as sp
+    w = synth.online_workload()
+    c, det, bank, sigma = w["cfg"], w["det"], w["bank"], w["sigma"]
+    sky = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, c["nside"], 2048.0))
+    _, G, d_or = oracle.sky_geometry(det, sigma, c["nside"], 2048.0)
+    sky.set_scan_shape(512, 4, 1)
+    b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+    b.set_shape(8, 128, 32, 1024)
+    pipe = sp.Pipeline(b, sky, max_chunk=2048)
+    T, H = bank.n_templates, sky.halo
+    strain = np.concatenate([synth.online_chunk(i) for i in range(2)], axis=1)
+    outs = []
+    for s in range(0, strain.shape[1], 2048):
+        ms = torch.empty((T, 2048), dtype=torch.float32, device="cuda")
+        am = torch.empty((T, 2048), dtype=torch.int32, device="cuda")
+        nl = torch.empty((T, 2048), dtype=torch.float32, device="cuda")
+        pipe.run(torch.from_numpy(np.ascontiguousarray(strain[:, s:s + 2048])).cuda(), ms, am, nl)
+        outs.append((ms.cpu().numpy(), am.cpu().numpy(), nl.cpu().numpy()))
+    ms, am, nl = [np.concatenate([o[i] for o in outs], axis=1) for i in range(3)]
+    assert np.isfinite(ms).all() and np.isfinite(nl).all()
+    assert am.min() >= 0 and am.max() < sky.n_pix
+    pick = [0, 333, 1023]
+    sub = bank.subset(pick)
+    z_or, _, _ = oracle.filter_bank(strain, sub.offsets, sub.a1, sub.b0, sub.delay)
+    N = strain.shape[1]
+    zp = np.concatenate([np.zeros((len(pick), 3, 2 * H)), z_or], axis=2)
+    for i, t in enumerate(pick):
+        ms_or, am_or, nl_or, sm_or = oracle.coherent(zp[i:i + 1], G, d_or, H, N, skymap=True)
+        assert_coherent_close(ms[t:t + 1], am[t:t + 1], nl[t:t + 1], ms_or, am_or, nl_or, sm_or)
+
+
+@pytest.mark.parametrize("n", [777, 2050])
+def test_tensor_memory_sky_map_scalar_tail_and_odd_lengths(n):
+    """Sky map from the tensor-memory scan where n is not a multiple of 4 (scalar stores)."""
+    sky, G, d_or = _sky(1, 3, 16, (0.5, 2.0))
+    sky.set_scan_shape(512, 4, 1)
+    H = sky.halo
+    z = synth.complex_gaussian_snr(1, (2, 3, n + 2 * H), sub=15)
+    ms, am, nl, mp = _scan(sky, z, n, skymap=True)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    mp = np.transpose(mp, (0, 2, 1))
+    assert np.all(np.abs(mp - sm_or) <= 1e-4 * sm_or.max(axis=-1, keepdims=True))
