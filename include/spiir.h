@@ -54,6 +54,18 @@ int spiir_last_error(char *buf, size_t len);
  * (0 disables).  Used to exercise allocation-failure paths without a real shortage. */
 void spiir_debug_fail_allocs(int n);
 
+/* Test hook: only the k-th device or pinned-host allocation from now fails (k >= 1; 0
+ * disarms), so that the clean-up of a partially built object can be exercised at every
+ * allocation site.  No counterpart in the paper. */
+void spiir_debug_fail_alloc_at(int k);
+
+/* Test hook for failure detection, with no counterpart in the paper: launches one block on
+ * `stream` whose bounded wait on an mbarrier that nothing completes gives up after
+ * `iterations` tries (1 .. 2^26) and records a timeout in the device status word, as a
+ * production wait that ran out does.  The next spiir_device_status call reports
+ * SPIIR_ETIMEOUT; the context stays usable.  Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
+int spiir_debug_wait_timeout(uint32_t iterations, void *stream);
+
 /* Sticky device-side status: SPIIR_OK, or SPIIR_ETIMEOUT after a bounded wait inside a
  * kernel gave up.  Synchronises the device.  clear != 0 resets the word. */
 int spiir_device_status(int clear);

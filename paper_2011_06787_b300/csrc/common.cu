@@ -11,6 +11,7 @@ namespace spiir {
 
 static thread_local std::string g_last_error;
 static std::atomic<int> g_fail_allocs{0};
+static std::atomic<int> g_fail_at{0};
 
 int fail(int code, const char *fmt, ...) {
     char buf[1024];
@@ -28,6 +29,10 @@ static bool take_injected_failure() {
     int n = g_fail_allocs.load();
     while (n > 0) {
         if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    }
+    int k = g_fail_at.load();
+    while (k > 0) {
+        if (g_fail_at.compare_exchange_weak(k, k - 1)) return k == 1;
     }
     return false;
 }
@@ -108,6 +113,33 @@ extern "C" int spiir_last_error(char *buf, size_t len) {
 }
 
 extern "C" void spiir_debug_fail_allocs(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
+
+extern "C" void spiir_debug_fail_alloc_at(int k) { g_fail_at.store(k > 0 ? k : 0); }
+
+namespace spiir {
+
+// One block waits on an mbarrier that nothing arrives on: the bounded wait gives up after
+// `limit` tries and records the timeout, as every production wait does.
+__global__ void k_debug_wait(uint32_t limit, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u, limit);
+    if (!ok && threadIdx.x == 0) report_timeout(status);
+}
+
+}  // namespace spiir
+
+extern "C" int spiir_debug_wait_timeout(uint32_t iterations, void *stream) {
+    clear_error();
+    if (iterations < 1 || iterations > kWaitLimit)
+        return fail(SPIIR_EINVAL, "iterations = %u outside [1, %u]", iterations, kWaitLimit);
+    int *w = device_status_word();
+    if (!w) return fail(SPIIR_ECUDA, "device status word unavailable");
+    k_debug_wait<<<1, 32, 0, (cudaStream_t)stream>>>(iterations, w);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
 
 extern "C" int spiir_device_status(int clear) {
     int *w = device_status_word();

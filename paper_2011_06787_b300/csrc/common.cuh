@@ -100,9 +100,9 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, 
 
 // Bounded wait for the given phase parity of an mbarrier.  Returns false when the
 // iteration limit ran out (the caller records a timeout and leaves).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kWaitLimit) {
     uint32_t ok = 0;
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 "
             "%0, 1, 0, p;\n}\n"

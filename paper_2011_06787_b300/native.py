@@ -33,7 +33,9 @@ SIGNATURES = {
     "spiir_version": (_I, []),
     "spiir_last_error": (_I, [ctypes.c_char_p, _SZ]),
     "spiir_debug_fail_allocs": (None, [_I]),
+    "spiir_debug_fail_alloc_at": (None, [_I]),
     "spiir_device_status": (_I, [_I]),
+    "spiir_debug_wait_timeout": (_I, [ctypes.c_uint32, _P]),
     "spiir_bank_create": (_I, [_I, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "spiir_bank_destroy": (None, [_P]),
     "spiir_bank_info": (_I, [_P, _P, _P, _P, _P]),

@@ -170,6 +170,17 @@ def online_bank(n_templates: int = ONLINE["n_templates"]) -> Bank:
     return full.subset(range(n_templates))
 
 
+def online_bank_global(world: int = 1, per_rank: int = ONLINE["n_templates"]) -> Bank:
+    """Bank of world x per_rank online-sized templates for a run sharded by template over
+    world GPUs (each rank filters a contiguous slice).  world = 1 gives online_bank(per_rank)."""
+    if world == 1:
+        return online_bank(per_rank)
+    c = ONLINE
+    g = rng(c["index"], "bank", world)
+    counts = g.integers(c["f_range"][0], c["f_range"][1] + 1, world * per_rank)
+    return random_bank(g, counts, c["d_max"])
+
+
 def online_workload(n_templates: int = ONLINE["n_templates"]):
     c = ONLINE
     det = detectors(c["index"], c["n_det"])

@@ -89,3 +89,9 @@ def test_batch_create_rejects_invalid_arguments():
     with pytest.raises(sp.SpiirError) as e:
         sp.Batch(3, bad, (1, 4, 16), FakeSky(), 512)
     assert "band 3" in str(e.value)
+
+
+def test_wait_timeout_hook_rejects_bad_limits():
+    L = native.lib()
+    for it in (0, (1 << 26) + 1):
+        assert L.spiir_debug_wait_timeout(it, None) == native.EINVAL
