@@ -291,6 +291,7 @@ int spiir_pipeline_run_host(spiir_pipeline_t pipe, const float *strain_host, int
  *             Nyquist, unit DC gain; M = 1 passes x through)
  *   z_b     = the band-b filters of each template on x_b (Eq. (zk), Sec. II.B.1)
  *   z[k]    = sum_b (1 - w) z_b[m-1] + w z_b[m],  m = floor(k / M_b), w = (k mod M_b) / M_b
+ *             (one low-rate sample of lag; a band with M = 1 contributes z_b[k], no lag)
  *   coherent scan of z over all templates of all banks (Sec. II.C.1), one H-sample lag as in
  *   the streaming pipeline.
  * The paper filters one rate only (its front end downsamples 16 kHz to 2 kHz by FIR); the

@@ -234,19 +234,17 @@ def segment_fit(h: np.ndarray, n_filters: int):
     edges = np.searchsorted(cum, np.linspace(0.0, cum[-1], n_filters + 1))
     edges = np.clip(edges, 0, n)
     edges[0], edges[-1] = 0, n
-    for i in range(1, edges.size):           # strictly increasing, at least one sample each
-        edges[i] = max(edges[i], edges[i - 1] + 1)
+    # strictly increasing, at least one sample each: e_i = max(e_i, e_{i-1} + 1)
+    k = np.arange(edges.size)
+    edges = np.maximum.accumulate(edges - k) + k
     edges = np.minimum(edges, n)
-    a1 = np.empty(n_filters, dtype=np.complex128)
-    b0 = np.empty(n_filters, dtype=np.complex128)
-    d = np.empty(n_filters, dtype=np.int32)
-    for m in range(n_filters):
-        lo, hi = int(min(edges[m], n - 1)), int(max(min(edges[m + 1], n), min(edges[m], n - 1) + 1))
-        L = max(hi - lo, 1)
-        omega = (ph[hi - 1] - ph[lo]) / max(L - 1, 1) if L > 1 else (ph[min(lo + 1, n - 1)] - ph[lo])
-        a1[m] = np.exp(-1.0 / L + 1j * omega)
-        b0[m] = h[lo]
-        d[m] = lo
+    lo = np.minimum(edges[:-1], n - 1)
+    hi = np.maximum(np.minimum(edges[1:], n), lo + 1)
+    L = np.maximum(hi - lo, 1)
+    omega = np.where(L > 1, (ph[hi - 1] - ph[lo]) / np.maximum(L - 1, 1), ph[np.minimum(lo + 1, n - 1)] - ph[lo])
+    a1 = np.exp(-1.0 / L + 1j * omega)
+    b0 = h[lo].astype(np.complex128)
+    d = lo.astype(np.int32)
     return a1, b0, d
 
 
@@ -283,6 +281,62 @@ def chirp_workload(n_templates: int = CHIRP["n_templates"], n_filters: int = CHI
         B[t] = (b0 * (1.0 + 0.05 * u[2]) * np.exp(1j * 0.05 * math.pi * u[3])).astype(np.complex64)
         D[t] = d
     return dict(h=H, a1=A, b0=B, delay=D, s0=np.zeros_like(A), mc=mc)
+
+
+# ----------------------------------------------------------------------------------------------
+# Scale workload: 4096 chirp templates x 600 filters, 60 s, 20 injections, nside 32
+
+SCALE = dict(index=4, n_det=3, rate=2048, chunk=2048, n_chunks=60, n_templates=4096, n_filters=600,
+             mc=(1.0, 3.0), f_lo=30.0, max_template_s=15.0, nside=32, sigma=(0.5, 2.0),
+             n_inj=20, snr=(8.0, 20.0), tc_s=(20.0, 58.0))
+
+
+def template_f_lo(mc_msun: float, max_s: float = SCALE["max_template_s"], f_lo: float = SCALE["f_lo"]) -> float:
+    """Start frequency of a template: f_lo, raised so that the Newtonian chirp lasts at most
+    max_s seconds (the time to coalescence tau(f) = 5/256 (pi f)^(-8/3) M^(-5/3))."""
+    M = mc_msun * G_MSUN_S
+    f = (max_s * 256.0 / 5.0 * M ** (5.0 / 3.0)) ** (-3.0 / 8.0) / math.pi
+    return max(f_lo, f)
+
+
+def scale_bank(n_templates: int = SCALE["n_templates"], n_filters: int = SCALE["n_filters"]):
+    """Template bank on a uniform chirp-mass grid over [1, 3] Msun.  Template t is the
+    first-order IIR fit (segment_fit) of conj(h_t), h_t the time-reversed Newtonian chirp from
+    template_f_lo(Mc_t) to 1024 Hz, so that the bank's output is the correlation with the
+    chirp; b0 is scaled by sqrt(2 / sum |h_t|^2), which makes E|z|^2 = 2 in unit white noise
+    (up to the fit's mismatch).  Returns (Bank, mc [T], template lengths [T])."""
+    c = SCALE
+    mcs = np.linspace(c["mc"][0], c["mc"][1], n_templates)
+    A = np.empty((n_templates, n_filters), dtype=np.complex64)
+    B = np.empty_like(A)
+    D = np.empty((n_templates, n_filters), dtype=np.int32)
+    lens = np.empty(n_templates, dtype=np.int64)
+    for t, mc in enumerate(mcs):
+        h = newtonian_chirp(float(mc), f_lo=template_f_lo(float(mc)))
+        a1, b0, d = segment_fit(np.conj(h), n_filters)
+        A[t] = a1.astype(np.complex64)
+        B[t] = (b0 * math.sqrt(2.0 / float(np.sum(np.abs(h) ** 2)))).astype(np.complex64)
+        D[t] = d
+        lens[t] = h.size
+    off = np.arange(n_templates + 1, dtype=np.int64) * n_filters
+    return Bank(off, A.ravel(), B.ravel(), D.ravel()), mcs, lens
+
+
+def scale_injections(n: int = SCALE["n_inj"]):
+    """Injection parameters: chirp mass U[1, 3] Msun; source direction isotropic (unit
+    vector); polarisation angle U[0, pi); cos(inclination) U[-1, 1]; coalescence phase
+    U[0, 2 pi); geocentric coalescence sample round(2048 x U[20, 58] s); network SNR U[8, 20]."""
+    c = SCALE
+    g = rng(c["index"], "inject")
+    mc = g.uniform(c["mc"][0], c["mc"][1], n)
+    cz = g.uniform(-1.0, 1.0, n)
+    ph = g.uniform(0.0, 2.0 * math.pi, n)
+    sz = np.sqrt(1.0 - cz ** 2)
+    nhat = np.stack([sz * np.cos(ph), sz * np.sin(ph), cz], axis=1)
+    return dict(mc=mc, nhat=nhat, psi=g.uniform(0.0, math.pi, n), cosi=g.uniform(-1.0, 1.0, n),
+                phic=g.uniform(0.0, 2.0 * math.pi, n),
+                tc=np.rint(g.uniform(c["tc_s"][0], c["tc_s"][1], n) * c["rate"]).astype(np.int64),
+                snr=g.uniform(c["snr"][0], c["snr"][1], n))
 
 
 # ----------------------------------------------------------------------------------------------
