@@ -157,9 +157,10 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                     for (int r = 0; r < nr; ++r) step(r);
                 }
             }
-            __syncthreads();
+            __syncwarp();
             // pass 1: each warp sums its own rows per column, split at template boundaries;
             // piece j of the warp overwrites row 32*warp + j (a row it has already read).
+            // Only rows written by the same warp are read, so a warp barrier suffices.
             // Lane r owns column r; with R < 32 the remaining lanes have no column.
             if (busy && wfirst >= 0 && lane < R) {
                 int j = 0;
@@ -217,8 +218,10 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
     return true;
 }
 
+// The default shape (8 filters per lane, 128 lanes) asks for 5 resident blocks: the compiler
+// then keeps it at 92 registers without spills (117 otherwise).
 template <int S, int NL, int R>
-__global__ void __launch_bounds__(NL, 1) k_filter_bank(const __grid_constant__ BankArgs a) {
+__global__ void __launch_bounds__(NL, (S == 8 && NL == 128) ? 5 : 1) k_filter_bank(const __grid_constant__ BankArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     if (threadIdx.x == 0) mbar_init(bar, 1);
