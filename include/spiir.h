@@ -232,9 +232,12 @@ int spiir_coherent_scan(spiir_sky_t sky, const float *snr_dev, int64_t snr_pitch
 
 /* u_t[k] = sum_l y_l[k] for k = 0..n-1, with y_l[-1] = s0_l and
  * y_l[k] = a1_l y_l[k-1] + b0_l [k == d_l] (Eq. (zk) driven by a unit impulse at k = 0).
- *   u_dev [T][n] complex.  ckpt_dev: NULL, or [T][F][ceil(n / ckpt_every)] complex that
+ *   u_dev [T][n] complex.  ckpt_dev: NULL, or [ceil(n / ckpt_every)][T][F] complex that
  *   receives y_l[j ckpt_every - 1] for every j (the state before sample j ckpt_every);
- *   ckpt_every a multiple of 32 in [32, 8192].  Delays may exceed n.  Enqueued on stream. */
+ *   ckpt_every a multiple of 32 in [32, 8192].  Delays may exceed n.  Enqueued on stream.
+ * With checkpoints the segment starting states are found by FP64 jumps,
+ *   y[(j+1)C - 1] = a^C y[jC - 1] + b a^((j+1)C - 1 - d) [jC <= d < (j+1)C],
+ * and the segments run in parallel in FP32; without, one pass per template over all n. */
 int spiir_impulse_forward(int n_templates, int filters_per_template, const float *a1_dev,
                           const float *b0_dev, const int32_t *delay_dev, const float *s0_dev,
                           int64_t n, float *u_dev, int ckpt_every, float *ckpt_dev, void *stream);
@@ -242,18 +245,20 @@ int spiir_impulse_forward(int n_templates, int filters_per_template, const float
 /* Reverse mode of spiir_impulse_forward for a real loss L(u).
  *   grad_u_dev [T][n] complex: dL/dRe u + i dL/dIm u (PyTorch's convention).
  *   ckpt_dev   the checkpoints written by spiir_impulse_forward with the same ckpt_every.
+ *   workspace_dev [ceil(n / ckpt_every) + 2][T][F] complex: scratch, overwritten.
  * Outputs [T][F] complex in the same convention:
  *   grad_a1 = sum_k lambda_l[k] conj(y_l[k-1]), grad_b0 = lambda_l[d_l] (0 if d_l >= n),
  *   grad_s0 = conj(a1_l) lambda_l[0], where lambda_l[n] = 0 and
  *   lambda_l[k] = grad_u_t[k] + conj(a1_l) lambda_l[k+1].
- * States are recomputed from the checkpoints, segment by segment in reverse.  Shared memory
- * grows with ckpt_every x filters: SPIIR_EUNSUPPORTED when it does not fit (1024 x 320 fits).
- * Enqueued on stream. */
+ * Parallel over checkpoint segments: each segment's own part of lambda, an FP64 scan over the
+ * segments for their boundary values, then states recomputed from the checkpoints and the
+ * gradients formed segment by segment (added over segments in FP64, in order).  Shared memory
+ * grows with ckpt_every: SPIIR_EUNSUPPORTED when it does not fit.  Enqueued on stream. */
 int spiir_impulse_backward(int n_templates, int filters_per_template, const float *a1_dev,
                            const float *b0_dev, const int32_t *delay_dev, int64_t n,
                            const float *grad_u_dev, int ckpt_every, const float *ckpt_dev,
                            float *grad_a1_dev, float *grad_b0_dev, float *grad_s0_dev,
-                           void *stream);
+                           float *workspace_dev, void *stream);
 
 /* ------------------------------------------------------------------------------------
  * Streaming pipeline: one call per strain chunk runs the whole hot path (filter bank,

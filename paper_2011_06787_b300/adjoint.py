@@ -38,7 +38,7 @@ def _impulse_fn():
             T, F = a1c.shape
             u = torch.empty((T, n), dtype=torch.complex64, device=a1.device)
             nck = (n + ckpt_every - 1) // ckpt_every
-            ck = torch.empty((T, F, nck), dtype=torch.complex64, device=a1.device)
+            ck = torch.empty((nck, T, F), dtype=torch.complex64, device=a1.device)
             check(native.lib().spiir_impulse_forward(T, F, _p(a1c), _p(b0c), _p(dc), _p(s0c), n, _p(u), ckpt_every,
                                                      _p(ck), _stream()))
             ctx.save_for_backward(a1c, b0c, dc, ck)
@@ -53,8 +53,9 @@ def _impulse_fn():
             ga = torch.empty_like(a1c)
             gb = torch.empty_like(b0c)
             gs = torch.empty_like(a1c)
+            work = torch.empty((ck.shape[0] + 2, T, F), dtype=torch.complex64, device=ck.device)
             check(native.lib().spiir_impulse_backward(T, F, _p(a1c), _p(b0c), _p(dc), ctx.n, _p(g), ctx.ckpt_every,
-                                                      _p(ck), _p(ga), _p(gb), _p(gs), _stream()))
+                                                      _p(ck), _p(ga), _p(gb), _p(gs), _p(work), _stream()))
             return ga, gb, gs, None, None, None
 
     return IIRImpulse

@@ -55,7 +55,7 @@ SIGNATURES = {
     "spiir_sky_info": (_I, [_P, _P, _P, _P]),
     "spiir_coherent_scan": (_I, [_P, _P, _I64, _I, _I64, _P, _P, _P, _P, _P]),
     "spiir_impulse_forward": (_I, [_I, _I, _P, _P, _P, _P, _I64, _P, _I, _P, _P]),
-    "spiir_impulse_backward": (_I, [_I, _I, _P, _P, _P, _I64, _P, _I, _P, _P, _P, _P, _P]),
+    "spiir_impulse_backward": (_I, [_I, _I, _P, _P, _P, _I64, _P, _I, _P, _P, _P, _P, _P, _P]),
     "spiir_batch_create": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _I64, ctypes.POINTER(_P)]),
     "spiir_batch_destroy": (None, [_P]),
     "spiir_batch_info": (_I, [_P, _P, _P, _P]),

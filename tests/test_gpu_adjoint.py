@@ -55,14 +55,16 @@ def test_backward_matches_oracle_adjoint(ckpt_every):
     a1, b0, d, s = _cuda(w["a1"]), _cuda(w["b0"]), _cuda(w["delay"]), _cuda(s0)
     u = torch.empty((T, n), dtype=torch.complex64, device="cuda")
     nck = (n + ckpt_every - 1) // ckpt_every
-    ck = torch.empty((T, F, nck), dtype=torch.complex64, device="cuda")
+    ck = torch.empty((nck, T, F), dtype=torch.complex64, device="cuda")
     P = lambda t: ctypes.c_void_p(t.data_ptr())
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     L = native.lib()
     native.check(L.spiir_impulse_forward(T, F, P(a1), P(b0), P(d), P(s), n, P(u), ckpt_every, P(ck), st))
     gu = _cuda(grad_u)
     ga, gb, gs = (torch.empty_like(a1) for _ in range(3))
-    native.check(L.spiir_impulse_backward(T, F, P(a1), P(b0), P(d), n, P(gu), ckpt_every, P(ck), P(ga), P(gb), P(gs), st))
+    work = torch.empty((nck + 2, T, F), dtype=torch.complex64, device="cuda")
+    native.check(L.spiir_impulse_backward(T, F, P(a1), P(b0), P(d), n, P(gu), ckpt_every, P(ck), P(ga), P(gb), P(gs),
+                                          P(work), st))
     torch.cuda.synchronize()
     ga_or, gb_or, gs_or = oracle.impulse_backward(_flat_bank(w), w["a1"].ravel(), w["b0"].ravel(), w["delay"].ravel(),
                                                   s0.ravel(), grad_u)
@@ -72,7 +74,7 @@ def test_backward_matches_oracle_adjoint(ckpt_every):
     # checkpoints: state before sample j * ckpt_every
     _, yend = oracle.impulse_forward(_flat_bank(w), w["a1"].ravel(), w["b0"].ravel(), w["delay"].ravel(), s0.ravel(),
                                      ckpt_every, return_end=True)
-    assert np.max(np.abs(ck[:, :, 1].cpu().numpy().ravel() - yend)) <= 1e-4 * np.max(np.abs(yend))
+    assert np.max(np.abs(ck[1].cpu().numpy().ravel() - yend)) <= 1e-4 * np.max(np.abs(yend))
 
 
 def _loss_oracle(w, T8, a1, b0, s0):
@@ -176,3 +178,35 @@ def test_gradient_descent_improves_the_overlap():
         opt.step()
         first = loss.item() if first is None else first
     assert loss.item() < 0.95 * first
+
+
+@pytest.mark.parametrize("ckpt_every", [32, 96, 4096])
+def test_forward_without_checkpoints_matches_the_segmented_forward(ckpt_every):
+    """The segmented forward (FP64 jumps between checkpoints, segments in parallel) against the
+    sequential one (no checkpoint buffer) and the oracle; ragged last segments, delays past n,
+    non-zero initial states."""
+    import torch
+    from paper_2011_06787_b300 import native
+    import ctypes
+    w = synth.chirp_workload(3, 64, mc=[2.5, 2.8, 3.0], max_len=5000)
+    T, F = w["a1"].shape
+    n = 4999
+    g = np.random.default_rng(5)
+    s0 = ((g.standard_normal((T, F)) + 1j * g.standard_normal((T, F))) * 0.02).astype(np.complex64)
+    d = w["delay"].copy()
+    d[:, -3:] = n + 100  # impulses that never arrive
+    a1, b0, dd, s = _cuda(w["a1"]), _cuda(w["b0"]), _cuda(d), _cuda(s0)
+    P = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = native.lib()
+    u_seq = torch.empty((T, n), dtype=torch.complex64, device="cuda")
+    native.check(L.spiir_impulse_forward(T, F, P(a1), P(b0), P(dd), P(s), n, P(u_seq), ckpt_every, None, st))
+    u_seg = torch.empty_like(u_seq)
+    ck = torch.empty(((n + ckpt_every - 1) // ckpt_every, T, F), dtype=torch.complex64, device="cuda")
+    native.check(L.spiir_impulse_forward(T, F, P(a1), P(b0), P(dd), P(s), n, P(u_seg), ckpt_every, P(ck), st))
+    torch.cuda.synchronize()
+    u_or = oracle.impulse_forward(_flat_bank(w), w["a1"].ravel(), w["b0"].ravel(), d.ravel(), s0.ravel(), n)
+    for u in (u_seq, u_seg):
+        u = u.cpu().numpy()
+        err = np.abs(u - u_or).max(axis=1) / np.abs(u_or).max(axis=1)
+        assert np.all(err < 1e-4), err
