@@ -133,7 +133,7 @@ __global__ void k_fwd_jump(const float2 *__restrict__ a1, const float2 *__restri
     }
 }
 
-constexpr int kFwdS = 4;  // filters per thread in the segment forward (two packed pairs)
+constexpr int kFwdS = 4;  // filters per thread in the segment forward for templates above 320 filters
 constexpr int kL1 = 64, kL2 = 16;  // mark spacings of the backward segment pass
 
 // Forward 2: one block per (segment, template); u over the segment.
@@ -539,15 +539,20 @@ extern "C" int spiir_impulse_forward(int T, int F, const float *a1, const float 
         auto CK = reinterpret_cast<float2 *>(ckpt);
         k_fwd_jump<<<(unsigned)((TF + 127) / 128), 128, 0, st>>>(A, B, delay, S0, TF, n, C, nck, CK);
         SPIIR_CUDA_TRY(cudaGetLastError());
-        const int nt = ((F + kFwdS - 1) / kFwdS + 31) / 32 * 32;
+        // filters per thread: a template of up to 320 filters in one warp (S even, at most 10),
+        // larger templates 4 per thread over several warps
+        const int S = F <= 320 ? std::max(2, ((F + 31) / 32 + 1) / 2 * 2) : kFwdS;
+        const int nt = ((F + S - 1) / S + 31) / 32 * 32;
         const size_t smem = (size_t)nt * (kAdjR + 1) * sizeof(float2) + (size_t)(nt / 32) * kAdjR * sizeof(float2);
-        static bool attr = false;
-        if (!attr) {
-            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<kFwdS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-            attr = true;
+        const dim3 grid((unsigned)nck, (unsigned)T);
+        float2 *U = reinterpret_cast<float2 *>(u);
+        switch (S) {
+            case 2: k_fwd_seg<2><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
+            case 4: k_fwd_seg<4><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
+            case 6: k_fwd_seg<6><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
+            case 8: k_fwd_seg<8><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
+            default: k_fwd_seg<10><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
         }
-        k_fwd_seg<kFwdS><<<dim3((unsigned)nck, (unsigned)T), nt, smem, st>>>(A, B, delay, F, n, C, nck, CK,
-                                                                        reinterpret_cast<float2 *>(u));
         SPIIR_CUDA_TRY(cudaGetLastError());
         return SPIIR_OK;
     }
