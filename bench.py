@@ -392,7 +392,12 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     nl = torch.empty((T, chunk), device=dev)
     xs = [torch.from_numpy(synth.multirate_chunk(i, 3, chunk)).to(dev) for i in range(args.warmup + args.steps)]
     x = torch.empty((3, chunk), device=dev)
-    tuned = autotune.tune_batch(batch, x, ms, am, nl)
+    if args.batch_shape:
+        shp = [int(v) for v in args.batch_shape.split(",")]
+        batch.set_shape(*shp)
+        tuned = {"shape": shp, "fixed": True}
+    else:
+        tuned = autotune.tune_batch(batch, x, ms, am, nl)
     out = {"workload": f"{len(banks)} banks, {T} templates, {F} filters over bands 2048/512/128 Hz, "
                        f"3 det, {chunk}-sample chunks, nside {c['nside']}",
            "updates_per_chunk": updates, "pixel_samples_per_chunk": T * chunk * sky.n_pix,
@@ -523,6 +528,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--scan-shape", default="", help="fixed coherent-scan shape threads,pairs,table (no autotuning)")
     ap.add_argument("--bank-shape", default="", help="fixed filter-bank shape S,NL,R,tile (no autotuning)")
+    ap.add_argument("--batch-shape", default="", help="fixed persistent-launch shape S,NL,R,blocks_per_sm (no autotuning)")
     ap.add_argument("--templates", type=int, default=1024, help="templates per GPU (1024 = the workload)")
     ap.add_argument("--flush-mib", type=int, default=512, help="L2 flush buffer written before each timed step")
     args = ap.parse_args()
