@@ -73,6 +73,10 @@ def _load():
         lib.oracle_impulse_forward.restype = None
         lib.oracle_impulse_backward.argtypes = [ctypes.c_int, P, P, P, P, P, i64, P, P, P, P]
         lib.oracle_impulse_backward.restype = ctypes.c_int
+        lib.oracle_autocorr.argtypes = [ctypes.c_int, P, i64, ctypes.c_int, P]
+        lib.oracle_autocorr.restype = None
+        lib.oracle_xi2.argtypes = [ctypes.c_int, ctypes.c_int, P, i64, P, ctypes.c_int, i64, P]
+        lib.oracle_xi2.restype = None
         _lib = lib
     return _lib
 
@@ -420,3 +424,48 @@ def multirate_bank(x, offsets, a1, b0, delay, band, factors):
         up, _ = upsample_linear(zb, M)
         z += up
     return z
+
+
+# --------------------------------------------------------------------------------------------
+# Signal consistency: Sec. II.C.2
+
+
+def autocorr(u, Nj: int):
+    """A[t][Nj + j] = R[j] / R[0], R[j] = sum_k conj(u_t[k]) u_t[k + j], A[-j] = conj(A[j]);
+    u [T][nr] complex.  Returns [T][2 Nj + 1] complex128."""
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.complex128)
+    T, nr = u.shape
+    A = np.zeros((T, 2 * Nj + 1), dtype=np.complex128)
+    lib.oracle_autocorr(T, _ptr(u), nr, int(Nj), _ptr(A))
+    return A
+
+
+def xi2(z, A, Nj: int, n: int):
+    """xi^2[t][I][k] = sum_{|j| <= Nj} |z[k + j] - z[k] A[j]|^2 / sum_{|j| <= Nj} (2 - 2 |A[j]|^2)
+    for z [T][n_det][pitch] with entry Nj + k = sample k and A [T][2 Nj + 1]."""
+    lib = _load()
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    T, n_det, pitch = z.shape
+    if pitch < n + 2 * Nj:
+        raise ValueError("z holds fewer than n + 2 Nj samples")
+    out = np.zeros((T, n_det, n), dtype=np.float64)
+    lib.oracle_xi2(T, n_det, _ptr(z), pitch, _ptr(A), int(Nj), n, _ptr(out))
+    return out
+
+
+def xi2_network(xi, delays, argmax, H: int):
+    """xi_C^2[t][k] = (1 / N_d) sum_I xi_I^2 at the detector's sample k + Delta_I(p), p the
+    argmax pixel of (t, k) (Sec. II.C.2); xi [T][n_det][pitch] with entry H + k = sample k."""
+    xi = np.asarray(xi, dtype=np.float64)
+    delays = np.asarray(delays)
+    argmax = np.asarray(argmax)
+    T, n_det, _ = xi.shape
+    n = argmax.shape[1]
+    out = np.zeros((T, n), dtype=np.float64)
+    for t in range(T):
+        for k in range(n):
+            d = delays[argmax[t, k]]
+            out[t, k] = sum(xi[t, I, H + k + d[I]] for I in range(n_det)) / n_det
+    return out

@@ -24,6 +24,12 @@
  *                           y_l[-1] = s_l, x = unit impulse at k = 0.
  *   oracle_impulse_backward reverse-mode derivative of a real loss of that response
  *                           (adjoint recurrence, see the function comment).
+ *   oracle_autocorr         the correlation of a template with itself (Sec. II.C.2):
+ *                             R[j] = sum_k conj(u[k]) u[k + j],  A[j] = R[j] / R[0],
+ *                             A[-j] = conj(A[j]).
+ *   oracle_xi2              Sec. II.C.2 signal-consistency statistic, per sample:
+ *                             xi^2[k] = sum_{j=-Nj}^{Nj} |z[k + j] - z[k] A[j]|^2
+ *                                       / sum_{j=-Nj}^{Nj} (2 - 2 |A[j]|^2).
  */
 #include <complex.h>
 #include <math.h>
@@ -222,4 +228,53 @@ int oracle_impulse_backward(int T, const int64_t *off, const cplx *a1, const cpl
         free(y);
     }
     return err;
+}
+
+/*
+ * Template autocorrelation.  u [T][nr] (a template's response), A [T][2 Nj + 1] out with
+ * A[t][Nj + j] the lag-j value for -Nj <= j <= Nj.  Lags beyond the response are zero terms.
+ */
+void oracle_autocorr(int T, const cplx *u, int64_t nr, int Nj, cplx *A)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < T; ++t) {
+        const cplx *ut = u + (int64_t)t * nr;
+        cplx *At = A + (int64_t)t * (2 * Nj + 1);
+        cplx R0 = 0.0;
+        for (int64_t k = 0; k < nr; ++k) R0 += conj(ut[k]) * ut[k];
+        for (int j = 0; j <= Nj; ++j) {
+            cplx R = 0.0;
+            for (int64_t k = 0; k + j < nr; ++k) R += conj(ut[k]) * ut[k + j];
+            At[Nj + j] = R / R0;
+            At[Nj - j] = conj(R / R0);
+        }
+    }
+}
+
+/*
+ * Signal-consistency statistic of every sample of SNR series.
+ *   z   [T][n_det][pitch]: entry Nj + k is sample k, so samples -Nj .. n + Nj - 1 are read.
+ *   A   [T][2 Nj + 1]: autocorrelation of each template, A[t][Nj + j] = A_t[j].
+ *   out [T][n_det][n].
+ */
+void oracle_xi2(int T, int n_det, const cplx *z, int64_t pitch, const cplx *A, int Nj, int64_t n,
+                double *out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < T; ++t) {
+        const cplx *At = A + (int64_t)t * (2 * Nj + 1);
+        double den = 0.0;
+        for (int j = -Nj; j <= Nj; ++j) den += 2.0 - 2.0 * creal(At[Nj + j] * conj(At[Nj + j]));
+        for (int di = 0; di < n_det; ++di) {
+            const cplx *zr = z + ((int64_t)t * n_det + di) * pitch + Nj;
+            for (int64_t k = 0; k < n; ++k) {
+                double num = 0.0;
+                for (int j = -Nj; j <= Nj; ++j) {
+                    const cplx d = zr[k + j] - zr[k] * At[Nj + j];
+                    num += creal(d * conj(d));
+                }
+                out[((int64_t)t * n_det + di) * n + k] = num / den;
+            }
+        }
+    }
 }

@@ -452,3 +452,97 @@ def test_linear_upsample_reproduces_ramp_with_one_sample_lag():
     k = np.arange(40)
     np.testing.assert_allclose(z[0, M:], (k[M:] / M - 1) * (1 + 0.5j), rtol=1e-14)
     assert last[0] == zb[0, -1]
+
+
+# ---------------------------------------------------------------------------------------------
+# Signal-consistency statistic (Sec. II.C.2)
+
+
+def _random_template(seed, F=6, d_max=40):
+    g = np.random.default_rng(seed)
+    a1 = (g.uniform(0.7, 0.95, F) * np.exp(1j * g.uniform(0, 2 * np.pi, F))).astype(np.complex64)
+    b0 = ((g.standard_normal(F) + 1j * g.standard_normal(F)) / np.sqrt(2 * F)).astype(np.complex64)
+    d = g.integers(0, d_max, F).astype(np.int32)
+    return a1, b0, d
+
+
+def _response(a1, b0, d, nr):
+    F = a1.size
+    return oracle.impulse_forward(np.array([0, F], np.int64), a1, b0, d, np.zeros(F, np.complex64), nr)[0]
+
+
+def test_autocorr_of_one_filter_is_a_power_of_its_pole():
+    """u[k] = b a^k (k >= 0): R[j] = |b|^2 a^j sum_k |a|^2k, so A[j] = a^j and A[-j] = conj(a)^j."""
+    a = 0.9 * np.exp(0.7j)
+    nr, Nj = 4000, 12
+    u = (0.3 - 0.2j) * a ** np.arange(nr)
+    A = oracle.autocorr(u[None, :], Nj)[0]
+    j = np.arange(Nj + 1)
+    np.testing.assert_allclose(A[Nj:], a ** j, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(A[:Nj + 1][::-1], np.conj(a) ** j, rtol=0, atol=1e-12)
+
+
+def test_xi2_vanishes_for_a_window_shaped_like_the_autocorrelation():
+    """z[k0 + j] = c A[j] for |j| <= Nj is exactly what the statistic expects: xi^2[k0] = 0,
+    while the same window mirrored in time (A[-j]) or conjugated does not vanish."""
+    Nj = 9
+    a1, b0, d = _random_template(1)
+    A = oracle.autocorr(_response(a1, b0, d, 300)[None, :], Nj)[0]
+    g = np.random.default_rng(2)
+    z = (g.standard_normal(4 * Nj + 1) + 1j * g.standard_normal(4 * Nj + 1))
+    k0 = 2 * Nj
+    c = 3.0 - 1.5j
+    for mod, zero in ((lambda x: x, True), (lambda x: x[::-1], False), (np.conj, False)):
+        zz = z.copy()
+        zz[k0 - Nj: k0 + Nj + 1] = c * mod(A)
+        x = oracle.xi2(zz[None, None, :], A[None, :], Nj, 2 * Nj + 1)[0, 0, Nj]
+        assert (x < 1e-24) == zero, x
+
+
+def test_xi2_of_a_matched_signal_through_the_filter_bank_vanishes():
+    """A signal s with s[k0 - m] = conj(u[m]) filtered by the template's own filters gives
+    z[k0 + j] = R[j] = z[k0] A[j] exactly (finite sums over the same range): xi^2[k0] = 0."""
+    Nj, nr = 10, 400
+    a1, b0, d = _random_template(3)
+    u = _response(a1, b0, d, nr)
+    A = oracle.autocorr(u[None, :], Nj)[0]
+    k0 = nr + 50
+    x = np.zeros((1, k0 + Nj + 60), np.complex128)
+    x[0, k0 - np.arange(nr)] = np.conj(u)
+    z, _, _ = oracle.filter_bank(x, np.array([0, a1.size], np.int64), a1, b0, d)
+    zr = z[0, 0]
+    np.testing.assert_allclose(zr[k0 + np.arange(-Nj, Nj + 1)], zr[k0] * A, rtol=0, atol=1e-12 * abs(zr[k0]))
+    xi = oracle.xi2(zr[None, None, k0 - 2 * Nj: k0 + 2 * Nj + 1], A[None, :], Nj, 2 * Nj + 1)[0, 0, Nj]
+    assert xi < 1e-20
+
+
+def test_xi2_has_mean_one_in_white_noise():
+    """z = u * x with x unit white noise and sum |u|^2 = 2: E|z[k+j] - z[k] A[j]|^2 = 2 - 2|A[j]|^2
+    term by term, so the statistic is a reduced chi-square of mean 1."""
+    Nj, nr = 30, 600
+    a1, b0, d = _random_template(4, F=8, d_max=200)
+    u = _response(a1, b0, d, nr)
+    s = np.sqrt(2.0 / np.sum(np.abs(u) ** 2))
+    b0 = (b0 * s).astype(np.complex64)
+    u = _response(a1, b0, d, nr)
+    A = oracle.autocorr(u[None, :], Nj)[0]
+    x = synth.white_noise(0, 1, 120000, sub=99).astype(np.float64)
+    z, _, _ = oracle.filter_bank(x, np.array([0, a1.size], np.int64), a1, b0, d)
+    zs = z[0, 0, 2 * nr:]  # past the start-up transient
+    n = zs.size - 2 * Nj
+    xi = oracle.xi2(zs[None, None, :], A[None, :], Nj, n)[0, 0]
+    assert abs(xi.mean() - 1.0) < 0.03, xi.mean()
+
+
+def test_network_average_reads_each_detector_at_its_arrival_time():
+    """xi_C^2 at (t, k) is the mean over detectors of xi_I^2 at k + Delta_I(argmax)."""
+    T, n_det, n, H = 2, 3, 7, 4
+    xi = np.arange(T * n_det * (n + 2 * H), dtype=np.float64).reshape(T, n_det, n + 2 * H)
+    delays = np.array([[0, 0, 0], [-4, 1, 4], [3, -2, 0]])
+    argmax = np.array([[0, 1, 2, 1, 0, 2, 1], [2, 2, 1, 0, 0, 1, 2]])
+    out = oracle.xi2_network(xi, delays, argmax, H)
+    for t in range(T):
+        for k in range(n):
+            p = argmax[t, k]
+            expect = np.mean([xi[t, I, H + k + delays[p, I]] for I in range(n_det)])
+            assert out[t, k] == expect
