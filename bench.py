@@ -333,6 +333,9 @@ def run_gpu(args):
     skymap = None
     if "skymap" in args.sections:
         skymap = skymap_rate(args, torch, sky, zbuf, n, ms, am, nl, timed_loop)
+    xi2 = None
+    if "xi2" in args.sections:
+        xi2 = xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -363,6 +366,7 @@ def run_gpu(args):
             "batched_vs_plain": batched,
             "adjoint": adjoint,
             "skymap": skymap,
+            "xi2": xi2,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
                                                    "h2d_bytes_per_step": n_det * n * 4,
@@ -419,6 +423,53 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     out["kernel_launches_per_chunk"] = {"plain": 1 + sum(1 for b in banks for k in range(3) if np.any(b[4] == k)) +
                                         2 * len(banks), "batched": 4}
     return out
+
+
+def xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop):
+    """Signal-consistency statistic (Sec. II.C.2) on the online workload: xi_I^2 for every
+    template, detector and sample of a chunk with Nj = 175 (351 taps), from each template's
+    own autocorrelation (responses of 6000 samples by the impulse forward, templates padded to
+    the largest filter count with zero filters), and xi_C^2 at the coherent argmax."""
+    Nj, nr = 175, 6000
+    T, dev = bank.n_templates, am.device
+    F = int(np.diff(bank.offsets).max())
+    a1 = np.zeros((T, F), np.complex64)
+    b0 = np.zeros((T, F), np.complex64)
+    dl = np.zeros((T, F), np.int32)
+    for t in range(T):
+        lo, hi = int(bank.offsets[t]), int(bank.offsets[t + 1])
+        a1[t, :hi - lo], b0[t, :hi - lo], dl[t, :hi - lo] = bank.a1[lo:hi], bank.b0[lo:hi], bank.delay[lo:hi]
+    from paper_2011_06787_b300.adjoint import impulse_response
+    cu = lambda x: torch.from_numpy(x).to(dev)
+    u = impulse_response(cu(a1), cu(b0), torch.zeros((T, F), dtype=torch.complex64, device=dev), cu(dl), nr, 1024)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    A = sp.autocorr(u.contiguous(), Nj)
+    e1.record()
+    e1.synchronize()
+    ac_ms = e0.elapsed_time(e1)
+    del u
+    # SNR of two chunks: entry Nj + k of each row is sample k of the xi^2 window
+    z = torch.zeros((T, 3, 2 * n), dtype=torch.complex64, device=dev)
+    b.reset()
+    b.filter_chunk(torch.cat([chunks[0], chunks[1]], dim=1).contiguous(), z)
+    xi = torch.empty((T, 3, n + 2 * sky.halo), dtype=torch.float32, device=dev)
+    steps = max(3, min(args.steps, 16))
+    sp.xi2(z, A, Nj, n + 2 * sky.halo, xi)
+    t = timed_loop(lambda i: sp.xi2(z, A, Nj, n + 2 * sky.halo, xi), steps)
+    xi_ms = float(np.mean(t))
+    out = torch.empty((T, n), dtype=torch.float32, device=dev)
+    tn = timed_loop(lambda i: sp.xi2_network(sky, xi, am, n, out), steps)
+    flops = T * 3 * (n + 2 * sky.halo) * (2 * Nj + 1) * 12  # d = z[k+j] - z[k] A[j]: 4 FMA; |d|^2: 2 FMA
+    peak = 148 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    del z, xi, out, A
+    torch.cuda.empty_cache()
+    return {"workload": f"{T} templates x 3 det x {n + 2 * sky.halo} samples, Nj = {Nj} ({2 * Nj + 1} taps)",
+            "steps": steps, "xi2_ms": xi_ms, "network_ms": float(np.mean(tn)), "autocorr_ms_once": ac_ms,
+            "samples_per_s": T * 3 * (n + 2 * sky.halo) / (xi_ms * 1e-3),
+            "roofline": {"kernel": "k_xi2", "bound": "alu", "achieved": flops / (xi_ms * 1e-3) / 1e12,
+                         "peak": peak, "unit": "TFLOP/s", "frac": flops / (xi_ms * 1e-3) / 1e12 / peak,
+                         "flops_per_launch": flops}}
 
 
 def skymap_rate(args, torch, sky, zbuf, n, ms, am, nl, timed_loop):
@@ -522,8 +573,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
-    ap.add_argument("--sections", default="main,batched,adjoint,skymap",
-                    help="comma list of measurements: main (always timed), batched, adjoint, skymap")
+    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2",
+                    help="comma list of measurements: main (always timed), batched, adjoint, skymap, xi2")
     ap.add_argument("--adjoint-templates", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--scan-shape", default="", help="fixed coherent-scan shape threads,pairs,table (no autotuning)")

@@ -224,6 +224,38 @@ int spiir_coherent_scan(spiir_sky_t sky, const float *snr_dev, int64_t snr_pitch
                         float *null_stat_dev, float *skymap_dev, void *stream);
 
 /* ------------------------------------------------------------------------------------
+ * Signal-consistency statistic (Sec. II.C.2).  For template t, detector I and sample k,
+ *   xi_I^2[k] = sum_{j=-Nj}^{Nj} |z_I[k + j] - z_I[k] A_t[j]|^2 / sum_{j=-Nj}^{Nj} (2 - 2 |A_t[j]|^2)
+ * with A_t the autocorrelation of the template's response u_t (A[j] = R[j] / R[0],
+ * R[j] = sum_k conj(u[k]) u[k + j], A[-j] = conj(A[j])); the SNR is taken as normalised
+ * (E|z|^2 = 2 in noise), so the statistic is a reduced chi-square of mean 1.  The network
+ * value is xi_C^2 = (1 / N_d) sum_I xi_I^2, each detector read at its arrival time for the
+ * coherent argmax pixel.  Nj ("n_lags") is typically 175 (Sec. IV); at most 1024.
+ * ---------------------------------------------------------------------------------- */
+
+/* A_dev [T][2 n_lags + 1] complex (entry n_lags + j is lag j) from the responses
+ * u_dev [T][n_resp] complex (e.g. spiir_impulse_forward with zero initial states); lags past
+ * the response contribute nothing.  Device pointers, enqueued on stream.
+ * Errors: SPIIR_EINVAL. */
+int spiir_autocorr(int n_templates, const float *u_dev, int64_t n_resp, int n_lags, float *A_dev,
+                   void *stream);
+
+/* xi2_dev [T][n_det][xi2_pitch] (f32): xi_I^2 of samples k = 0 .. n-1, from
+ * snr_dev [T][n_det][snr_pitch] complex in which entry n_lags + k is sample k (samples
+ * -n_lags .. n + n_lags - 1 are read; snr_pitch >= n + 2 n_lags, 8-byte aligned) and
+ * A_dev [T][2 n_lags + 1] complex.  Device pointers, enqueued on stream.
+ * Errors: SPIIR_EINVAL. */
+int spiir_xi2(int n_templates, int n_det, const float *snr_dev, int64_t snr_pitch, const float *A_dev,
+              int n_lags, int64_t n, float *xi2_dev, int64_t xi2_pitch, void *stream);
+
+/* out_dev [T][n] (f32): xi_C^2 at every (template, sample) of a coherent scan of the same SNR,
+ * from xi2_dev [T][n_det][xi2_pitch] in which entry H + k is sample k (H = the sky's halo,
+ * xi2_pitch >= n + 2 H) and argmax_dev [T][n] (the scan's argmax).  An argmax outside the sky
+ * gives NaN.  Device pointers, enqueued on stream.  Errors: SPIIR_EINVAL. */
+int spiir_xi2_network(spiir_sky_t sky, int n_templates, const float *xi2_dev, int64_t xi2_pitch,
+                      const int32_t *argmax_dev, int64_t n, float *out_dev, void *stream);
+
+/* ------------------------------------------------------------------------------------
  * Impulse response and its adjoint, for refining IIR coefficients against target
  * templates (the overlap of Sec. II.B.1 Eq. (overlap) is the usual objective).
  * Layout: T templates x F filters each (F <= 1024), row-major [T][F]; complex values are
@@ -237,7 +269,8 @@ int spiir_coherent_scan(spiir_sky_t sky, const float *snr_dev, int64_t snr_pitch
  *   ckpt_every a multiple of 32 in [32, 8192].  Delays may exceed n.  Enqueued on stream.
  * With checkpoints the segment starting states are found by FP64 jumps,
  *   y[(j+1)C - 1] = a^C y[jC - 1] + b a^((j+1)C - 1 - d) [jC <= d < (j+1)C],
- * and the segments run in parallel in FP32; without, one pass per template over all n. */
+ * and the segments run in parallel in FP32; without, one pass per template over all n, which
+ * holds at most 864 filters per template (SPIIR_EUNSUPPORTED above). */
 int spiir_impulse_forward(int n_templates, int filters_per_template, const float *a1_dev,
                           const float *b0_dev, const int32_t *delay_dev, const float *s0_dev,
                           int64_t n, float *u_dev, int ckpt_every, float *ckpt_dev, void *stream);

@@ -13,7 +13,8 @@ import numpy as np
 from . import native
 from .native import SpiirError, check
 
-__all__ = ["Bank", "Sky", "Pipeline", "Batch", "sky_tables", "SpiirError", "device_status", "version"]
+__all__ = ["Bank", "Sky", "Pipeline", "Batch", "sky_tables", "autocorr", "xi2", "xi2_network", "SpiirError",
+           "device_status", "version"]
 
 
 def _stream_ptr(stream=None):
@@ -316,3 +317,52 @@ class Batch:
             raise ValueError("strain must be a contiguous [n_det][chunk] tensor")
         check(native.lib().spiir_batch_run(self._h, int(mode), _dev_ptr(strain), _dev_ptr(max_stat),
                                            _dev_ptr(argmax), _dev_ptr(null_stat), _stream_ptr(stream)))
+
+
+# ------------------------------------------------------------------------------------------------
+# Signal-consistency statistic (spiir_autocorr, spiir_xi2, spiir_xi2_network)
+
+
+def autocorr(u, n_lags: int, out=None, stream=None):
+    """Template autocorrelation A [T][2 n_lags + 1] (complex64 CUDA tensor) of the responses
+    u [T][n_resp] (complex64 CUDA tensor); entry n_lags + j is lag j."""
+    import torch
+    _require_cuda(u, torch.complex64, "u")
+    if u.dim() != 2 or not u.is_contiguous():
+        raise ValueError("u must be a contiguous [T][n_resp] tensor")
+    T, nr = u.shape
+    if out is None:
+        out = torch.empty((T, 2 * n_lags + 1), dtype=torch.complex64, device=u.device)
+    check(native.lib().spiir_autocorr(T, _dev_ptr(u), nr, int(n_lags), _dev_ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def xi2(snr, A, n_lags: int, n: int, out=None, stream=None):
+    """xi_I^2 [T][n_det][n] (float32 CUDA tensor) from snr [T][n_det][pitch] (complex64, entry
+    n_lags + k = sample k) and A [T][2 n_lags + 1]."""
+    import torch
+    _require_cuda(snr, torch.complex64, "snr")
+    _require_cuda(A, torch.complex64, "A")
+    if snr.dim() != 3 or not snr.is_contiguous() or not A.is_contiguous():
+        raise ValueError("snr must be a contiguous [T][n_det][pitch] tensor and A contiguous")
+    T, n_det, pitch = snr.shape
+    if out is None:
+        out = torch.empty((T, n_det, n), dtype=torch.float32, device=snr.device)
+    _require_cuda(out, torch.float32, "out")
+    check(native.lib().spiir_xi2(T, n_det, _dev_ptr(snr), pitch, _dev_ptr(A), int(n_lags), int(n), _dev_ptr(out),
+                                 out.shape[-1], _stream_ptr(stream)))
+    return out
+
+
+def xi2_network(sky, xi, argmax, n: int, out=None, stream=None):
+    """xi_C^2 [T][n] from xi [T][n_det][pitch] (entry H + k = sample k, H = sky.halo) and the
+    coherent scan's argmax [T][n]."""
+    import torch
+    _require_cuda(xi, torch.float32, "xi")
+    _require_cuda(argmax, torch.int32, "argmax")
+    T = xi.shape[0]
+    if out is None:
+        out = torch.empty((T, n), dtype=torch.float32, device=xi.device)
+    check(native.lib().spiir_xi2_network(sky.handle, T, _dev_ptr(xi), xi.shape[-1], _dev_ptr(argmax), int(n),
+                                         _dev_ptr(out), _stream_ptr(stream)))
+    return out

@@ -546,6 +546,15 @@ extern "C" int spiir_impulse_forward(int T, int F, const float *a1, const float 
         const size_t smem = (size_t)nt * (kAdjR + 1) * sizeof(float2) + (size_t)(nt / 32) * kAdjR * sizeof(float2);
         const dim3 grid((unsigned)nck, (unsigned)T);
         float2 *U = reinterpret_cast<float2 *>(u);
+        static bool attr = false;
+        if (!attr) {  // up to 256 threads x 33 float2 of reduction rows: above the 48 KB default
+            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+            attr = true;
+        }
         switch (S) {
             case 2: k_fwd_seg<2><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
             case 4: k_fwd_seg<4><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
@@ -559,6 +568,9 @@ extern "C" int spiir_impulse_forward(int T, int F, const float *a1, const float 
     // no checkpoints: one block per template, sequential over all samples
     const int nt = (F + 31) / 32 * 32;
     const size_t smem = (size_t)nt * (kAdjR + 1) * sizeof(float2);
+    if (smem > 227 * 1024)
+        return fail(SPIIR_EUNSUPPORTED, "%d filters per template need a checkpoint buffer (the sequential form "
+                                        "fits %d)", F, 227 * 1024 / ((kAdjR + 1) * (int)sizeof(float2)) / 32 * 32);
     static bool attr_seq = false;
     if (!attr_seq) {
         SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_impulse_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));

@@ -553,6 +553,7 @@ static void sky_free(spiir_sky_s *s) {
     dev_free(s->g_orig);
     dev_free(s->g_grp);
     dev_free(s->t_ent);
+    dev_free(s->d_delays);
     delete s;
 }
 
@@ -699,6 +700,12 @@ extern "C" int spiir_sky_create(int n_det, int n_pix, const int32_t *delays, con
     }
     if (rc == SPIIR_OK) {
         s->h_delays.assign(delays, delays + (size_t)n_pix * n_det);
+        std::vector<int16_t> d16(s->h_delays.begin(), s->h_delays.end());
+        rc = dev_alloc((void **)&s->d_delays, sizeof(int16_t) * d16.size(), "sky delays");
+        if (rc == SPIIR_OK && cudaMemcpy(s->d_delays, d16.data(), sizeof(int16_t) * d16.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = fail(SPIIR_ECUDA, "copy of the sky delays failed");
+    }
+    if (rc == SPIIR_OK) {
         s->h_usig.assign(u_sig, u_sig + (size_t)n_pix * n_det * 2);
         if (n_det > 2) s->h_unull.assign(u_null, u_null + (size_t)n_pix * n_det * (n_det - 2));
         rc = build_grouped(s, delays, u_sig, u_null);

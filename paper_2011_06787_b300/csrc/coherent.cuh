@@ -103,6 +103,7 @@ struct spiir_sky_s {
     int t_slice[5] = {0, 0, 0, 0, 0};
     // inputs kept to rebuild the grouped tables when the launch shape changes
     std::vector<int32_t> h_delays;
+    int16_t *d_delays = nullptr;  // [P][n_det] on the device (signal-consistency gather)
     std::vector<float> h_usig, h_unull;
 };
 

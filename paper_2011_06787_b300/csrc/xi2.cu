@@ -1,0 +1,219 @@
+// Signal-consistency statistic (Sec. II.C.2): for template t, detector I and sample k,
+//     xi_I^2[k] = sum_{j=-Nj}^{Nj} |z_I[k + j] - z_I[k] A_t[j]|^2 / sum_{j=-Nj}^{Nj} (2 - 2 |A_t[j]|^2),
+// A_t the template's autocorrelation, A[j] = R[j] / R[0], R[j] = sum_k conj(u[k]) u[k + j], and
+// the network average xi_C^2 = (1 / N_d) sum_I xi_I^2 at the detectors' arrival times of the
+// coherent argmax pixel.
+//
+// xi^2 kernel: a block covers 1024 samples of one (template, detector) with 128 threads of 8
+// consecutive samples.  The SNR tile (1024 + 2 Nj + 8 samples) is staged in shared memory
+// transposed by 8 (element x at (x % 8) L + x / 8), so the 32 threads of a warp reading sample
+// 8 r + c hit 32 consecutive words.  Each thread keeps the 8-sample window z[k + j] of its
+// samples in registers and slides it by one sample per tap (one shared load); the registers
+// rotate with the tap index, unrolled by 8, so no moves are needed.  Per tap and sample the
+// difference d = z[k + j] - z[k] A[j] and its squared modulus take three packed FP32 FMAs
+// against a broadcast table entry (-A.re, -A.im, A.im, -A.re).
+#include <algorithm>
+
+#include "coherent.cuh"
+
+namespace spiir {
+
+constexpr int kXiThreads = 128, kXiM = 8, kXiKT = kXiThreads * kXiM;
+constexpr int kXiMaxLags = 1024;
+
+__device__ __forceinline__ int xpos(int x, int L) { return (x & 7) * L + (x >> 3); }
+
+__global__ void __launch_bounds__(kXiThreads) k_xi2(const float2 *__restrict__ snr, int64_t pitch,
+                                                    const float2 *__restrict__ A, int Nj, int64_t n, int n_det,
+                                                    float *__restrict__ out, int64_t opitch) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int t = blockIdx.z, I = blockIdx.y, tid = threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.x * kXiKT;
+    const int ntap = 2 * Nj + 1;
+    const int W = kXiKT + 2 * Nj + kXiM;  // staged samples
+    const int L = W / 8 + 1;
+    float4 *tab = reinterpret_cast<float4 *>(smem);           // [ntap]
+    float2 *zt = reinterpret_cast<float2 *>(tab + ntap);      // [8 L] transposed tile
+    __shared__ float den_part[kXiThreads / 32];
+    const float2 *At = A + (int64_t)t * ntap;
+    float dsum = 0.f;
+    for (int j = tid; j < ntap; j += kXiThreads) {
+        const float2 a = At[j];
+        tab[j] = make_float4(-a.x, -a.y, a.y, -a.x);
+        dsum += 2.f - 2.f * (a.x * a.x + a.y * a.y);
+    }
+    const float2 *row = snr + ((int64_t)t * n_det + I) * pitch + k0;
+    const int64_t lim = n + 2 * Nj - k0;  // entries of the row this tile may read
+    for (int x = tid; x < W; x += kXiThreads) zt[xpos(x, L)] = x < lim ? row[x] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((tid & 31) == 0) den_part[tid >> 5] = dsum;
+    __syncthreads();
+    float den = 0.f;
+#pragma unroll
+    for (int w = 0; w < kXiThreads / 32; ++w) den += den_part[w];
+
+    const int base = kXiM * tid;  // tile position of this thread's first sample at tap -Nj
+    if (k0 + base >= n) return;   // all of this thread's samples lie past the end (no barrier follows)
+    u64 z0r[kXiM], z0i[kXiM], w[kXiM], acc[kXiM];
+#pragma unroll
+    for (int m = 0; m < kXiM; ++m) {
+        const float2 c = zt[xpos(base + m + Nj, L)];
+        z0r[m] = pack2(c.x, c.x);
+        z0i[m] = pack2(c.y, c.y);
+        const float2 v = zt[xpos(base + m, L)];
+        w[m] = pack2(v.x, v.y);
+        acc[m] = 0;
+    }
+    // tap s (j = s - Nj): logical window element m (sample m of this thread) is w[(m + s) % 8];
+    // afterwards w[s % 8] takes the element that enters at the next tap
+    auto tap = [&](int s, int u) {
+        const float4 e = tab[s];
+        const u64 M1 = pack2(e.x, e.y), M2 = pack2(e.z, e.w);
+#pragma unroll
+        for (int m = 0; m < kXiM; ++m) {
+            const u64 d = fma2(z0i[m], M2, fma2(z0r[m], M1, w[(m + u) & 7]));
+            acc[m] = fma2(d, d, acc[m]);
+        }
+        const float2 v = zt[xpos(base + s + kXiM, L)];
+        w[u] = pack2(v.x, v.y);
+    };
+    int s = 0;
+    for (; s + 8 <= ntap; s += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tap(s + u, u);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        if (s + u < ntap) tap(s + u, u);
+
+    float *orow = out + ((int64_t)t * n_det + I) * opitch + k0 + base;
+    const float rden = 1.f / den;
+    float r[kXiM];
+#pragma unroll
+    for (int m = 0; m < kXiM; ++m) {
+        const float2 a = unpack2(acc[m]);
+        r[m] = (a.x + a.y) * rden;
+    }
+    const int64_t kk = k0 + base;
+#pragma unroll
+    for (int m = 0; m < kXiM; ++m)
+        if (kk + m < n) orow[m] = r[m];
+}
+
+// R[j] and R[0] of one template, one block per (lag, template)
+__global__ void k_autocorr(const float2 *__restrict__ u, int64_t nr, int Nj, float2 *__restrict__ A) {
+    const int j = blockIdx.x, t = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+    const float2 *ut = u + (int64_t)t * nr;
+    float rj_x = 0.f, rj_y = 0.f, r0 = 0.f;
+    for (int64_t k = tid; k < nr; k += nt) {
+        const float2 a = ut[k];
+        r0 = fmaf(a.x, a.x, fmaf(a.y, a.y, r0));
+        if (k + j < nr) {
+            const float2 b = ut[k + j];
+            // conj(a) b
+            rj_x = fmaf(a.x, b.x, fmaf(a.y, b.y, rj_x));
+            rj_y = fmaf(a.x, b.y, fmaf(-a.y, b.x, rj_y));
+        }
+    }
+    __shared__ float part[3][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rj_x += __shfl_xor_sync(0xffffffffu, rj_x, o);
+        rj_y += __shfl_xor_sync(0xffffffffu, rj_y, o);
+        r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+    }
+    if ((tid & 31) == 0) {
+        part[0][tid >> 5] = rj_x;
+        part[1][tid >> 5] = rj_y;
+        part[2][tid >> 5] = r0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float sx = 0.f, sy = 0.f, s0 = 0.f;
+        for (int w = 0; w < nt / 32; ++w) {
+            sx += part[0][w];
+            sy += part[1][w];
+            s0 += part[2][w];
+        }
+        float2 *At = A + (int64_t)t * (2 * Nj + 1);
+        At[Nj + j] = make_float2(sx / s0, sy / s0);
+        At[Nj - j] = make_float2(sx / s0, -sy / s0);
+    }
+}
+
+// xi_C^2 at every (template, sample): the mean of each detector's xi^2 at k + Delta_I(argmax)
+__global__ void k_xi2_network(const float *__restrict__ xi, int64_t pitch, const int32_t *__restrict__ argmax,
+                              const int16_t *__restrict__ dl, int n_det, int P, int H, int64_t Tn, int64_t n,
+                              float *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= Tn) return;
+    const int64_t t = i / n, k = i % n;
+    const int p = argmax[i];
+    if (p < 0 || p >= P) {
+        out[i] = __int_as_float(0x7fc00000);  // NaN: not a pixel of this sky
+        return;
+    }
+    float s = 0.f;
+    for (int I = 0; I < n_det; ++I) s += xi[(t * n_det + I) * pitch + H + k + dl[p * n_det + I]];
+    out[i] = s / n_det;
+}
+
+}  // namespace spiir
+
+using namespace spiir;
+
+extern "C" int spiir_autocorr(int T, const float *u, int64_t n_resp, int n_lags, float *A, void *stream) {
+    clear_error();
+    if (T < 1 || n_resp < 1) return fail(SPIIR_EINVAL, "n_templates = %d, n_resp = %lld", T, (long long)n_resp);
+    if (n_lags < 0 || n_lags > kXiMaxLags) return fail(SPIIR_EINVAL, "n_lags = %d outside [0, %d]", n_lags, kXiMaxLags);
+    if (!u || !A) return fail(SPIIR_EINVAL, "NULL pointer");
+    k_autocorr<<<dim3((unsigned)(n_lags + 1), (unsigned)T), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float2 *>(u), n_resp, n_lags, reinterpret_cast<float2 *>(A));
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_xi2(int T, int n_det, const float *snr, int64_t snr_pitch, const float *A, int n_lags, int64_t n,
+                         float *xi2, int64_t xi2_pitch, void *stream) {
+    clear_error();
+    if (T < 1 || n_det < 1 || n < 1) return fail(SPIIR_EINVAL, "n_templates = %d, n_det = %d, n = %lld", T, n_det, (long long)n);
+    if (T > 65535 || n_det > 65535) return fail(SPIIR_EINVAL, "n_templates and n_det must be at most 65535");
+    if (n_lags < 0 || n_lags > kXiMaxLags) return fail(SPIIR_EINVAL, "n_lags = %d outside [0, %d]", n_lags, kXiMaxLags);
+    if (!snr || !A || !xi2) return fail(SPIIR_EINVAL, "NULL pointer");
+    if (snr_pitch < n + 2 * (int64_t)n_lags)
+        return fail(SPIIR_EINVAL, "snr_pitch %lld < n + 2 n_lags = %lld", (long long)snr_pitch,
+                    (long long)(n + 2 * (int64_t)n_lags));
+    if (xi2_pitch < n) return fail(SPIIR_EINVAL, "xi2_pitch %lld < n", (long long)xi2_pitch);
+    if (((uintptr_t)snr) % 8 || ((uintptr_t)A) % 8) return fail(SPIIR_EINVAL, "snr and A must be 8-byte aligned");
+    const int ntap = 2 * n_lags + 1;
+    const int W = kXiKT + 2 * n_lags + kXiM, L = W / 8 + 1;
+    const size_t smem = (size_t)ntap * sizeof(float4) + (size_t)8 * L * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_xi2, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        attr = true;
+    }
+    const dim3 grid((unsigned)((n + kXiKT - 1) / kXiKT), (unsigned)n_det, (unsigned)T);
+    k_xi2<<<grid, kXiThreads, smem, (cudaStream_t)stream>>>(reinterpret_cast<const float2 *>(snr), snr_pitch,
+                                                             reinterpret_cast<const float2 *>(A), n_lags, n, n_det,
+                                                             xi2, xi2_pitch);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_xi2_network(spiir_sky_t sky, int T, const float *xi2, int64_t xi2_pitch, const int32_t *argmax,
+                                 int64_t n, float *out, void *stream) {
+    clear_error();
+    if (!sky) return fail(SPIIR_EINVAL, "sky is NULL");
+    if (T < 1 || n < 1) return fail(SPIIR_EINVAL, "n_templates = %d, n = %lld", T, (long long)n);
+    if (!xi2 || !argmax || !out) return fail(SPIIR_EINVAL, "NULL pointer");
+    if (xi2_pitch < n + 2 * (int64_t)sky->halo)
+        return fail(SPIIR_EINVAL, "xi2_pitch %lld < n + 2 H = %lld", (long long)xi2_pitch,
+                    (long long)(n + 2 * (int64_t)sky->halo));
+    const int64_t Tn = (int64_t)T * n;
+    k_xi2_network<<<(unsigned)((Tn + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        xi2, xi2_pitch, argmax, sky->d_delays, sky->n_det, sky->n_pix, sky->halo, Tn, n, out);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}

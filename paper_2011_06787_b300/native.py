@@ -54,6 +54,9 @@ SIGNATURES = {
     "spiir_sky_destroy": (None, [_P]),
     "spiir_sky_info": (_I, [_P, _P, _P, _P]),
     "spiir_coherent_scan": (_I, [_P, _P, _I64, _I, _I64, _P, _P, _P, _P, _P]),
+    "spiir_autocorr": (_I, [_I, _P, _I64, _I, _P, _P]),
+    "spiir_xi2": (_I, [_I, _I, _P, _I64, _P, _I, _I64, _P, _I64, _P]),
+    "spiir_xi2_network": (_I, [_P, _I, _P, _I64, _P, _I64, _P, _P]),
     "spiir_impulse_forward": (_I, [_I, _I, _P, _P, _P, _P, _I64, _P, _I, _P, _P]),
     "spiir_impulse_backward": (_I, [_I, _I, _P, _P, _P, _I64, _P, _I, _P, _P, _P, _P, _P, _P]),
     "spiir_batch_create": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _I64, ctypes.POINTER(_P)]),
