@@ -73,6 +73,8 @@ def _load():
         lib.oracle_impulse_forward.restype = None
         lib.oracle_impulse_backward.argtypes = [ctypes.c_int, P, P, P, P, P, i64, P, P, P, P]
         lib.oracle_impulse_backward.restype = ctypes.c_int
+        lib.oracle_coherent_points.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, i64, i64, P, P, P, P, P]
+        lib.oracle_coherent_points.restype = ctypes.c_int
         lib.oracle_autocorr.argtypes = [ctypes.c_int, P, i64, ctypes.c_int, P]
         lib.oracle_autocorr.restype = None
         lib.oracle_xi2.argtypes = [ctypes.c_int, ctypes.c_int, P, i64, P, ctypes.c_int, i64, P]
@@ -468,4 +470,65 @@ def xi2_network(xi, delays, argmax, H: int):
         for k in range(n):
             d = delays[argmax[t, k]]
             out[t, k] = sum(xi[t, I, H + k + d[I]] for I in range(n_det)) / n_det
+    return out
+
+
+# --------------------------------------------------------------------------------------------
+# Candidate selection and the candidate-driven scan: Sec. II.C.1; background: Sec. II.C.3
+
+
+def select_candidates(z, off: int, n: int, threshold: float = 4.0, per_second: int = 2048):
+    """Single-detector candidates of one bank (Sec. II.C.1): for every detector and sample, the
+    largest |z| over the bank's templates (the lowest template among equals); samples where it
+    exceeds the threshold are candidates of that template; a template keeps only its largest
+    candidate per second (the earliest among equals).  z [T][n_det][pitch], entry off + k =
+    sample k; the n samples are split into seconds of per_second samples from sample 0.
+    Returns a list of (detector, template, sample, |z|) sorted by detector, then template, then
+    second."""
+    z = np.asarray(z)
+    T, n_det, _ = z.shape
+    out = []
+    for I in range(n_det):
+        mag = np.abs(z[:, I, off: off + n].astype(np.complex128))  # [T][n]
+        best_t = np.argmax(mag, axis=0)
+        best = mag[best_t, np.arange(n)]
+        for t in range(T):
+            for s0 in range(0, n, per_second):
+                ks = [k for k in range(s0, min(n, s0 + per_second)) if best[k] > threshold and best_t[k] == t]
+                if ks:
+                    k = max(ks, key=lambda q: (best[q], -q))
+                    out.append((I, t, k, float(best[k])))
+    return out
+
+
+def coherent_points(z, G, delays, pts, shifts):
+    """Coherent statistic at points (template, reference detector, buffer entry of its sample)
+    with per-detector extra offsets; see oracle_coherent_points.  Returns (max, argmax, null)."""
+    lib = _load()
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    delays = np.ascontiguousarray(delays, dtype=np.int32)
+    pts = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
+    shifts = np.ascontiguousarray(shifts, dtype=np.int64).reshape(pts.shape[0], -1)
+    T, n_det, pitch = z.shape
+    m = pts.shape[0]
+    ms = np.zeros(m)
+    am = np.zeros(m, dtype=np.int32)
+    nl = np.zeros(m)
+    rc = lib.oracle_coherent_points(n_det, G.shape[0], _ptr(G), _ptr(delays), _ptr(z), pitch, m, _ptr(pts),
+                                    _ptr(shifts), _ptr(ms), _ptr(am), _ptr(nl))
+    if rc != 0:
+        raise ValueError(f"oracle_coherent_points failed ({rc})")
+    return ms, am, nl
+
+
+def background_shifts(ref: int, n_det: int, s: int, step: int):
+    """Offsets of time shift s (Sec. II.C.3): the reference detector is unshifted and the c-th
+    other detector (c = 1, 2, ...) is read s c step samples earlier."""
+    out = np.zeros(n_det, dtype=np.int64)
+    c = 0
+    for J in range(n_det):
+        if J != ref:
+            c += 1
+            out[J] = -s * c * step
     return out

@@ -86,17 +86,14 @@ int oracle_filter_bank(int n_det, int T, const int64_t *off, const cplx *a1, con
  * dominant direction only (rank 1); the paper does not treat this measure-zero case.
  * Returns 0, or -1 if a read would fall outside [0, pitch).
  */
-int oracle_coherent(int n_det, int P, const double *G, const int32_t *delay, int T,
-                    const cplx *z, int64_t pitch, int64_t H, int64_t n, double *max_stat,
-                    int32_t *argmax, double *null_stat, double *skymap)
+/*
+ * Projector onto the column space of G_sigma for every pixel: Pi = G (G^T G)^-1 G^T from the
+ * normal equations (no SVD); rank <= 1 pixels project onto the dominant direction.
+ * Pi [P][n_det][n_det] out.
+ */
+static void build_projectors(int n_det, int P, const double *G, double *Pi)
 {
-    double *Pi = (double *)malloc(sizeof(double) * (size_t)P * n_det * n_det);
-    if (!Pi) return -2;
     for (int p = 0; p < P; ++p) {
-        for (int di = 0; di < n_det; ++di) {
-            int dd = delay[(int64_t)p * n_det + di];
-            if (H + dd < 0 || H + dd + n > pitch) { free(Pi); return -1; }
-        }
         const double *g = G + (int64_t)p * n_det * 2;
         double m00 = 0, m01 = 0, m11 = 0; /* G^T G */
         for (int di = 0; di < n_det; ++di) {
@@ -122,13 +119,26 @@ int oracle_coherent(int n_det, int P, const double *G, const int32_t *delay, int
             double vn = sqrt(vx * vx + vy * vy);
             vx /= vn; vy /= vn;
             double un = 0;
-            double *u = (double *)malloc(sizeof(double) * n_det);
+            double u[8];
             for (int di = 0; di < n_det; ++di) { u[di] = g[2 * di] * vx + g[2 * di + 1] * vy; un += u[di] * u[di]; }
             for (int di = 0; di < n_det; ++di)
                 for (int dj = 0; dj < n_det; ++dj) pp[di * n_det + dj] = (un > 0) ? u[di] * u[dj] / un : 0.0;
-            free(u);
         }
     }
+}
+
+int oracle_coherent(int n_det, int P, const double *G, const int32_t *delay, int T,
+                    const cplx *z, int64_t pitch, int64_t H, int64_t n, double *max_stat,
+                    int32_t *argmax, double *null_stat, double *skymap)
+{
+    for (int p = 0; p < P; ++p)
+        for (int di = 0; di < n_det; ++di) {
+            int dd = delay[(int64_t)p * n_det + di];
+            if (H + dd < 0 || H + dd + n > pitch) return -1;
+        }
+    double *Pi = (double *)malloc(sizeof(double) * (size_t)P * n_det * n_det);
+    if (!Pi) return -2;
+    build_projectors(n_det, P, G, Pi);
 #pragma omp parallel
     {
         cplx *w = (cplx *)malloc(sizeof(cplx) * n_det);
@@ -277,4 +287,56 @@ void oracle_xi2(int T, int n_det, const cplx *z, int64_t pitch, const cplx *A, i
             }
         }
     }
+}
+
+/*
+ * Coherent statistic at given points instead of on a grid of geocentric times.  Point i names
+ * a template t, a reference detector r and the buffer entry e of the reference detector's
+ * sample, plus an extra offset per detector (0 for the foreground; the time shifts of a
+ * background event).  For every pixel p the delayed vector is
+ *     w_I = z[t][I][e + Delta_I(p) - Delta_r(p) + shift_I],
+ * i.e. the reference detector is read at its own sample and the others at the times a source
+ * in direction p implies; the statistic is w^H Pi_p w (Sec. II.C.1 Eq. (llr_form)).
+ *   pts    [n_pts][3] int64: t, r, e;   shifts [n_pts][n_det] int64
+ *   out: max_stat, argmax (lowest p among equals), null (sum |w|^2 - rho^2 at the argmax).
+ * Returns 0, or -1 if a read falls outside [0, pitch).
+ */
+int oracle_coherent_points(int n_det, int P, const double *G, const int32_t *delay, const cplx *z,
+                           int64_t pitch, int64_t n_pts, const int64_t *pts, const int64_t *shifts,
+                           double *max_stat, int32_t *argmax, double *null_stat)
+{
+    double *Pi = (double *)malloc(sizeof(double) * (size_t)P * n_det * n_det);
+    if (!Pi) return -2;
+    build_projectors(n_det, P, G, Pi);
+    int err = 0;
+#pragma omp parallel
+    {
+        cplx w[8];
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n_pts; ++i) {
+            const int64_t t = pts[3 * i], r = pts[3 * i + 1], e = pts[3 * i + 2];
+            double best = -INFINITY, best_null = 0.0;
+            int32_t best_p = -1;
+            for (int p = 0; p < P; ++p) {
+                double norm2 = 0.0;
+                for (int di = 0; di < n_det; ++di) {
+                    const int64_t x = e + delay[(int64_t)p * n_det + di] - delay[(int64_t)p * n_det + r] +
+                                      shifts[i * n_det + di];
+                    if (x < 0 || x >= pitch) { err = -1; w[di] = 0.0; continue; }
+                    w[di] = z[(t * n_det + di) * pitch + x];
+                    norm2 += creal(w[di]) * creal(w[di]) + cimag(w[di]) * cimag(w[di]);
+                }
+                const double *pp = Pi + (int64_t)p * n_det * n_det;
+                double rho2 = 0.0;
+                for (int di = 0; di < n_det; ++di)
+                    for (int dj = 0; dj < n_det; ++dj) rho2 += pp[di * n_det + dj] * creal(conj(w[di]) * w[dj]);
+                if (rho2 > best) { best = rho2; best_p = p; best_null = norm2 - rho2; }
+            }
+            max_stat[i] = best;
+            argmax[i] = best_p;
+            null_stat[i] = best_null;
+        }
+    }
+    free(Pi);
+    return err;
 }

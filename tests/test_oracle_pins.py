@@ -546,3 +546,92 @@ def test_network_average_reads_each_detector_at_its_arrival_time():
             p = argmax[t, k]
             expect = np.mean([xi[t, I, H + k + delays[p, I]] for I in range(n_det)])
             assert out[t, k] == expect
+
+
+# ---------------------------------------------------------------------------------------------
+# Candidate selection and the candidate-driven scan (Sec. II.C.1), time-shift background
+# (Sec. II.C.3)
+
+
+def test_candidate_selection_on_constructed_peaks():
+    """Largest SNR over the bank per sample, kept when over 4; one candidate per template per
+    second (the largest, the earliest among equals); the lowest template among equal maxima."""
+    T, nd, n, sec = 4, 2, 4096, 2048
+    z = np.zeros((T, nd, n), np.complex128)
+    put = lambda t, I, k, v: z.__setitem__((t, I, k), v * np.exp(0.3j * (k % 7)))
+    put(1, 0, 100, 5.0); put(1, 0, 300, 7.0)         # same template, same second: only 300
+    put(2, 0, 500, 4.0)                               # exactly 4: not over the threshold
+    put(3, 0, 2100, 6.0)                              # second 1
+    put(0, 0, 700, 5.0); put(3, 0, 700, 5.5)          # template 3 holds the maximum at 700
+    put(0, 0, 900, 6.0); put(2, 0, 900, 6.0)          # equal maxima: template 0
+    put(2, 0, 1000, 5.0); put(2, 0, 1200, 5.0)        # equal values in one second: the earlier
+    put(1, 1, 2047, 4.5); put(1, 1, 2048, 4.6)        # either side of the second boundary
+    got = oracle.select_candidates(z, 0, n, 4.0, sec)
+    expect = [(0, 0, 900, 6.0), (0, 1, 300, 7.0), (0, 2, 1000, 5.0), (0, 3, 700, 5.5), (0, 3, 2100, 6.0),
+              (1, 1, 2047, 4.5), (1, 1, 2048, 4.6)]
+    assert [(a, b, c) for a, b, c, _ in got] == [(a, b, c) for a, b, c, _ in expect]
+    np.testing.assert_allclose([v for *_, v in got], [v for *_, v in expect], rtol=1e-12)
+
+
+def test_point_scan_with_two_detectors_is_the_power_at_the_implied_times():
+    """N_d = 2 (rank-2 G): the statistic at every pixel is |w_0|^2 + |w_1|^2, w read at the
+    reference detector's own sample and the other detector at e + Delta_1(p) - Delta_r(p)."""
+    g = _rng(21)
+    P, n, H = 11, 80, 4
+    G = _random_g(g, P, 2)
+    delays = g.integers(-H, H + 1, (P, 2)).astype(np.int32)
+    z = g.standard_normal((2, 2, n)) + 1j * g.standard_normal((2, 2, n))
+    pts = np.array([[0, 0, 20], [1, 1, 40], [1, 0, 2 * H]], np.int64)
+    ms, am, nl = oracle.coherent_points(z, G, delays, pts, np.zeros((3, 2), np.int64))
+    for i, (t, r, e) in enumerate(pts):
+        power = [sum(abs(z[t, I, e + delays[p, I] - delays[p, r]]) ** 2 for I in range(2)) for p in range(P)]
+        assert am[i] == int(np.argmax(power))
+        np.testing.assert_allclose(ms[i], max(power), rtol=1e-12)
+        assert abs(nl[i]) < 1e-10 * ms[i]
+
+
+def test_point_scan_recovers_an_injection_from_any_reference_detector():
+    """A noiseless source in direction p*: read from any detector's arrival sample, the scan
+    keeps the whole power at p* with a vanishing null (Sec. II.C.1)."""
+    det = synth.detectors(1, 3)
+    sigma = np.array([0.7, 1.3, 1.9])
+    nhat, G, delays = oracle.sky_geometry(det, sigma, 4, 2048.0)
+    H = int(np.abs(delays).max())
+    g = _rng(22)
+    pstar, n, k0 = 101, 200, 100
+    A = g.standard_normal(2) + 1j * g.standard_normal(2)
+    amp = G[pstar] @ A
+    z = np.zeros((1, 3, n), np.complex128)
+    for I in range(3):
+        z[0, I, k0 + delays[pstar, I]] = amp[I]            # geocentric sample k0 arrives at k0 + Delta_I
+    tot = float(np.sum(np.abs(amp) ** 2))
+    for r in range(3):
+        pts = np.array([[0, r, k0 + delays[pstar, r]]], np.int64)
+        ms, am, nl = oracle.coherent_points(z, G, delays, pts, np.zeros((1, 3), np.int64))
+        assert am[0] == pstar and abs(ms[0] - tot) < 1e-10 * tot and abs(nl[0]) < 1e-10 * tot
+
+
+def test_background_shift_pairs_the_reference_with_earlier_companion_data():
+    """A companion detector holding the signal s c step samples earlier than coincidence is
+    realigned by time shift s and by no other (Sec. II.C.3: shifts of at least 0.1 s)."""
+    det = synth.detectors(1, 3)
+    sigma = np.array([1.0, 1.0, 1.0])
+    nhat, G, delays = oracle.sky_geometry(det, sigma, 2, 2048.0)
+    H = int(np.abs(delays).max())
+    g = _rng(23)
+    pstar, step, sstar, r = 20, 205, 3, 1
+    n = 2 * H + 3 * 100 * step
+    k0 = n - 2 * H - 1
+    A = g.standard_normal(2) + 1j * g.standard_normal(2)
+    amp = G[pstar] @ A
+    sh = oracle.background_shifts(r, 3, sstar, step)
+    z = 1e-6 * (g.standard_normal((1, 3, n)) + 1j * g.standard_normal((1, 3, n)))
+    for I in range(3):
+        z[0, I, k0 + delays[pstar, I] + sh[I]] += amp[I]
+    e = k0 + delays[pstar, r]
+    pts = np.array([[0, r, e]] * 6, np.int64)
+    shifts = np.stack([oracle.background_shifts(r, 3, s, step) for s in range(6)])
+    ms, am, nl = oracle.coherent_points(z, G, delays, pts, shifts)
+    tot = float(np.sum(np.abs(amp) ** 2))
+    assert int(np.argmax(ms)) == sstar and am[sstar] == pstar and abs(ms[sstar] - tot) < 1e-6 * tot
+    assert all(ms[s] < 0.9 * tot for s in range(6) if s != sstar)
