@@ -483,21 +483,28 @@ def select_candidates(z, off: int, n: int, threshold: float = 4.0, per_second: i
     exceeds the threshold are candidates of that template; a template keeps only its largest
     candidate per second (the earliest among equals).  z [T][n_det][pitch], entry off + k =
     sample k; the n samples are split into seconds of per_second samples from sample 0.
-    Returns a list of (detector, template, sample, |z|) sorted by detector, then template, then
-    second."""
+
+    Every comparison is made on |z|^2 in FP32, re*re + im*im with each operation rounded, against
+    threshold^2 rounded the same way (the values the GPU decides on; equal values are equal on
+    both sides).  Returns a list of (detector, template, sample, |z|) sorted by detector, then
+    template, then second; |z| is the square root, in FP64, of that FP32 |z|^2."""
     z = np.asarray(z)
     T, n_det, _ = z.shape
+    thr2 = np.float32(threshold) * np.float32(threshold)
     out = []
     for I in range(n_det):
-        mag = np.abs(z[:, I, off: off + n].astype(np.complex128))  # [T][n]
-        best_t = np.argmax(mag, axis=0)
-        best = mag[best_t, np.arange(n)]
-        for t in range(T):
-            for s0 in range(0, n, per_second):
-                ks = [k for k in range(s0, min(n, s0 + per_second)) if best[k] > threshold and best_t[k] == t]
-                if ks:
-                    k = max(ks, key=lambda q: (best[q], -q))
-                    out.append((I, t, k, float(best[k])))
+        w = z[:, I, off: off + n].astype(np.complex64)
+        re, im = w.real.astype(np.float32), w.imag.astype(np.float32)
+        m2 = re * re + im * im                          # [T][n] float32
+        best_t = np.argmax(m2, axis=0)                  # first (lowest) template among equals
+        best = m2[best_t, np.arange(n)]
+        kept = {}                                       # (template, second) -> sample
+        for k in np.flatnonzero(best > thr2):           # ascending: the earliest stays on ties
+            key = (int(best_t[k]), int(k) // per_second)
+            if key not in kept or best[k] > best[kept[key]]:
+                kept[key] = int(k)
+        for (t, _), k in sorted(kept.items()):
+            out.append((I, t, k, float(np.sqrt(np.float64(best[k])))))
     return out
 
 

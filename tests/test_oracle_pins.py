@@ -560,17 +560,27 @@ def test_candidate_selection_on_constructed_peaks():
     z = np.zeros((T, nd, n), np.complex128)
     put = lambda t, I, k, v: z.__setitem__((t, I, k), v * np.exp(0.3j * (k % 7)))
     put(1, 0, 100, 5.0); put(1, 0, 300, 7.0)         # same template, same second: only 300
-    put(2, 0, 500, 4.0)                               # exactly 4: not over the threshold
+    put(2, 0, 497, 4.0)                               # exactly 4 (phase 0): not over the threshold
     put(3, 0, 2100, 6.0)                              # second 1
     put(0, 0, 700, 5.0); put(3, 0, 700, 5.5)          # template 3 holds the maximum at 700
     put(0, 0, 900, 6.0); put(2, 0, 900, 6.0)          # equal maxima: template 0
-    put(2, 0, 1000, 5.0); put(2, 0, 1200, 5.0)        # equal values in one second: the earlier
+    put(2, 0, 1000, 5.0); put(2, 0, 1203, 5.0)        # equal values (same phase) in one second: the earlier
     put(1, 1, 2047, 4.5); put(1, 1, 2048, 4.6)        # either side of the second boundary
     got = oracle.select_candidates(z, 0, n, 4.0, sec)
     expect = [(0, 0, 900, 6.0), (0, 1, 300, 7.0), (0, 2, 1000, 5.0), (0, 3, 700, 5.5), (0, 3, 2100, 6.0),
               (1, 1, 2047, 4.5), (1, 1, 2048, 4.6)]
     assert [(a, b, c) for a, b, c, _ in got] == [(a, b, c) for a, b, c, _ in expect]
-    np.testing.assert_allclose([v for *_, v in got], [v for *_, v in expect], rtol=1e-12)
+    np.testing.assert_allclose([v for *_, v in got], [v for *_, v in expect], rtol=1e-6)
+
+
+def test_candidate_threshold_is_decided_in_fp32():
+    """|z| just above 4 in FP64 but 4 after rounding to FP32 is not a candidate; the next FP32
+    value above 4 is (the decision is taken on FP32 |z|^2, as on the GPU)."""
+    z = np.zeros((1, 1, 8), np.complex128)
+    z[0, 0, 2] = 4.0 + 1e-9
+    z[0, 0, 5] = float(np.nextafter(np.float32(4.0), np.float32(5.0)))
+    got = oracle.select_candidates(z, 0, 8, 4.0, 8)
+    assert [(a, b, c) for a, b, c, _ in got] == [(0, 0, 5)]
 
 
 def test_point_scan_with_two_detectors_is_the_power_at_the_implied_times():
