@@ -256,6 +256,64 @@ int spiir_xi2_network(spiir_sky_t sky, int n_templates, const float *xi2_dev, in
                       const int32_t *argmax_dev, int64_t n, float *out_dev, void *stream);
 
 /* ------------------------------------------------------------------------------------
+ * Candidates and the time-shift background (Sec. II.C.1, II.C.3).
+ * A single-detector candidate is a sample k of detector I at which the largest |z_I| over
+ * the bank's templates exceeds the threshold (4 in the paper); it belongs to the template
+ * that attains that maximum (the lowest template among equals), and each template keeps at
+ * most one candidate per second: its largest, the earliest among equals.  Seconds are
+ * counted from sample 0 of the analysed span in blocks of per_second samples.  Every
+ * comparison is made on |z|^2 = re*re + im*im in FP32 with each operation rounded, against
+ * threshold^2 rounded the same way, so the selection is exact and reproducible.
+ * Each candidate is then evaluated coherently at every sky pixel p: its own detector is read
+ * at its sample and every other detector J at k + Delta_J(p) - Delta_I(p) + shift_J, the
+ * times a source in direction p implies.  Time shift s moves the c-th other detector of I
+ * (c = 1, 2, ... in detector order) by shift_J = -s c step samples (it is read earlier);
+ * s = 0 is the zero-lag (foreground) statistic, s = 1..100 with step = 205 (0.1 s at
+ * 2048 Hz) the paper's background.
+ * ---------------------------------------------------------------------------------- */
+
+/* Bytes of the workspace spiir_select_candidates needs: one 64-bit slot per
+ * (detector, template, second).  Errors: SPIIR_EINVAL. */
+int spiir_select_workspace_bytes(int n_templates, int n_det, int64_t n, int per_second,
+                                 size_t *bytes);
+
+/* Select the candidates of samples 0 .. n-1 of snr_dev [T][n_det][snr_pitch] complex, in
+ * which entry snr_offset + k is sample k (snr_offset + n <= snr_pitch; n < 2^31).
+ *   workspace_dev: device buffer of at least spiir_select_workspace_bytes, 8-byte aligned,
+ *       ALL ZERO on entry (cudaMemset once after allocation); the call leaves it zero.
+ *   cand_dev [max_cand][4] int32, 16-byte aligned: (detector, template, sample, bits of the
+ *       FP32 |z|^2) ordered by detector, then template, then second.
+ *   n_cand_dev: one int32 on the device, set to the number of candidates found (records past
+ *       max_cand are dropped: a count above max_cand signals the overflow).
+ * Two launches on stream; nothing is synchronised and nothing returns to the host.  The
+ * threshold must be finite and >= 0.  NaN SNR values are never candidates.
+ * Errors: SPIIR_EINVAL. */
+int spiir_select_candidates(int n_templates, int n_det, const float *snr_dev, int64_t snr_pitch,
+                            int64_t snr_offset, int64_t n, float threshold, int per_second,
+                            void *workspace_dev, size_t workspace_bytes, int32_t *cand_dev,
+                            int max_cand, int32_t *n_cand_dev, void *stream);
+
+/* Coherent statistic at the first min(*n_cand_dev, max_cand) candidates of cand_dev (the
+ * records of spiir_select_candidates, or any (detector, template, sample, unused) records),
+ * under the time shifts s = first_shift .. first_shift + n_shifts - 1 (shift_step samples
+ * per unit), on the SNR snr_dev [T][n_det][snr_pitch] in which entry snr_offset + k is
+ * sample k.  Outputs [max_cand][n_shifts] (row c, column s - first_shift):
+ *   max_dev    max over pixels of rho_C^2 (same U tables and arithmetic as
+ *              spiir_coherent_scan), argmax_dev the pixel (lowest among equals),
+ *   null_dev   the null stream at that pixel (0 for two detectors).
+ * An entry whose reads would leave [0, snr_pitch) for some pixel, or whose record names a
+ * detector or template outside the sky or bank, is (NaN, -1, NaN).  Rows past the count are
+ * not written.  For the background the SNR must hold first_shift + n_shifts - 1 times
+ * (n_det - 1) shift_step samples of history before the earliest candidate, plus the sky's
+ * delay range.  One persistent launch on stream; the count is read on the device.
+ * Errors: SPIIR_EINVAL, SPIIR_EUNSUPPORTED (SNR windows above 200 KB of shared memory). */
+int spiir_coherent_candidates(spiir_sky_t sky, int n_templates, const float *snr_dev,
+                              int64_t snr_pitch, int64_t snr_offset, const int32_t *cand_dev,
+                              const int32_t *n_cand_dev, int max_cand, int first_shift,
+                              int n_shifts, int shift_step, float *max_dev, int32_t *argmax_dev,
+                              float *null_dev, void *stream);
+
+/* ------------------------------------------------------------------------------------
  * Impulse response and its adjoint, for refining IIR coefficients against target
  * templates (the overlap of Sec. II.B.1 Eq. (overlap) is the usual objective).
  * Layout: T templates x F filters each (F <= 1024), row-major [T][F]; complex values are

@@ -13,8 +13,8 @@ import numpy as np
 from . import native
 from .native import SpiirError, check
 
-__all__ = ["Bank", "Sky", "Pipeline", "Batch", "sky_tables", "autocorr", "xi2", "xi2_network", "SpiirError",
-           "device_status", "version"]
+__all__ = ["Bank", "Sky", "Pipeline", "Batch", "sky_tables", "autocorr", "xi2", "xi2_network", "Selector",
+           "coherent_candidates", "SpiirError", "device_status", "version"]
 
 
 def _stream_ptr(stream=None):
@@ -366,3 +366,67 @@ def xi2_network(sky, xi, argmax, n: int, out=None, stream=None):
     check(native.lib().spiir_xi2_network(sky.handle, T, _dev_ptr(xi), xi.shape[-1], _dev_ptr(argmax), int(n),
                                          _dev_ptr(out), _stream_ptr(stream)))
     return out
+
+
+class Selector:
+    """Single-detector candidate selection (Sec. II.C.1) for spans of n samples of a bank of
+    n_templates templates: owns the zeroed slot workspace and the record buffers.
+
+    select() returns (cand, n_cand): cand [max_cand][4] int32 (detector, template, sample,
+    bits of the FP32 |z|^2), n_cand a one-element int32 tensor holding the number found (above
+    max_cand on overflow).  Both stay on the device; nothing is synchronised."""
+
+    def __init__(self, n_templates: int, n_det: int, n: int, per_second: int = 2048, max_cand: int = 65536,
+                 device="cuda"):
+        import torch
+        nb = ctypes.c_size_t()
+        check(native.lib().spiir_select_workspace_bytes(n_templates, n_det, int(n), per_second, ctypes.byref(nb)))
+        self.n_templates, self.n_det, self.n, self.per_second, self.max_cand = n_templates, n_det, int(n), per_second, max_cand
+        self.workspace = torch.zeros(nb.value // 8, dtype=torch.int64, device=device)
+        self.cand = torch.zeros((max(max_cand, 1), 4), dtype=torch.int32, device=device)
+        self.n_cand = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def select(self, snr, offset: int, threshold: float = 4.0, stream=None):
+        import torch
+        _require_cuda(snr, torch.complex64, "snr")
+        if snr.dim() != 3 or not snr.is_contiguous() or tuple(snr.shape[:2]) != (self.n_templates, self.n_det):
+            raise ValueError("snr must be a contiguous [n_templates][n_det][pitch] tensor")
+        check(native.lib().spiir_select_candidates(
+            self.n_templates, self.n_det, _dev_ptr(snr), snr.shape[-1], int(offset), self.n, float(threshold),
+            self.per_second, _dev_ptr(self.workspace), self.workspace.numel() * 8, _dev_ptr(self.cand),
+            self.max_cand, _dev_ptr(self.n_cand), _stream_ptr(stream)))
+        return self.cand, self.n_cand
+
+    @staticmethod
+    def records(cand, n_cand):
+        """Host copy of the records as a list of (detector, template, sample, |z|) (synchronises)."""
+        n = min(int(n_cand.item()), cand.shape[0])
+        c = cand[:n].cpu().numpy()
+        m2 = c[:, 3].copy().view(np.float32).astype(np.float64)
+        return [(int(a), int(b), int(k), float(np.sqrt(v))) for (a, b, k), v in zip(c[:, :3], m2)]
+
+
+def coherent_candidates(sky, snr, offset: int, cand, n_cand, first_shift: int = 0, n_shifts: int = 1,
+                        shift_step: int = 205, out=None, stream=None):
+    """Coherent statistic at the candidates (Sec. II.C.1) under time shifts
+    first_shift .. first_shift + n_shifts - 1 of shift_step samples per companion detector
+    (Sec. II.C.3).  snr [T][n_det][pitch] complex64 with entry offset + k = sample k; cand and
+    n_cand as returned by Selector.select.  Returns (max, argmax, null), each
+    [max_cand][n_shifts]; rows past the count are left as they were."""
+    import torch
+    _require_cuda(snr, torch.complex64, "snr")
+    _require_cuda(cand, torch.int32, "cand")
+    _require_cuda(n_cand, torch.int32, "n_cand")
+    if snr.dim() != 3 or not snr.is_contiguous() or not cand.is_contiguous():
+        raise ValueError("snr must be a contiguous [T][n_det][pitch] tensor and cand contiguous")
+    m = cand.shape[0]
+    if out is None:
+        out = (torch.full((m, n_shifts), float("nan"), dtype=torch.float32, device=snr.device),
+               torch.full((m, n_shifts), -1, dtype=torch.int32, device=snr.device),
+               torch.full((m, n_shifts), float("nan"), dtype=torch.float32, device=snr.device))
+    ms, am, nl = out
+    check(native.lib().spiir_coherent_candidates(
+        sky.handle, snr.shape[0], _dev_ptr(snr), snr.shape[-1], int(offset), _dev_ptr(cand), _dev_ptr(n_cand), m,
+        int(first_shift), int(n_shifts), int(shift_step), _dev_ptr(ms), _dev_ptr(am), _dev_ptr(nl),
+        _stream_ptr(stream)))
+    return ms, am, nl

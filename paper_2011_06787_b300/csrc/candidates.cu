@@ -1,0 +1,421 @@
+// Single-detector candidate selection (Sec. II.C.1) and the coherent statistic evaluated at
+// those candidates, at zero lag and under the time shifts of the background (Sec. II.C.3).
+//
+// Selection.  For every detector I and sample k the largest |z_I|^2 over the bank's templates
+// (the lowest template among equals) is compared with threshold^2; a sample over it is a
+// candidate of its template, and each (detector, template, second) keeps the largest one (the
+// earliest among equals).  All decisions are taken on |z|^2 = re*re + im*im in FP32 with each
+// operation rounded (no contraction), so that they are reproducible bit for bit.
+//   k_select:  one block per (32 samples, detector); warp w reads templates w, w + 8, ... with
+//              coalesced 8-byte loads (lane = sample), the 8 warps combine in shared memory and
+//              a sample over the threshold posts the key (|z|^2 bits, ~k) to its slot
+//              (detector, template, second) with a 64-bit atomicMax: the largest value wins,
+//              then the smallest sample.
+//   k_compact: one block walks the slots in (detector, template, second) order, writes a
+//              record per occupied slot with a block-wide prefix sum and clears the slot, so the
+//              workspace is zero again for the next call; the count stays on the device.
+//
+// Candidate-driven scan.  A candidate (detector r, template t, sample k) is evaluated at every
+// pixel p with detector r read at its own sample and each other detector J at
+// k + Delta_J(p) - Delta_r(p) + shift_J, shift_J = -s c_J step for time shift s (c_J = 1, 2, ...
+// the companions of r in detector order; s = 0 is the foreground).  One block per
+// (candidate, shift) item in a persistent grid: it stages each detector's window of the SNR
+// (the range of Delta_J - Delta_r over the sky) in shared memory, its threads loop over pixels
+// with the arithmetic of the all-sky scan, and a block reduction keeps the largest statistic
+// (the lowest pixel among equals) and the null stream at that pixel.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "coherent.cuh"
+
+namespace spiir {
+
+constexpr int kSelWarps = 8;
+constexpr int kSelThreads = 32 * kSelWarps;
+constexpr int kSelUnroll = 8;
+constexpr int kCompThreads = 1024;
+constexpr int kPtThreads = 256;
+constexpr int kPtMaxSmem = 200 * 1024;
+
+__device__ __forceinline__ float mag2_rn(float2 z) { return __fadd_rn(__fmul_rn(z.x, z.x), __fmul_rn(z.y, z.y)); }
+
+__global__ void __launch_bounds__(kSelThreads) k_select(const float2 *__restrict__ snr, int64_t pitch, int64_t off,
+                                                       int T, int n_det, int64_t n, float thr2, int per_second,
+                                                       int64_t n_sec, u64 *__restrict__ slots) {
+    __shared__ float s_best[kSelWarps][32];
+    __shared__ int s_t[kSelWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int I = blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+    float best = -1.f;
+    int bt = INT_MAX;
+    if (k < n) {
+        const float2 *p = snr + (int64_t)I * pitch + off + k;
+        const int64_t ts = (int64_t)n_det * pitch;  // template stride
+        int t = w;
+        for (; t + (kSelUnroll - 1) * kSelWarps < T; t += kSelUnroll * kSelWarps) {
+            float2 v[kSelUnroll];
+#pragma unroll
+            for (int j = 0; j < kSelUnroll; ++j) v[j] = p[(int64_t)(t + j * kSelWarps) * ts];
+#pragma unroll
+            for (int j = 0; j < kSelUnroll; ++j) {
+                const float m = mag2_rn(v[j]);
+                if (m > best) {
+                    best = m;
+                    bt = t + j * kSelWarps;
+                }
+            }
+        }
+        for (; t < T; t += kSelWarps) {
+            const float m = mag2_rn(p[(int64_t)t * ts]);
+            if (m > best) {
+                best = m;
+                bt = t;
+            }
+        }
+    }
+    s_best[w][lane] = best;
+    s_t[w][lane] = bt;
+    __syncthreads();
+    if (w != 0 || k >= n) return;
+#pragma unroll
+    for (int q = 1; q < kSelWarps; ++q) {
+        const float m = s_best[q][lane];
+        const int tq = s_t[q][lane];
+        if (m > best || (m == best && tq < bt)) {
+            best = m;
+            bt = tq;
+        }
+    }
+    if (best > thr2) {
+        const int64_t slot = ((int64_t)I * T + bt) * n_sec + k / per_second;
+        const u64 key = ((u64)__float_as_uint(best) << 32) | (u64)(0xFFFFFFFFu - (uint32_t)k);
+        atomicMax(slots + slot, key);
+    }
+}
+
+__global__ void __launch_bounds__(kCompThreads) k_compact(u64 *__restrict__ slots, int64_t n_slots, int T,
+                                                         int64_t n_sec, int4 *__restrict__ cand, int max_cand,
+                                                         int32_t *__restrict__ n_cand) {
+    __shared__ int s_warp[32];
+    __shared__ int s_total;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t base = 0;
+    for (int64_t c0 = 0; c0 < n_slots; c0 += kCompThreads) {
+        const int64_t i = c0 + threadIdx.x;
+        u64 key = 0;
+        if (i < n_slots) {
+            key = slots[i];
+            if (key) slots[i] = 0;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, key != 0);
+        __syncthreads();  // the previous chunk is done with s_warp and s_total
+        if (lane == 0) s_warp[w] = __popc(b);
+        __syncthreads();
+        if (w == 0) {
+            const int v = s_warp[lane];
+            int x = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= d) x += y;
+            }
+            s_warp[lane] = x - v;
+            if (lane == 31) s_total = x;
+        }
+        __syncthreads();
+        if (key) {
+            const int64_t pos = base + s_warp[w] + __popc(b & ((1u << lane) - 1u));
+            if (pos < max_cand) {
+                const int64_t it = i / n_sec;  // I * T + t
+                cand[pos] = make_int4((int)(it / T), (int)(it % T), (int)(0xFFFFFFFFu - (uint32_t)key),
+                                      (int)(key >> 32));
+            }
+        }
+        base += s_total;
+    }
+    if (threadIdx.x == 0) *n_cand = (int32_t)std::min<int64_t>(base, INT_MAX);
+}
+
+struct PointArgs {
+    const float2 *snr;  // [T][n_det][pitch], entry off + k is sample k
+    int64_t pitch, off;
+    int n_templates;
+    const int4 *cand;  // [max_cand] (detector, template, sample, |z|^2 bits)
+    const int32_t *n_cand;
+    int max_cand;
+    int first_shift, n_shifts;
+    int64_t step;
+    const void *table;  // TabEntry<ND>[n_pix]
+    const float *u_null;
+    int n_pix, H;
+    int dmin[4][4], dmax[4][4];  // range of Delta_J - Delta_r over the sky, [r][J]
+    int Wmax;                    // largest window, entries per detector in shared memory
+    size_t tab_bytes;            // table staged in shared memory (0: read from global)
+    float *max_stat;             // [max_cand][n_shifts]
+    int32_t *argmax;
+    float *null_stat;
+};
+
+struct Best {
+    float v;
+    int p;
+    float nul;
+};
+__device__ __forceinline__ void take(Best &a, float v, int p, float nul) {
+    if (v > a.v || (v == a.v && p < a.p)) {
+        a.v = v;
+        a.p = p;
+        a.nul = nul;
+    }
+}
+
+template <int ND, bool SMEM_TAB>
+__global__ void __launch_bounds__(kPtThreads) k_points(const __grid_constant__ PointArgs a) {
+    using Entry = TabEntry<ND>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Best s_red[kPtThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const Entry *tab = reinterpret_cast<const Entry *>(a.table);
+    if (SMEM_TAB) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.table);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        for (size_t i = tid; i < a.tab_bytes / 16; i += kPtThreads) dst[i] = src[i];
+        tab = reinterpret_cast<const Entry *>(smem);
+    }
+    float2 *win = reinterpret_cast<float2 *>(smem + a.tab_bytes);  // [ND][Wmax]
+    const int nc = min(*a.n_cand, a.max_cand);
+    const int64_t n_items = (int64_t)max(nc, 0) * a.n_shifts;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int c = (int)(item / a.n_shifts);
+        const int si = (int)(item % a.n_shifts);
+        const int4 cd = a.cand[c];
+        const int r = cd.x, t = cd.y;
+        const int64_t e = a.off + (int64_t)cd.z;
+        const int64_t s = (int64_t)a.first_shift + si;
+        const int64_t o = (int64_t)c * a.n_shifts + si;
+        // the first entry of each detector's window; the item is void if any read leaves the row
+        bool ok = r >= 0 && r < ND && t >= 0 && t < a.n_templates && cd.z >= 0;
+        int64_t lo[ND];
+        int len[ND];
+        if (ok) {
+            int comp = 0;
+#pragma unroll
+            for (int J = 0; J < ND; ++J) {
+                const int64_t sh = (J == r) ? 0 : -s * (++comp) * a.step;
+                lo[J] = e + sh + a.dmin[r][J];
+                len[J] = a.dmax[r][J] - a.dmin[r][J] + 1;
+                ok = ok && lo[J] >= 0 && lo[J] + len[J] <= a.pitch;
+            }
+        }
+        if (!ok) {
+            if (tid == 0) {
+                a.max_stat[o] = __int_as_float(0x7fc00000);
+                a.argmax[o] = -1;
+                a.null_stat[o] = __int_as_float(0x7fc00000);
+            }
+            continue;
+        }
+        __syncthreads();  // the previous item is done with the windows (and the table is staged)
+#pragma unroll
+        for (int J = 0; J < ND; ++J) {
+            const float2 *row = a.snr + ((int64_t)t * ND + J) * a.pitch + lo[J];
+            for (int j = tid; j < len[J]; j += kPtThreads) win[J * a.Wmax + j] = row[j];
+        }
+        __syncthreads();
+        int base[ND];  // window index of pixel p for detector J: off[J] - off[r] - dmin[r][J]
+#pragma unroll
+        for (int J = 0; J < ND; ++J) base[J] = J * a.Wmax - a.dmin[r][J];
+        Best b{-1.f, INT_MAX, 0.f};
+        for (int p = tid; p < a.n_pix; p += kPtThreads) {
+            const Entry en = tab[p];
+            int orr = 0;  // off[r], selected without indexing the entry at run time
+#pragma unroll
+            for (int J = 0; J < ND; ++J) orr = (J == r) ? en.off[J] : orr;
+            float y0r = 0.f, y0i = 0.f, y1r = 0.f, y1i = 0.f;
+#pragma unroll
+            for (int J = 0; J < ND; ++J) {
+                const float2 wv = win[base[J] + en.off[J] - orr];
+                y0r = fmaf(en.u[J][0], wv.x, y0r);
+                y0i = fmaf(en.u[J][0], wv.y, y0i);
+                y1r = fmaf(en.u[J][1], wv.x, y1r);
+                y1i = fmaf(en.u[J][1], wv.y, y1i);
+            }
+            const float v = fmaf(y1i, y1i, fmaf(y1r, y1r, fmaf(y0i, y0i, y0r * y0r)));
+            if (v > b.v) {
+                b.v = v;
+                b.p = p;
+            }
+        }
+        if (ND > 2 && b.p != INT_MAX) {
+            const Entry en = tab[b.p];
+            int orr = 0;
+#pragma unroll
+            for (int J = 0; J < ND; ++J) orr = (J == r) ? en.off[J] : orr;
+            const float *un = a.u_null + (int64_t)b.p * ND * (ND - 2);
+            float nul = 0.f;
+            for (int j = 0; j < ND - 2; ++j) {
+                float cr = 0.f, ci = 0.f;
+#pragma unroll
+                for (int J = 0; J < ND; ++J) {
+                    const float2 wv = win[base[J] + en.off[J] - orr];
+                    const float u = un[J * (ND - 2) + j];
+                    cr = fmaf(u, wv.x, cr);
+                    ci = fmaf(u, wv.y, ci);
+                }
+                nul = fmaf(cr, cr, fmaf(ci, ci, nul));
+            }
+            b.nul = nul;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const float v = __shfl_down_sync(0xffffffffu, b.v, d);
+            const int p = __shfl_down_sync(0xffffffffu, b.p, d);
+            const float nl = __shfl_down_sync(0xffffffffu, b.nul, d);
+            take(b, v, p, nl);
+        }
+        if (lane == 0) s_red[wid] = b;
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 1; q < kPtThreads / 32; ++q) take(b, s_red[q].v, s_red[q].p, s_red[q].nul);
+            const bool found = b.p != INT_MAX;
+            a.max_stat[o] = found ? b.v : __int_as_float(0x7fc00000);
+            a.argmax[o] = found ? b.p : -1;
+            a.null_stat[o] = found ? b.nul : __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+template <int ND, bool SMEM_TAB>
+static int launch_points(const PointArgs &a, size_t smem, cudaStream_t stream) {
+    auto kern = k_points<ND, SMEM_TAB>;
+    SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, n_sm = 0, per_sm = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPtThreads, smem));
+    const int64_t items = (int64_t)a.max_cand * a.n_shifts;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
+    kern<<<grid, kPtThreads, smem, stream>>>(a);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+template <int ND>
+static int dispatch_points(const PointArgs &a, size_t smem, cudaStream_t stream) {
+    return a.tab_bytes ? launch_points<ND, true>(a, smem, stream) : launch_points<ND, false>(a, smem, stream);
+}
+
+}  // namespace spiir
+
+using namespace spiir;
+
+static int64_t n_seconds(int64_t n, int per_second) { return (n + per_second - 1) / per_second; }
+
+extern "C" int spiir_select_workspace_bytes(int T, int n_det, int64_t n, int per_second, size_t *bytes) {
+    clear_error();
+    if (!bytes) return fail(SPIIR_EINVAL, "bytes is NULL");
+    if (T < 1 || n_det < 1 || n < 1 || per_second < 1)
+        return fail(SPIIR_EINVAL, "n_templates = %d, n_det = %d, n = %lld, per_second = %d", T, n_det, (long long)n,
+                    per_second);
+    *bytes = sizeof(u64) * (size_t)n_det * (size_t)T * (size_t)n_seconds(n, per_second);
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_select_candidates(int T, int n_det, const float *snr, int64_t pitch, int64_t off, int64_t n,
+                                       float threshold, int per_second, void *workspace, size_t workspace_bytes,
+                                       int32_t *cand, int max_cand, int32_t *n_cand, void *stream) {
+    clear_error();
+    if (T < 1 || n_det < 1 || n < 1 || per_second < 1)
+        return fail(SPIIR_EINVAL, "n_templates = %d, n_det = %d, n = %lld, per_second = %d", T, n_det, (long long)n,
+                    per_second);
+    if (n_det > 65535) return fail(SPIIR_EINVAL, "n_det = %d above 65535", n_det);
+    if (n > INT_MAX) return fail(SPIIR_EINVAL, "n = %lld above 2^31 - 1", (long long)n);
+    if (off < 0 || pitch < off + n)
+        return fail(SPIIR_EINVAL, "entries [%lld, %lld) outside the row pitch %lld", (long long)off,
+                    (long long)(off + n), (long long)pitch);
+    if (max_cand < 0) return fail(SPIIR_EINVAL, "max_cand = %d", max_cand);
+    if (!snr || !workspace || !n_cand || (max_cand > 0 && !cand)) return fail(SPIIR_EINVAL, "NULL pointer");
+    if (((uintptr_t)snr) % 8 || ((uintptr_t)workspace) % 8 || (cand && ((uintptr_t)cand) % 16))
+        return fail(SPIIR_EINVAL, "snr and workspace must be 8-byte aligned, cand 16-byte aligned");
+    if (!(threshold >= 0.f) || !std::isfinite(threshold)) return fail(SPIIR_EINVAL, "threshold must be finite and >= 0");
+    const int64_t n_sec = n_seconds(n, per_second);
+    const size_t need = sizeof(u64) * (size_t)n_det * (size_t)T * (size_t)n_sec;
+    if (workspace_bytes < need)
+        return fail(SPIIR_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, need);
+    const float thr2 = threshold * threshold;  // FP32, round to nearest (as the per-sample |z|^2)
+    cudaStream_t st = (cudaStream_t)stream;
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)n_det);
+    k_select<<<grid, kSelThreads, 0, st>>>(reinterpret_cast<const float2 *>(snr), pitch, off, T, n_det, n, thr2,
+                                           per_second, n_sec, static_cast<u64 *>(workspace));
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    k_compact<<<1, kCompThreads, 0, st>>>(static_cast<u64 *>(workspace), (int64_t)n_det * T * n_sec, T, n_sec,
+                                          reinterpret_cast<int4 *>(cand), max_cand, n_cand);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_coherent_candidates(spiir_sky_t sky, int T, const float *snr, int64_t pitch, int64_t off,
+                                         const int32_t *cand, const int32_t *n_cand, int max_cand, int first_shift,
+                                         int n_shifts, int shift_step, float *max_stat, int32_t *argmax,
+                                         float *null_stat, void *stream) {
+    clear_error();
+    if (!sky) return fail(SPIIR_EINVAL, "sky is NULL");
+    if (T < 1 || max_cand < 0 || n_shifts < 1 || first_shift < 0 || shift_step < 0 || off < 0 || pitch < 1)
+        return fail(SPIIR_EINVAL,
+                    "n_templates = %d, max_cand = %d, first_shift = %d, n_shifts = %d, shift_step = %d, "
+                    "offset = %lld, pitch = %lld",
+                    T, max_cand, first_shift, n_shifts, shift_step, (long long)off, (long long)pitch);
+    if ((int64_t)max_cand * n_shifts > INT_MAX) return fail(SPIIR_EINVAL, "max_cand x n_shifts above 2^31 - 1");
+    if (!snr || !n_cand || (max_cand > 0 && (!cand || !max_stat || !argmax || !null_stat)))
+        return fail(SPIIR_EINVAL, "NULL pointer");
+    if (((uintptr_t)snr) % 8 || (cand && ((uintptr_t)cand) % 16))
+        return fail(SPIIR_EINVAL, "snr must be 8-byte aligned, cand 16-byte aligned");
+    if (max_cand == 0) return SPIIR_OK;
+    const int ND = sky->n_det;
+    PointArgs a{};
+    a.snr = reinterpret_cast<const float2 *>(snr);
+    a.pitch = pitch;
+    a.off = off;
+    a.n_templates = T;
+    a.cand = reinterpret_cast<const int4 *>(cand);
+    a.n_cand = n_cand;
+    a.max_cand = max_cand;
+    a.first_shift = first_shift;
+    a.n_shifts = n_shifts;
+    a.step = shift_step;
+    a.table = sky->table;
+    a.u_null = sky->u_null;
+    a.n_pix = sky->n_pix;
+    a.H = sky->halo;
+    int Wmax = 1;
+    for (int r = 0; r < ND; ++r)
+        for (int J = 0; J < ND; ++J) {
+            int lo = INT_MAX, hi = INT_MIN;
+            for (int p = 0; p < sky->n_pix; ++p) {
+                const int d = sky->h_delays[(size_t)p * ND + J] - sky->h_delays[(size_t)p * ND + r];
+                lo = std::min(lo, d);
+                hi = std::max(hi, d);
+            }
+            a.dmin[r][J] = lo;
+            a.dmax[r][J] = hi;
+            Wmax = std::max(Wmax, hi - lo + 1);
+        }
+    a.Wmax = Wmax;
+    const size_t win_bytes = sizeof(float2) * (size_t)ND * Wmax;
+    a.tab_bytes = (sky->table_bytes + win_bytes <= (size_t)kPtMaxSmem) ? sky->table_bytes : 0;
+    a.max_stat = max_stat;
+    a.argmax = argmax;
+    a.null_stat = null_stat;
+    const size_t smem = a.tab_bytes + win_bytes;
+    if (smem > (size_t)kPtMaxSmem) return fail(SPIIR_EUNSUPPORTED, "SNR windows of %zu bytes", win_bytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (ND) {
+        case 2: return dispatch_points<2>(a, smem, st);
+        case 3: return dispatch_points<3>(a, smem, st);
+        case 4: return dispatch_points<4>(a, smem, st);
+        default: return fail(SPIIR_EUNSUPPORTED, "n_det = %d", ND);
+    }
+}

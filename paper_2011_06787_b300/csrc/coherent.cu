@@ -20,12 +20,6 @@
 
 namespace spiir {
 
-template <int ND>
-struct __align__(16) TabEntry {
-    float u[ND][2];
-    short off[ND];
-};
-
 template <int ND, bool SMEM_TAB, bool MAP>
 __global__ void __launch_bounds__(kCohThreads) k_coherent(const __grid_constant__ CohArgs a) {
     constexpr int Q = kCohQ;

@@ -61,6 +61,13 @@ int tmem_columns(int H);
 bool tmem_fits(int n_pix, int n_grp, int H);
 int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream);
 
+// Per-pixel entry of the general table: the two signal columns of U_s and H + Delta_I.
+template <int ND>
+struct __align__(16) TabEntry {
+    float u[ND][2];
+    short off[ND];
+};
+
 struct CohArgs {
     const float2 *snr;   // [T][n_det][pitch], entry H + k is output sample k
     int64_t pitch;
