@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,6 +38,8 @@ UNIT = "filter·sample updates/s"
 K1_FLOPS_PER_UPDATE = 12          # Sec. II.B.2
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
+# candidate-driven scan, 3 detectors: U_s^T w (3 detectors x 4 FMA) and |.|^2 (3 FMA + 1 MUL)
+K_POINT_FLOPS = 2 * 12 + 2 * 3 + 1
 
 
 def k2_flops_per_pixel_sample(n_det):
@@ -337,6 +340,10 @@ def run_gpu(args):
     if "xi2" in args.sections:
         xi2 = xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop)
 
+    cands = None
+    if "candidates" in args.sections:
+        cands = candidates_rate(args, torch, sp, det, sigma, timed_loop)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -367,6 +374,7 @@ def run_gpu(args):
             "adjoint": adjoint,
             "skymap": skymap,
             "xi2": xi2,
+            "candidates": cands,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
                                                    "h2d_bytes_per_step": n_det * n * 4,
@@ -472,6 +480,72 @@ def xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop):
                          "flops_per_launch": flops}}
 
 
+def candidates_rate(args, torch, sp, det, sigma, timed_loop):
+    """Candidates and the time-shift background (Sec. II.C.1, II.C.3) for one second of the
+    online workload: selection over 1024 templates x 3 detectors x 2048 samples (threshold 4),
+    the zero-lag coherent statistic of every candidate on the nside-16 sky and 100 time shifts
+    of 0.1 s (205 samples) on the nside-8 sky.  The SNR is normalised complex Gaussian noise
+    (E|z|^2 = 2, seeded on the device) holding 20.5 s of history for the shifts."""
+    T, n, step, n_sh = 1024, 2048, 205, 100
+    dev = torch.cuda.current_device()
+    sky16 = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 16, 2048.0))
+    sky8 = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 8, 2048.0))
+    H = max(sky16.halo, sky8.halo)
+    off = n_sh * 2 * step + 2 * H
+    pitch = off + n + 2 * H
+    g = torch.Generator(device="cuda").manual_seed(20110678)
+    z = torch.randn((T, 3, pitch), dtype=torch.complex64, device=dev, generator=g) * math.sqrt(2.0)
+    sel = sp.Selector(T, 3, n, 2048, 16384)
+    fg = bg = None
+
+    def select(i):
+        sel.select(z, off, 4.0)
+
+    def fore(i):
+        nonlocal fg
+        fg = sp.coherent_candidates(sky16, z, off, sel.cand, sel.n_cand, 0, 1, step, out=fg)
+
+    def back(i):
+        nonlocal bg
+        bg = sp.coherent_candidates(sky8, z, off, sel.cand, sel.n_cand, 1, n_sh, step, out=bg)
+
+    def whole(i):
+        select(i)
+        fore(i)
+        back(i)
+
+    whole(0)
+    torch.cuda.synchronize()
+    n_c = int(sel.n_cand.item())
+    steps = max(3, min(args.steps, 16))
+    t_sel = float(np.mean(timed_loop(select, steps)))
+    t_fg = float(np.mean(timed_loop(fore, steps)))
+    t_bg = float(np.mean(timed_loop(back, steps)))
+    t_all = float(np.mean(timed_loop(whole, steps)))
+    sp.device_status()
+    sel_bytes = T * 3 * n * 8
+    evals_fg, evals_bg = n_c * sky16.n_pix, n_c * n_sh * sky8.n_pix
+    flops_bg = evals_bg * K_POINT_FLOPS
+    peak_alu = 148 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    hbm = measured_peaks().get("hbm_gbs")
+    out = {"workload": f"{T} templates x 3 det x {n} samples, threshold 4; foreground nside 16 ({sky16.n_pix} px), "
+                       f"background {n_sh} shifts x {step} samples on nside 8 ({sky8.n_pix} px); "
+                       f"SNR complex Gaussian E|z|^2 = 2 with {pitch} samples per row",
+           "steps": steps, "candidates": n_c, "ms_per_second_of_data": t_all,
+           "kernel_ms": {"select (k_select + k_compact)": t_sel, "foreground k_points": t_fg,
+                         "background k_points": t_bg},
+           "pixel_evaluations_per_s": (evals_fg + evals_bg) / (t_all * 1e-3),
+           "select_gbs": sel_bytes / (t_sel * 1e-3) / 1e9,
+           "select_frac_of_measured_hbm": (sel_bytes / (t_sel * 1e-3) / 1e9 / hbm) if hbm else None,
+           "roofline": {"kernel": "k_points (background)", "bound": "alu",
+                        "achieved": flops_bg / (t_bg * 1e-3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+                        "frac": flops_bg / (t_bg * 1e-3) / 1e12 / peak_alu,
+                        "flops_per_launch": flops_bg, "flops_per_pixel": K_POINT_FLOPS}}
+    del z, sel, fg, bg
+    torch.cuda.empty_cache()
+    return out
+
+
 def skymap_rate(args, torch, sky, zbuf, n, ms, am, nl, timed_loop):
     """Coherent scan in sky-map mode: the statistic of every (template, pixel, sample) is
     written to HBM ([T][P][n] f32; 25.8 GB for the online workload), so the HBM roofline
@@ -573,8 +647,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
-    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2",
-                    help="comma list of measurements: main (always timed), batched, adjoint, skymap, xi2")
+    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2,candidates",
+                    help="comma list of measurements: main (always timed), batched, adjoint, skymap, xi2, candidates")
     ap.add_argument("--adjoint-templates", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--scan-shape", default="", help="fixed coherent-scan shape threads,pairs,table (no autotuning)")

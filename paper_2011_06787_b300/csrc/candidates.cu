@@ -38,6 +38,9 @@ constexpr int kSelUnroll = 8;
 constexpr int kCompThreads = 1024;
 constexpr int kPtThreads = 256;
 constexpr int kPtMaxSmem = 200 * 1024;
+constexpr int kPtChunkSmem = 110 * 1024;  // two blocks per SM
+
+__device__ __forceinline__ u64 lds64(const float *p) { return *reinterpret_cast<const u64 *>(p); }
 
 __device__ __forceinline__ float mag2_rn(float2 z) { return __fadd_rn(__fmul_rn(z.x, z.x), __fmul_rn(z.y, z.y)); }
 
@@ -288,14 +291,316 @@ __global__ void __launch_bounds__(kPtThreads) k_points(const __grid_constant__ P
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Chunked candidate scan: one block per (candidate, chunk of S consecutive shifts), for skies
+// whose windows (the range of Delta_J - Delta_r) fit in kPtWP entries and whose table fits in
+// shared memory with the windows of S shifts.
+//
+// The reference detector is never shifted, so its term U_s[p][r] w_r is the same for every
+// shift and is formed once per pixel; each shift adds the N_d - 1 companion terms.  The
+// windows are laid out [shift][companion][kPtWP], so that for one pixel the address of every
+// shift differs by a compile-time constant.  Each thread keeps a running maximum per shift;
+// a warp reduces its S (value, pixel) pairs in log2(32) butterfly steps that halve the pairs
+// a lane holds at each of the first log2(S) steps (S + log2(32 / S) shuffles per value instead
+// of 5 S), then the warps combine through shared memory.
+constexpr int kPtWP = 192;
+
+__device__ __forceinline__ void take_pair(float &kv, int &kp, float rv, int rp) {
+    if (rv > kv || (rv == kv && rp < kp)) {
+        kv = rv;
+        kp = rp;
+    }
+}
+
+// after the halving steps lane L holds the pair of shift (L >> (5 - log2 S)) reduced over the
+// lanes that share those bits; the remaining steps reduce over the low lane bits
+template <int S>
+__device__ __forceinline__ void warp_reduce_shifts(float (&v)[S], int (&p)[S], int lane) {
+    static_assert(S == 1 || S == 2 || S == 4 || S == 8 || S == 16 || S == 32, "S must be a power of two <= 32");
+#pragma unroll
+    for (int n = S, bit = 16; n > 1; n >>= 1, bit >>= 1) {
+        const bool up = (lane & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const float sv = up ? v[i] : v[i + n / 2];
+            const int sp = up ? p[i] : p[i + n / 2];
+            float kv = up ? v[i + n / 2] : v[i];
+            int kp = up ? p[i + n / 2] : p[i];
+            take_pair(kv, kp, __shfl_xor_sync(0xffffffffu, sv, bit), __shfl_xor_sync(0xffffffffu, sp, bit));
+            v[i] = kv;
+            p[i] = kp;
+        }
+    }
+    constexpr int kDone = (S == 1) ? 0 : (S == 2) ? 1 : (S == 4) ? 2 : (S == 8) ? 3 : (S == 16) ? 4 : 5;
+#pragma unroll
+    for (int bit = 16 >> kDone; bit > 0; bit >>= 1)
+        take_pair(v[0], p[0], __shfl_xor_sync(0xffffffffu, v[0], bit), __shfl_xor_sync(0xffffffffu, p[0], bit));
+}
+
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One (candidate, chunk) work item as every thread of the block sees it.
+template <int ND>
+struct PtItem {
+    int c, s_first, ns, r, t;
+    int64_t e;
+    uint32_t okmask;  // bit i: every read of shift column i stays inside the row
+    int Jq[ND - 1], dmn[ND - 1], dmx[ND - 1];
+};
+
+template <int ND, int S>
+__device__ __forceinline__ PtItem<ND> decode_item(const PointArgs &a, int64_t item, int n_chunks, int lane) {
+    constexpr int NC = ND - 1;
+    PtItem<ND> it;
+    it.c = (int)(item / n_chunks);
+    it.s_first = (int)(item % n_chunks) * S;
+    it.ns = min(S, a.n_shifts - it.s_first);
+    const int4 cd = a.cand[it.c];
+    it.r = cd.x;
+    it.t = cd.y;
+    it.e = a.off + (int64_t)cd.z;
+    const bool rec_ok = it.r >= 0 && it.r < ND && it.t >= 0 && it.t < a.n_templates && cd.z >= 0 && it.e < a.pitch;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        it.Jq[q] = (q < it.r) ? q : q + 1;
+        it.dmn[q] = rec_ok ? a.dmin[it.r][it.Jq[q]] : 0;
+        it.dmx[q] = rec_ok ? a.dmax[it.r][it.Jq[q]] : 0;
+    }
+    // lane i tests shift column i; companion q of shift s reads entries
+    // e - s (q + 1) step + [dmn[q], dmx[q]]
+    bool ok = rec_ok && lane < it.ns;
+    if (ok) {
+        const int64_t s = (int64_t)a.first_shift + it.s_first + lane;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const int64_t x = it.e - s * (q + 1) * a.step;
+            ok = ok && x + it.dmn[q] >= 0 && x + it.dmx[q] < a.pitch;
+        }
+    }
+    it.okmask = __ballot_sync(0xffffffffu, ok);
+    return it;
+}
+
+// Start the copies of an item's windows into buf ([S][NC][kPtWP]): one warp per
+// (shift column, companion) window, lanes striding it, 8-byte asynchronous copies.
+template <int ND, int S>
+__device__ __forceinline__ void stage_item(const PointArgs &a, const PtItem<ND> &it, float2 *buf, int wid, int lane) {
+    constexpr int NC = ND - 1;
+    constexpr int kWarps = kPtThreads / 32;
+    for (int wi = wid; wi < S * NC; wi += kWarps) {
+        const int i = wi / NC, q = wi % NC;
+        if (!((it.okmask >> i) & 1u)) continue;
+        int J = 0, dq = 0, len = 0;
+#pragma unroll
+        for (int qq = 0; qq < NC; ++qq) {
+            J = (qq == q) ? it.Jq[qq] : J;
+            dq = (qq == q) ? it.dmn[qq] : dq;
+            len = (qq == q) ? it.dmx[qq] - it.dmn[qq] + 1 : len;
+        }
+        const int64_t s = (int64_t)a.first_shift + it.s_first + i;
+        const float2 *row = a.snr + ((int64_t)it.t * ND + J) * a.pitch + it.e - s * (q + 1) * a.step + dq;
+        float2 *dst = buf + (i * NC + q) * kPtWP;
+        for (int j = lane; j < len; j += 32) cp_async8(dst + j, row + j);
+    }
+}
+
+template <int ND, int S>
+__global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_constant__ PointArgs a) {
+    using Entry = TabEntry<ND>;
+    constexpr int NC = ND - 1;                    // companions of the reference detector
+    constexpr int kShiftWords = NC * kPtWP;       // float2 entries per shift
+    constexpr int kWarps = kPtThreads / 32;
+    constexpr int kLog = (S == 1) ? 0 : (S == 2) ? 1 : (S == 4) ? 2 : (S == 8) ? 3 : (S == 16) ? 4 : 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_v[kWarps][S];
+    __shared__ int s_p[kWarps][S];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const Entry *__restrict__ tab = reinterpret_cast<const Entry *>(a.table);  // read through L1
+    float2 *wbuf = reinterpret_cast<float2 *>(smem);                             // [2][S][NC][kPtWP]
+    const int nc = min(*a.n_cand, a.max_cand);
+    const int n_chunks = (a.n_shifts + S - 1) / S;
+    const int64_t n_items = (int64_t)max(nc, 0) * n_chunks;
+    int64_t item = blockIdx.x;
+    if (item >= n_items) return;
+    PtItem<ND> cur = decode_item<ND, S>(a, item, n_chunks, lane);
+    stage_item<ND, S>(a, cur, wbuf, wid, lane);
+    cp_async_commit();
+    for (int k = 0; item < n_items; ++k, item += gridDim.x) {
+        float2 *win = wbuf + (k & 1) * S * kShiftWords;
+        // prefetch the next item into the other buffer (freed by the barrier that ended the
+        // previous iteration), then wait for this item's copies
+        const int64_t nxt = item + gridDim.x;
+        PtItem<ND> nit = cur;
+        if (nxt < n_items) {
+            nit = decode_item<ND, S>(a, nxt, n_chunks, lane);
+            stage_item<ND, S>(a, nit, wbuf + ((k + 1) & 1) * S * kShiftWords, wid, lane);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int r = cur.r;
+        // the reference sample (a nonzero mask implies a valid record)
+        const float2 wr = cur.okmask ? a.snr[((int64_t)cur.t * ND + r) * a.pitch + cur.e] : make_float2(0.f, 0.f);
+        const u64 wr2 = pack2(wr.x, wr.y);
+        float best[S];
+        int arg[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            best[i] = -1.f;
+            arg[i] = INT_MAX;
+        }
+        if (cur.okmask) {
+            for (int p = tid; p < a.n_pix; p += kPtThreads) {
+                // the entry's fields of detectors r and Jq[q] at run-time offsets (a select over
+                // a register copy of the entry would be turned back into a local-memory array)
+                const Entry *ep = tab + p;
+                const int offr = ep->off[r];
+                const float ur0 = ep->u[r][0], ur1 = ep->u[r][1];
+                const u64 yb0 = mul2(pack2(ur0, ur0), wr2), yb1 = mul2(pack2(ur1, ur1), wr2);
+                u64 U0[NC], U1[NC];
+                const float *wq[NC];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    const float u0 = ep->u[cur.Jq[q]][0], u1 = ep->u[cur.Jq[q]][1];
+                    U0[q] = pack2(u0, u0);
+                    U1[q] = pack2(u1, u1);
+                    wq[q] = reinterpret_cast<const float *>(win + q * kPtWP + (ep->off[cur.Jq[q]] - offr - cur.dmn[q]));
+                }
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    u64 y0 = yb0, y1 = yb1;
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        const u64 w = lds64(wq[q] + 2 * i * kShiftWords);
+                        y0 = fma2(U0[q], w, y0);
+                        y1 = fma2(U1[q], w, y1);
+                    }
+                    const float2 m = unpack2(fma2(y1, y1, mul2(y0, y0)));
+                    const float v = m.x + m.y;
+                    if (v > best[i]) {
+                        best[i] = v;
+                        arg[i] = p;
+                    }
+                }
+            }
+        }
+        warp_reduce_shifts<S>(best, arg, lane);
+        if ((lane & ((32 >> kLog) - 1)) == 0) {
+            s_v[wid][lane >> (5 - kLog)] = best[0];
+            s_p[wid][lane >> (5 - kLog)] = arg[0];
+        }
+        __syncthreads();
+        if (tid < cur.ns) {
+            const int i = tid;
+            float bv = s_v[0][i];
+            int bp = s_p[0][i];
+#pragma unroll
+            for (int w = 1; w < kWarps; ++w) take_pair(bv, bp, s_v[w][i], s_p[w][i]);
+            const int64_t o = (int64_t)cur.c * a.n_shifts + cur.s_first + i;
+            if (!((cur.okmask >> i) & 1u) || bp == INT_MAX) {
+                a.max_stat[o] = __int_as_float(0x7fc00000);
+                a.argmax[o] = -1;
+                a.null_stat[o] = __int_as_float(0x7fc00000);
+            } else {
+                float nul = 0.f;
+                if (ND > 2) {
+                    const Entry en = tab[bp];
+                    int offr = 0;
+#pragma unroll
+                    for (int J = 0; J < ND; ++J) offr = (J == r) ? en.off[J] : offr;
+                    const float *un = a.u_null + (int64_t)bp * ND * (ND - 2);
+                    for (int j = 0; j < ND - 2; ++j) {
+                        float cr = 0.f, ci = 0.f;
+#pragma unroll
+                        for (int J = 0; J < ND; ++J) {
+                            // companion slot of detector J and its window start (J != r)
+                            const int q = (J < r) ? J : J - 1;
+                            const int dm = (J < r) ? cur.dmn[J < NC ? J : 0] : cur.dmn[J > 0 ? J - 1 : 0];
+                            const float2 w = (J == r) ? wr : win[i * kShiftWords + q * kPtWP + en.off[J] - offr - dm];
+                            const float u = un[J * (ND - 2) + j];
+                            cr = fmaf(u, w.x, cr);
+                            ci = fmaf(u, w.y, ci);
+                        }
+                        nul = fmaf(cr, cr, fmaf(ci, ci, nul));
+                    }
+                }
+                a.max_stat[o] = bv;
+                a.argmax[o] = bp;
+                a.null_stat[o] = nul;
+            }
+        }
+        __syncthreads();  // this buffer and the partial maxima are free again
+        cur = nit;
+    }
+    cp_async_wait<0>();
+}
+
+// Resident blocks of a kernel for a dynamic shared-memory size (the opt-in limit is raised to
+// max_smem once per kernel and device; the last query is cached).
+struct LaunchCache {
+    int dev = -1, n_sm = 0;
+    size_t smem = 0;
+    int per_sm = 0;
+};
+template <typename K>
+static int resident_blocks(LaunchCache &c, K kern, int threads, size_t smem, int max_smem, int &n_sm, int &per_sm) {
+    int dev = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != c.dev) {
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev));
+        c.dev = dev;
+        c.smem = (size_t)-1;
+    }
+    if (smem != c.smem) {
+        SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, kern, threads, smem));
+        c.smem = smem;
+    }
+    n_sm = c.n_sm;
+    per_sm = c.per_sm;
+    return SPIIR_OK;
+}
+
+template <int ND, int S>
+static int launch_chunked(const PointArgs &a, size_t smem, cudaStream_t stream) {
+    auto kern = k_points_chunked<ND, S>;
+    static LaunchCache cache;
+    int n_sm = 0, per_sm = 0;
+    SPIIR_TRY(resident_blocks(cache, kern, kPtThreads, smem, kPtChunkSmem, n_sm, per_sm));
+    const int64_t items = (int64_t)a.max_cand * ((a.n_shifts + S - 1) / S);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
+    kern<<<grid, kPtThreads, smem, stream>>>(a);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+// shifts per chunk: 1 for the zero-lag scan, else as many as keep the double-buffered windows
+// within two blocks per SM
+static int chunk_shifts(int nd, int n_shifts) { return n_shifts == 1 ? 1 : (nd <= 3 ? 16 : 8); }
+
+template <int ND>
+static int dispatch_chunked(const PointArgs &a, cudaStream_t stream) {
+    const size_t win1 = sizeof(float2) * (ND - 1) * kPtWP;  // one shift's windows
+    switch (chunk_shifts(ND, a.n_shifts)) {
+        case 1: return launch_chunked<ND, 1>(a, 2 * win1, stream);
+        case 8: return launch_chunked<ND, 8>(a, 2 * 8 * win1, stream);
+        default: return launch_chunked<ND, 16>(a, 2 * 16 * win1, stream);
+    }
+}
+
 template <int ND, bool SMEM_TAB>
 static int launch_points(const PointArgs &a, size_t smem, cudaStream_t stream) {
     auto kern = k_points<ND, SMEM_TAB>;
-    SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, n_sm = 0, per_sm = 0;
-    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
-    SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPtThreads, smem));
+    static LaunchCache cache;
+    int n_sm = 0, per_sm = 0;
+    SPIIR_TRY(resident_blocks(cache, kern, kPtThreads, smem, kPtMaxSmem, n_sm, per_sm));
     const int64_t items = (int64_t)a.max_cand * a.n_shifts;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
     kern<<<grid, kPtThreads, smem, stream>>>(a);
@@ -390,28 +695,51 @@ extern "C" int spiir_coherent_candidates(spiir_sky_t sky, int T, const float *sn
     a.u_null = sky->u_null;
     a.n_pix = sky->n_pix;
     a.H = sky->halo;
+    if (sky->rel_min.empty()) {
+        std::vector<int> mn(ND * ND), mx(ND * ND);
+        for (int r = 0; r < ND; ++r)
+            for (int J = 0; J < ND; ++J) {
+                int lo = INT_MAX, hi = INT_MIN;
+                for (int p = 0; p < sky->n_pix; ++p) {
+                    const int d = sky->h_delays[(size_t)p * ND + J] - sky->h_delays[(size_t)p * ND + r];
+                    lo = std::min(lo, d);
+                    hi = std::max(hi, d);
+                }
+                mn[r * ND + J] = lo;
+                mx[r * ND + J] = hi;
+            }
+        sky->rel_min = mn;
+        sky->rel_max = mx;
+    }
     int Wmax = 1;
     for (int r = 0; r < ND; ++r)
         for (int J = 0; J < ND; ++J) {
-            int lo = INT_MAX, hi = INT_MIN;
-            for (int p = 0; p < sky->n_pix; ++p) {
-                const int d = sky->h_delays[(size_t)p * ND + J] - sky->h_delays[(size_t)p * ND + r];
-                lo = std::min(lo, d);
-                hi = std::max(hi, d);
-            }
-            a.dmin[r][J] = lo;
-            a.dmax[r][J] = hi;
-            Wmax = std::max(Wmax, hi - lo + 1);
+            a.dmin[r][J] = sky->rel_min[r * ND + J];
+            a.dmax[r][J] = sky->rel_max[r * ND + J];
+            Wmax = std::max(Wmax, a.dmax[r][J] - a.dmin[r][J] + 1);
         }
     a.Wmax = Wmax;
-    const size_t win_bytes = sizeof(float2) * (size_t)ND * Wmax;
-    a.tab_bytes = (sky->table_bytes + win_bytes <= (size_t)kPtMaxSmem) ? sky->table_bytes : 0;
     a.max_stat = max_stat;
     a.argmax = argmax;
     a.null_stat = null_stat;
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        const int S = chunk_shifts(ND, n_shifts);
+        const size_t chunk_bytes = 2 * sizeof(float2) * (size_t)S * (ND - 1) * kPtWP;  // double-buffered windows
+        if (Wmax <= kPtWP && chunk_bytes <= (size_t)kPtChunkSmem) {
+            a.tab_bytes = 0;
+            switch (ND) {
+                case 2: return dispatch_chunked<2>(a, st);
+                case 3: return dispatch_chunked<3>(a, st);
+                case 4: return dispatch_chunked<4>(a, st);
+                default: return fail(SPIIR_EUNSUPPORTED, "n_det = %d", ND);
+            }
+        }
+    }
+    const size_t win_bytes = sizeof(float2) * (size_t)ND * Wmax;
+    a.tab_bytes = (sky->table_bytes + win_bytes <= (size_t)kPtMaxSmem) ? sky->table_bytes : 0;
     const size_t smem = a.tab_bytes + win_bytes;
     if (smem > (size_t)kPtMaxSmem) return fail(SPIIR_EUNSUPPORTED, "SNR windows of %zu bytes", win_bytes);
-    cudaStream_t st = (cudaStream_t)stream;
     switch (ND) {
         case 2: return dispatch_points<2>(a, smem, st);
         case 3: return dispatch_points<3>(a, smem, st);

@@ -111,6 +111,7 @@ struct spiir_sky_s {
     // inputs kept to rebuild the grouped tables when the launch shape changes
     std::vector<int32_t> h_delays;
     int16_t *d_delays = nullptr;  // [P][n_det] on the device (signal-consistency gather)
+    std::vector<int> rel_min, rel_max;  // [r][J]: range of Delta_J - Delta_r over the sky (on first use)
     std::vector<float> h_usig, h_unull;
 };
 

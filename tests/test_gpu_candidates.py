@@ -20,12 +20,12 @@ def _cuda(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def _sky(cfg, n_det, nside, sig=(0.5, 2.0)):
+def _sky(cfg, n_det, nside, sig=(0.5, 2.0), rate=2048.0):
     import paper_2011_06787_b300 as sp
     det = synth.detectors(cfg, n_det)
     sigma = synth.noise_weights(cfg, n_det, *sig)
-    tabs = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, nside, 2048.0)
-    _, G, d_or = oracle.sky_geometry(det, sigma, nside, 2048.0)
+    tabs = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, nside, rate)
+    _, G, d_or = oracle.sky_geometry(det, sigma, nside, rate)
     np.testing.assert_array_equal(np.asarray(tabs[0]).reshape(d_or.shape), d_or)
     return sp.Sky(*tabs), G, d_or
 
@@ -149,13 +149,17 @@ def _companion_shifts(r, nd, s, step):
     return oracle.background_shifts(r, nd, s, step)
 
 
-@pytest.mark.parametrize("n_det,nside", [(2, 4), (3, 8), (4, 4)])
-def test_foreground_points_match_oracle(n_det, nside):
+@pytest.mark.parametrize("n_det,nside,rate", [
+    (2, 4, 2048.0), (3, 8, 2048.0), (4, 4, 2048.0),   # chunked kernel
+    (3, 4, 8192.0),                                    # windows wider than 192 samples: one block per item
+    (3, 32, 2048.0),                                   # table above shared memory: read through L1
+])
+def test_foreground_points_match_oracle(n_det, nside, rate):
     """Zero-lag statistic at the selected candidates of Gaussian SNR (every detector serves as
     the reference of some candidates)."""
     import torch
     import paper_2011_06787_b300 as sp
-    sky, G, d_or = _sky(4, n_det, nside)
+    sky, G, d_or = _sky(4, n_det, nside, rate=rate)
     H = sky.halo
     T, n, off = 24, 3000, 2 * H + 3
     z = synth.complex_gaussian_snr(4, (T, n_det, off + n + 2 * H + 1), sub=n_det)
@@ -176,13 +180,14 @@ def test_foreground_points_match_oracle(n_det, nside):
     assert bool(torch.all(torch.isnan(ms[m:])))
 
 
-def test_background_shifts_match_oracle_and_realign_a_shifted_source():
+@pytest.mark.parametrize("rate", [2048.0, 8192.0])
+def test_background_shifts_match_oracle_and_realign_a_shifted_source(rate):
     """A source whose companion data sit s* c step samples early is realigned by time shift s*
     (Sec. II.C.3); every (candidate, shift) matches the oracle, and a shift whose reads would
     leave the buffer gives (NaN, -1, NaN)."""
     import torch
     import paper_2011_06787_b300 as sp
-    sky, G, d_or = _sky(1, 3, 4, (1.0, 1.0))
+    sky, G, d_or = _sky(1, 3, 4, (1.0, 1.0), rate)
     H = sky.halo
     step, sstar, n_sh, r = 205, 3, 6, 1
     T, n = 4, 2048
@@ -219,6 +224,43 @@ def test_background_shifts_match_oracle_and_realign_a_shifted_source():
     c = [(a, b, kk) for a, b, kk, _ in recs].index((r, 2, k0))
     assert int(np.argmax(ms[c])) == sstar and am[c, sstar] == pstar
     assert np.isnan(ms[[(a, b, kk) for a, b, kk, _ in recs].index((0, 1, 10)), 5])
+
+
+@pytest.mark.parametrize("n_det,rate,n_sh", [(2, 2048.0, 20), (3, 2048.0, 20), (4, 2048.0, 20), (4, 4096.0, 4)])
+def test_background_points_match_oracle_on_gaussian_snr(n_det, rate, n_sh):
+    """Every (candidate, shift) of 20 shifts of 41 samples (chunks of 16 or 8 shifts with a
+    ragged last chunk; two, three and four detectors; windows wider than the chunked kernel's
+    at 4096 Hz for four detectors) against the oracle; shifts reaching before the buffer give
+    (NaN, -1, NaN)."""
+    import torch
+    import paper_2011_06787_b300 as sp
+    sky, G, d_or = _sky(7, n_det, 4, rate=rate)
+    H = sky.halo
+    step, T, n = 41, 6, 1500
+    off = 2 * H + (n_sh // 2) * (n_det - 1) * step  # later shifts leave the buffer for early candidates
+    z = synth.complex_gaussian_snr(7, (T, n_det, off + n + 2 * H), sub=10 + n_det)
+    sel, cand, cnt = _select(z, off, n, 3.3, 512)
+    recs = sp.Selector.records(cand, cnt)
+    assert len(recs) > 10
+    ms, am, nl = sp.coherent_candidates(sky, _cuda(z), off, cand, cnt, 1, n_sh, step)
+    torch.cuda.synchronize()
+    ms, am, nl = ms.cpu().numpy(), am.cpu().numpy(), nl.cpu().numpy()
+    dmin = {(a, b): int(np.min(d_or[:, b] - d_or[:, a])) for a in range(n_det) for b in range(n_det)}
+    pts, shifts, rows, n_out = [], [], [], 0
+    for c, (rr, t, k, _) in enumerate(recs):
+        for si in range(n_sh):
+            shv = _companion_shifts(rr, n_det, 1 + si, step)
+            if all(off + k + shv[J] + dmin[(rr, J)] >= 0 for J in range(n_det)):
+                pts.append([t, rr, off + k])
+                shifts.append(shv)
+                rows.append((c, si))
+            else:
+                assert np.isnan(ms[c, si]) and am[c, si] == -1 and np.isnan(nl[c, si]), (c, si)
+                n_out += 1
+    assert n_out > 0 and len(rows) > 100
+    mo, ao, no, at = _points_oracle(z, G, d_or, np.array(pts, np.int64), np.array(shifts, np.int64))
+    _assert_points_close(np.array([ms[c, s] for c, s in rows]), np.array([am[c, s] for c, s in rows]),
+                         np.array([nl[c, s] for c, s in rows]), mo, ao, no, at)
 
 
 def test_online_full_size_candidates_and_background():
