@@ -34,7 +34,7 @@ namespace spiir {
 
 constexpr int kSelWarps = 8;
 constexpr int kSelThreads = 32 * kSelWarps;
-constexpr int kSelUnroll = 8;
+constexpr int kSelUnroll = 16;
 constexpr int kCompThreads = 1024;
 constexpr int kPtThreads = 256;
 constexpr int kPtMaxSmem = 200 * 1024;
