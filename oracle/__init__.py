@@ -22,6 +22,12 @@ Contents, each a plain restatement of the paper in double precision:
 * ``fir_taps`` / ``decimate`` / ``upsample_linear`` / ``multirate_bank``
                          multirate split of the bank (not in the paper; definition in
                          the design notes, "parity unpinned" by the paper)
+* ``autocorr`` / ``xi2`` / ``xi2_network``  Sec. II.C.2: template autocorrelation, xi_I^2 per
+                         sample, network average at the coherent argmax
+* ``select_candidates`` / ``coherent_points`` / ``background_shifts``  Sec. II.C.1 and II.C.3:
+                         single-detector candidates, the coherent statistic at them, time shifts
+* ``lowpass_taps`` / ``whitening_kernel`` / ``fir`` / ``frontend``  Sec. II.A: 16384 -> 2048 Hz
+                         FIR down-sampling and whitening (Eq. (whiten)) as a time-domain FIR
 
 Functions with no pin beyond their own definition: the multirate split
 (``fir_taps``, ``decimate``, ``upsample_linear``, ``multirate_bank``) is parity
@@ -539,3 +545,80 @@ def background_shifts(ref: int, n_det: int, s: int, step: int):
             c += 1
             out[J] = -s * c * step
     return out
+
+
+# --------------------------------------------------------------------------------------------
+# Front end (Sec. II.A): FIR down-sampling 16384 -> 2048 Hz and whitening, Eq. (whiten), in the
+# time domain
+
+
+def lowpass_taps(ntaps: int, M: int, cutoff: float) -> np.ndarray:
+    """Causal Hann-windowed sinc low-pass for decimation by M: cutoff at cutoff x the output
+    Nyquist frequency (cycles per input sample fc = cutoff / (2 M)), unit DC gain.
+    h[i], i = 0..ntaps-1, centred at (ntaps - 1) / 2."""
+    fc = cutoff * 0.5 / M
+    c = (ntaps - 1) / 2.0
+    h = np.zeros(ntaps)
+    for i in range(ntaps):
+        a = 2.0 * fc * (i - c)
+        sinc = math.sin(math.pi * a) / (math.pi * a) if a != 0 else 1.0
+        h[i] = 2.0 * fc * sinc * (0.5 - 0.5 * math.cos(2.0 * math.pi * (i + 0.5) / ntaps))
+    return h / h.sum()
+
+
+def whitening_kernel(psd, rate_hz: float, ntaps: int, window: bool = True) -> np.ndarray:
+    """Time-domain whitening filter of Eq. (whiten): the zero-phase response
+    A(f) = sqrt(2 / (f_s S_n(f))) (unit-variance output for noise of one-sided PSD S_n), as a
+    causal linear-phase FIR of odd length L = 2K + 1 with delay K.
+
+    psd[j] is S_n at f_j = j f_s / N, j = 0 .. N/2 (N = 2 (len(psd) - 1)); L < N.  The
+    impulse response of A on the N-point grid is
+        a[m] = (1/N) [A_0 + (-1)^m A_{N/2} + 2 sum_{j=1}^{N/2-1} A_j cos(2 pi j m / N)],
+    and w[i] = win[i] a[i - K] with the Hann window win[i] = 1/2 - 1/2 cos(2 pi (i+1) / (L+1))
+    (win[K] = 1; window=False keeps a[i - K] unwindowed)."""
+    psd = np.asarray(psd, dtype=np.float64)
+    N = 2 * (psd.size - 1)
+    if ntaps % 2 != 1 or ntaps >= N:
+        raise ValueError("ntaps must be odd and below 2 (len(psd) - 1)")
+    A = np.sqrt(2.0 / (rate_hz * psd))
+    K = ntaps // 2
+    w = np.zeros(ntaps)
+    for i in range(ntaps):
+        m = i - K
+        acc = A[0] + (-1.0) ** (m % 2) * A[N // 2]
+        for j in range(1, N // 2):
+            acc += 2.0 * A[j] * math.cos(2.0 * math.pi * j * m / N)
+        win = 0.5 - 0.5 * math.cos(2.0 * math.pi * (i + 1) / (ntaps + 1)) if window else 1.0
+        w[i] = win * acc / N
+    return w
+
+
+def fir(x, h, history=None):
+    """Causal FIR y[k] = sum_j h[j] x[k - j] over one segment of each row of x (FP64).
+    history: the len(h) - 1 samples before the segment (zeros at stream start).
+    Returns (y, new_history)."""
+    x = np.asarray(x, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    L = h.size
+    hist = np.zeros(x.shape[:-1] + (L - 1,)) if history is None else np.asarray(history, dtype=np.float64)
+    xx = np.concatenate([hist, x], axis=-1)
+    n = x.shape[-1]
+    y = np.convolve(xx, h)[L - 1: L - 1 + n] if x.ndim == 1 else \
+        np.stack([np.convolve(r, h)[L - 1: L - 1 + n] for r in xx])
+    return y, xx[..., xx.shape[-1] - (L - 1):]
+
+
+def frontend(x16, dec_taps, M: int, white_taps, hist16=None, hist2=None):
+    """Front end of one segment (Sec. II.A): each detector's strain at the input rate is
+    low-passed and decimated by M (decimate: x_2[j] = sum_i h[i] x[j M - i]), then whitened by
+    its own causal FIR (fir with white_taps[I]).  Returns (y [n_det][n / M], hist16, hist2),
+    the histories to pass with the next segment."""
+    x16 = np.asarray(x16, dtype=np.float64)
+    x2, h16 = decimate(x16, M, dec_taps, hist16)
+    white_taps = np.asarray(white_taps, dtype=np.float64)
+    ys, hs = [], []
+    for I in range(x16.shape[0]):
+        y, h = fir(x2[I], white_taps[I], None if hist2 is None else hist2[I])
+        ys.append(y)
+        hs.append(h)
+    return np.stack(ys), h16, np.stack(hs)

@@ -645,3 +645,95 @@ def test_background_shift_pairs_the_reference_with_earlier_companion_data():
     tot = float(np.sum(np.abs(amp) ** 2))
     assert int(np.argmax(ms)) == sstar and am[sstar] == pstar and abs(ms[sstar] - tot) < 1e-6 * tot
     assert all(ms[s] < 0.9 * tot for s in range(6) if s != sstar)
+
+
+# ---------------------------------------------------------------------------------------------
+# Front end (Sec. II.A): FIR down-sampling and whitening, Eq. (whiten), in the time domain
+
+
+def test_whitening_kernel_of_a_flat_psd_is_a_scaled_delta():
+    """White noise of variance sigma^2 has the one-sided PSD 2 sigma^2 / f_s: its whitening
+    filter is 1 / sigma at the centre tap and zero elsewhere."""
+    fs, sigma, N = 2048.0, 1.7, 256
+    psd = np.full(N // 2 + 1, 2.0 * sigma ** 2 / fs)
+    w = oracle.whitening_kernel(psd, fs, 101)
+    expect = np.zeros(101)
+    expect[50] = 1.0 / sigma
+    np.testing.assert_allclose(w, expect, rtol=0, atol=1e-13)
+
+
+def test_whitening_kernel_is_eq_whiten_in_the_time_domain():
+    """Eq. (whiten) on a periodic signal: division by sqrt(S_n) in the frequency domain (numpy
+    FFT, with the unit-variance factor sqrt(2 / f_s)) equals circular convolution with the
+    unwindowed kernel (the PSD of an AR(1) process is smooth, so the kernel vanishes well before
+    half the period)."""
+    g = _rng(30)
+    fs, N, phi, s = 2048.0, 512, 0.6, 1.3
+    f = np.arange(N // 2 + 1) * fs / N
+    psd = (2.0 * s ** 2 / fs) / np.abs(1.0 - phi * np.exp(-2j * np.pi * f / fs)) ** 2
+    w = oracle.whitening_kernel(psd, fs, N - 1, window=False)
+    K = N // 2 - 1
+    x = g.standard_normal(N)
+    y_fd = np.fft.irfft(np.fft.rfft(x) * np.sqrt(2.0 / (fs * psd)), n=N)
+    y_td = np.array([sum(w[m + K] * x[(k - m) % N] for m in range(-K, K + 1)) for k in range(N)])
+    np.testing.assert_allclose(y_td, y_fd, rtol=0, atol=1e-10)
+
+
+def test_whitened_ar1_noise_is_white_with_unit_variance():
+    """x[k] = phi x[k-1] + s e[k] has S_n(f) = (2 s^2 / f_s) / |1 - phi e^{-2 pi i f / f_s}|^2;
+    the whitening FIR turns it into unit-variance noise with vanishing autocorrelation."""
+    g = _rng(31)
+    fs, phi, s, n = 2048.0, 0.9, 2.5, 1 << 16
+    e = g.standard_normal(n)
+    x = np.zeros(n)
+    for k in range(1, n):
+        x[k] = phi * x[k - 1] + s * e[k]
+    N = 4096
+    f = np.arange(N // 2 + 1) * fs / N
+    psd = (2.0 * s ** 2 / fs) / np.abs(1.0 - phi * np.exp(-2j * np.pi * f / fs)) ** 2
+    w = oracle.whitening_kernel(psd, fs, 1025)
+    y, _ = oracle.fir(x, w)
+    y = y[2048:]
+    assert abs(y.var() - 1.0) < 0.03, y.var()
+    for lag in range(1, 6):
+        r = float(np.mean(y[lag:] * y[:-lag]) / y.var())
+        assert abs(r) < 0.02, (lag, r)
+    # without whitening the lag-1 correlation is phi
+    assert abs(float(np.mean(x[2049:] * x[2048:-1]) / x[2048:].var()) - phi) < 0.02
+
+
+def test_decimation_low_pass_dc_passband_and_stopband():
+    """192-tap low-pass for 16384 -> 2048 Hz: a constant passes with gain 1 once the filter is
+    full, a 100 Hz tone keeps its amplitude, a 3 kHz tone (above the output Nyquist frequency)
+    is suppressed before it aliases."""
+    h = oracle.lowpass_taps(192, 8, 0.9)
+    fs, n = 16384.0, 16384
+    k = np.arange(n)
+    y, _ = oracle.decimate(np.ones((1, n)), 8, h)
+    assert np.max(np.abs(y[0, 24:] - 1.0)) < 1e-12
+    for f0, lo, hi in ((100.0, 0.995, 1.005), (3000.0, 0.0, 3e-3)):
+        y, _ = oracle.decimate(np.cos(2 * np.pi * f0 * k / fs)[None], 8, h)
+        amp = math.sqrt(2.0 * float(np.mean(y[0, 64:] ** 2)))
+        assert lo <= amp <= hi, (f0, amp)
+
+
+def test_frontend_streams_identically_across_chunks():
+    """Decimation and whitening with histories carried between segments of any length (a
+    multiple of the decimation factor) reproduce the whole-stream result."""
+    g = _rng(32)
+    x = g.standard_normal((2, 8 * 600))
+    h = oracle.lowpass_taps(48, 8, 0.9)
+    fs, N = 2048.0, 128
+    f = np.arange(N // 2 + 1) * fs / N
+    psds = [(2.0 / fs) / np.abs(1.0 - p * np.exp(-2j * np.pi * f / fs)) ** 2 for p in (0.3, -0.5)]
+    w = np.stack([oracle.whitening_kernel(p, fs, 41) for p in psds])
+    y_all, _, _ = oracle.frontend(x, h, 8, w)
+    parts, h16, h2, k0 = [], None, None, 0
+    for c in (100, 37, 263, 200):
+        y, h16, h2 = oracle.frontend(x[:, k0: k0 + 8 * c], h, 8, w, h16, h2)
+        parts.append(y)
+        k0 += 8 * c
+    np.testing.assert_allclose(np.concatenate(parts, axis=1), y_all, rtol=0, atol=1e-12)
+    # the decimated stream is x low-passed and subsampled: M = 8 with a one-tap filter is x[8 j]
+    y1, _ = oracle.decimate(x, 8, np.array([1.0]))
+    np.testing.assert_array_equal(y1, x[:, ::8])
