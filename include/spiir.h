@@ -42,6 +42,7 @@ typedef struct spiir_bank_s *spiir_bank_t;
 typedef struct spiir_sky_s *spiir_sky_t;
 typedef struct spiir_pipeline_s *spiir_pipeline_t;
 typedef struct spiir_batch_s *spiir_batch_t;
+typedef struct spiir_frontend_s *spiir_frontend_t;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int spiir_version(void);
@@ -254,6 +255,51 @@ int spiir_xi2(int n_templates, int n_det, const float *snr_dev, int64_t snr_pitc
  * gives NaN.  Device pointers, enqueued on stream.  Errors: SPIIR_EINVAL. */
 int spiir_xi2_network(spiir_sky_t sky, int n_templates, const float *xi2_dev, int64_t xi2_pitch,
                       const int32_t *argmax_dev, int64_t n, float *out_dev, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Front end (Sec. II.A): down-sampling and whitening of the strain before the filter bank.
+ * Each detector's strain at the input rate (16384 Hz in the paper) is low-passed and
+ * decimated by M with a time-domain FIR filter, x_2[j] = sum_{i < L_d} h[i] x[j M - i], then
+ * whitened by a causal FIR of its own, y_I[k] = sum_{i < L_w} w_I[i] x_2,I[k - i].  The paper
+ * whitens in the frequency domain, Eq. (whiten), dividing by sqrt(S_n(f)); with
+ * spiir_whitening_kernel the FIR has that response (scaled to unit-variance output) with linear
+ * phase, so the output lags by (L_w - 1) / 2 samples and needs no segment collection.  The
+ * decimation filter's own delay (L_d - 1) / 2 input samples is not compensated either.
+ * ---------------------------------------------------------------------------------- */
+
+/* Host helper: Hann-windowed sinc low-pass for decimation by M with cutoff
+ * cutoff x (output Nyquist frequency), 0 < cutoff <= 1, unit DC gain, designed in FP64:
+ * h[i] = 2 fc sinc(2 fc (i - (n-1)/2)) (1/2 - 1/2 cos(2 pi (i + 1/2) / n)) / sum, fc = cutoff / (2 M)
+ * cycles per input sample.  taps_host [n_taps], n_taps <= 8192, M <= 64.  Errors: SPIIR_EINVAL. */
+int spiir_fir_lowpass(int n_taps, int M, double cutoff, float *taps_host);
+
+/* Host helper: whitening FIR of Eq. (whiten) from a one-sided PSD.  psd_host[j] is S_n at
+ * f_j = j rate_hz / N, j = 0 .. n_freq - 1, N = 2 (n_freq - 1), each finite and > 0.  With
+ * A_j = sqrt(2 / (rate_hz S_n(f_j))), the zero-phase response on the N-point grid has the
+ * impulse response a[m] = (1/N) [A_0 + (-1)^m A_{N/2} + 2 sum_{0<j<N/2} A_j cos(2 pi j m / N)];
+ * taps_host[i] = win[i] a[i - K] for i < n_taps = 2K + 1 (odd, below N, at most 16385), with
+ * the Hann window win[i] = 1/2 - 1/2 cos(2 pi (i + 1) / (n_taps + 1)).  Noise of PSD S_n comes
+ * out with unit variance.  FP64 design, FP32 taps.  Errors: SPIIR_EINVAL. */
+int spiir_whitening_kernel(int n_freq, const double *psd_host, double rate_hz, int n_taps,
+                           float *taps_host);
+
+/* Streaming front end for n_det detectors: the decimation taps (shared by all detectors) and
+ * one whitening kernel per detector (white_taps_host [n_det][n_white_taps]) are copied to the
+ * device; the FIR histories are owned by the object and start at zero.  max_in: the largest
+ * input segment (a multiple of M).  n_dec_taps <= 8192, n_white_taps <= 16385, M <= 64.
+ * Errors: SPIIR_EINVAL, SPIIR_ENOMEM, SPIIR_ECUDA. */
+int spiir_frontend_create(int n_det, int M, int n_dec_taps, const float *dec_taps_host,
+                          int n_white_taps, const float *white_taps_host, int64_t max_in,
+                          spiir_frontend_t *out);
+void spiir_frontend_destroy(spiir_frontend_t fe);
+/* Zero the histories (a new stream).  Enqueued on stream. */
+int spiir_frontend_reset(spiir_frontend_t fe, void *stream);
+/* One segment: strain_dev [n_det][strain_pitch] f32 at the input rate, n_in samples (a positive
+ * multiple of M, at most max_in); out_dev [n_det][out_pitch] f32 receives the n_in / M
+ * whitened samples at the output rate.  Continues the stream of the previous call.  Two
+ * launches on stream.  Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
+int spiir_frontend_run(spiir_frontend_t fe, const float *strain_dev, int64_t strain_pitch,
+                       int64_t n_in, float *out_dev, int64_t out_pitch, void *stream);
 
 /* ------------------------------------------------------------------------------------
  * Candidates and the time-shift background (Sec. II.C.1, II.C.3).

@@ -14,7 +14,7 @@ from . import native
 from .native import SpiirError, check
 
 __all__ = ["Bank", "Sky", "Pipeline", "Batch", "sky_tables", "autocorr", "xi2", "xi2_network", "Selector",
-           "coherent_candidates", "SpiirError", "device_status", "version"]
+           "coherent_candidates", "Frontend", "fir_lowpass", "whitening_kernel", "SpiirError", "device_status", "version"]
 
 
 def _stream_ptr(stream=None):
@@ -430,3 +430,69 @@ def coherent_candidates(sky, snr, offset: int, cand, n_cand, first_shift: int = 
         int(first_shift), int(n_shifts), int(shift_step), _dev_ptr(ms), _dev_ptr(am), _dev_ptr(nl),
         _stream_ptr(stream)))
     return ms, am, nl
+
+
+def fir_lowpass(n_taps: int, M: int, cutoff: float) -> np.ndarray:
+    """Hann-windowed sinc low-pass for decimation by M (cutoff x the output Nyquist frequency,
+    unit DC gain), designed in FP64 by the library; float32 [n_taps]."""
+    h = np.empty(n_taps, dtype=np.float32)
+    check(native.lib().spiir_fir_lowpass(int(n_taps), int(M), float(cutoff), _host_ptr(h)))
+    return h
+
+
+def whitening_kernel(psd, rate_hz: float, n_taps: int) -> np.ndarray:
+    """Whitening FIR of Eq. (whiten) from the one-sided PSD psd[j] at f_j = j rate / N,
+    N = 2 (len(psd) - 1): linear phase, odd length, unit-variance output; float32 [n_taps]."""
+    psd = np.ascontiguousarray(psd, dtype=np.float64)
+    w = np.empty(n_taps, dtype=np.float32)
+    check(native.lib().spiir_whitening_kernel(psd.size, _host_ptr(psd), float(rate_hz), int(n_taps), _host_ptr(w)))
+    return w
+
+
+class Frontend:
+    """Streaming down-sampling and whitening of n_det strain channels (Sec. II.A): decimation by
+    M with the FIR dec_taps, then each detector's whitening FIR white_taps[I]."""
+
+    def __init__(self, n_det: int, dec_taps, M: int, white_taps, max_in: int):
+        dec_taps = np.ascontiguousarray(dec_taps, dtype=np.float32)
+        white_taps = np.ascontiguousarray(white_taps, dtype=np.float32).reshape(n_det, -1)
+        self.n_det, self.M = n_det, M
+        h = ctypes.c_void_p()
+        check(native.lib().spiir_frontend_create(n_det, M, dec_taps.size, _host_ptr(dec_taps), white_taps.shape[1],
+                                                 _host_ptr(white_taps), int(max_in), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            native.lib().spiir_frontend_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        check(native.lib().spiir_frontend_reset(self._h, _stream_ptr(stream)))
+
+    def run(self, strain, out=None, stream=None):
+        """strain [n_det][n_in] float32 CUDA tensor (n_in a multiple of M); returns (or fills)
+        out [n_det][n_in / M]."""
+        import torch
+        _require_cuda(strain, torch.float32, "strain")
+        if strain.dim() != 2 or strain.shape[0] != self.n_det or strain.stride(1) != 1:
+            raise ValueError("strain must be [n_det][n] with unit stride along samples")
+        n_in = strain.shape[1]
+        if out is None:
+            out = torch.empty((self.n_det, n_in // self.M), dtype=torch.float32, device=strain.device)
+        _require_cuda(out, torch.float32, "out")
+        if out.stride(1) != 1:
+            raise ValueError("out must have unit stride along samples")
+        check(native.lib().spiir_frontend_run(self._h, _dev_ptr(strain), strain.stride(0), n_in, _dev_ptr(out),
+                                              out.stride(0), _stream_ptr(stream)))
+        return out
