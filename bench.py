@@ -340,6 +340,10 @@ def run_gpu(args):
     if "xi2" in args.sections:
         xi2 = xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop)
 
+    front = None
+    if "frontend" in args.sections:
+        front = frontend_rate(args, torch, sp, timed_loop)
+
     cands = None
     if "candidates" in args.sections:
         cands = candidates_rate(args, torch, sp, det, sigma, timed_loop)
@@ -375,6 +379,7 @@ def run_gpu(args):
             "skymap": skymap,
             "xi2": xi2,
             "candidates": cands,
+            "frontend": front,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
                                                    "h2d_bytes_per_step": n_det * n * 4,
@@ -478,6 +483,36 @@ def xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop):
             "roofline": {"kernel": "k_xi2", "bound": "alu", "achieved": flops / (xi_ms * 1e-3) / 1e12,
                          "peak": peak, "unit": "TFLOP/s", "frac": flops / (xi_ms * 1e-3) / 1e12 / peak,
                          "flops_per_launch": flops}}
+
+
+def frontend_rate(args, torch, sp, timed_loop):
+    """Front end (Sec. II.A) for the online workload's 3 detectors: 1 s segments of 16384 Hz
+    strain (unit white noise, seeded) down-sampled by 8 with a 192-tap low-pass and whitened by a
+    2 s (4097-tap) kernel per detector, built from AR(1)-shaped PSDs."""
+    n_det, M, Ld, Lw, fs16 = 3, 8, 192, 4097, 16384
+    h = sp.fir_lowpass(Ld, M, 0.9)
+    N = 8192
+    f = np.arange(N // 2 + 1) * 2048.0 / N
+    w = np.stack([sp.whitening_kernel((2.0 / 2048.0) / np.abs(1.0 - p * np.exp(-2j * np.pi * f / 2048.0)) ** 2,
+                                      2048.0, Lw) for p in (0.9, 0.5, -0.3)])
+    fe = sp.Frontend(n_det, h, M, w, fs16)
+    dev = torch.cuda.current_device()
+    x = [torch.from_numpy(synth.white_noise(1, n_det, fs16, sub=100 + i)).to(dev) for i in range(4)]
+    out = torch.empty((n_det, fs16 // M), dtype=torch.float32, device=dev)
+    for i in range(3):
+        fe.run(x[i % 4], out)
+    steps = max(3, min(args.steps, 16))
+    t = float(np.mean(timed_loop(lambda i: fe.run(x[i % 4], out), steps)))
+    sp.device_status()
+    flops = n_det * (fs16 // M) * 2 * (Ld + Lw)  # one FMA per tap and output sample
+    peak = 148 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return {"workload": f"{n_det} det x {fs16} samples at 16384 Hz per segment -> {fs16 // M} at 2048 Hz; "
+                        f"low-pass {Ld} taps, whitening {Lw} taps",
+            "steps": steps, "ms_per_second_of_data": t, "launches_per_segment": 2,
+            "output_samples_per_s": n_det * (fs16 // M) / (t * 1e-3),
+            "roofline": {"kernel": "k_fe_decimate + k_fe_whiten", "bound": "alu",
+                         "achieved": flops / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (t * 1e-3) / 1e12 / peak, "flops_per_segment": flops}}
 
 
 def candidates_rate(args, torch, sp, det, sigma, timed_loop):
@@ -647,8 +682,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
-    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2,candidates",
-                    help="comma list of measurements: main (always timed), batched, adjoint, skymap, xi2, candidates")
+    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2,candidates,frontend",
+                    help="comma list of measurements: main (always timed), batched, adjoint, skymap, xi2, candidates, "
+                         "frontend")
     ap.add_argument("--adjoint-templates", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--scan-shape", default="", help="fixed coherent-scan shape threads,pairs,table (no autotuning)")
