@@ -202,6 +202,10 @@ int spiir_sky_info(spiir_sky_t sky, int *n_det, int *n_pix, int *halo);
  * windows of its 8 consecutive samples in tensor memory (one block per SM, 512 columns).
  * It pairs the FP32 arithmetic differently from the shared-memory scan, so the two agree to
  * rounding; with a sky map each thread writes its 8 samples of a pixel as one 32-byte segment.
+ * For this shape the third value selects where the pixel groups and per-pixel delay offsets
+ * are read: 1 (default) from the kernel's parameter space when the sky has at most 4096
+ * pixels and 512 groups (warp-uniform reads, so the tensor-memory addresses stay in uniform
+ * registers), else from shared memory; 0 always from shared memory.
  * Errors: SPIIR_EUNSUPPORTED when the tensor-memory scan does not apply (the previous shape is
  * kept), SPIIR_EINVAL for other shapes. */
 int spiir_sky_set_scan_shape(spiir_sky_t sky, int threads, int pairs, int table_in_shared);

@@ -459,7 +459,7 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         m.null_stat = null_stat;
         m.skymap = skymap;
         m.map_vec = (n % 4 == 0 && ((uintptr_t)skymap % 16) == 0) ? 1 : 0;
-        return launch_coherent_tmem(m, stream);
+        return launch_coherent_tmem(m, sky->scan_tmem_param ? sky->t_tab : nullptr, stream);
     }
     if (sky->grouped) {
         GroupedArgs g{};
@@ -548,6 +548,7 @@ static void sky_free(spiir_sky_s *s) {
     dev_free(s->g_grp);
     dev_free(s->t_ent);
     dev_free(s->d_delays);
+    delete s->t_tab;
     delete s;
 }
 
@@ -647,6 +648,12 @@ static int build_grouped(spiir_sky_s *s, const int32_t *delays, const float *u_s
         }
         s->t_slice[4] = s->n_grp;
         s->tmem_ok = true;
+        if (P <= kTmTabPix && s->n_grp <= kTmTabGrp) {
+            s->t_tab = new (std::nothrow) TmemTab();
+            if (!s->t_tab) return fail(SPIIR_ENOMEM, "host copy of the tensor-memory tables");
+            for (int q = 0; q < P; ++q) memcpy(&s->t_tab->d12[q], &te[q].w, 4);
+            for (int g = 0; g < s->n_grp; ++g) s->t_tab->grp[g] = grp[g];
+        }
     }
     s->g_W = W;
     s->grouped = true;
@@ -744,7 +751,10 @@ extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs, i
         if (!s->tmem_ok)
             return fail(SPIIR_EUNSUPPORTED, "tensor-memory scan needs 3 detectors, an orthonormal basis, "
                                             "|Delta| <= 60 and a table that fits in shared memory");
+        if (table_in_shared != 0 && table_in_shared != 1)
+            return fail(SPIIR_EINVAL, "the third value of the tensor-memory shape must be 0 or 1");
         s->scan_tmem = 1;
+        s->scan_tmem_param = table_in_shared;
         return SPIIR_OK;
     }
     if ((threads != 256 && threads != 512) || (pairs != 1 && pairs != 2) || (table_in_shared != 0 && table_in_shared != 1))
@@ -762,6 +772,8 @@ extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs, i
     dev_free(s->g_orig);
     dev_free(s->g_grp);
     dev_free(s->t_ent);
+    delete s->t_tab;
+    s->t_tab = nullptr;
     s->g_ent = nullptr;
     s->g_orig = nullptr;
     s->g_grp = nullptr;
@@ -783,7 +795,7 @@ extern "C" int spiir_sky_get_scan_shape(spiir_sky_t s, int *threads, int *pairs,
     if (!s) return fail(SPIIR_EINVAL, "sky is NULL");
     if (threads) *threads = s->scan_tmem ? 512 : s->scan_threads;
     if (pairs) *pairs = s->scan_tmem ? 4 : s->scan_pairs;
-    if (table_in_shared) *table_in_shared = s->scan_table_shared;
+    if (table_in_shared) *table_in_shared = s->scan_tmem ? s->scan_tmem_param : s->scan_table_shared;
     if (grouped) *grouped = s->grouped ? 1 : 0;
     return SPIIR_OK;
 }

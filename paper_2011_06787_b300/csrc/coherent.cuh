@@ -57,9 +57,19 @@ struct TmemArgs {
     int map_vec;            // 1: n % 4 == 0 and skymap 16-byte aligned (vector stores)
 };
 
+// Per-pixel delay offsets (delta_1 | delta_2 << 16) and the pixel groups of the tensor-memory
+// scan, passed as a kernel parameter when the sky is small enough: read with warp-uniform
+// indices from the parameter bank, they yield tensor-memory addresses in uniform registers.
+constexpr int kTmTabPix = 4096;
+constexpr int kTmTabGrp = 512;
+struct TmemTab {
+    uint32_t d12[kTmTabPix];
+    int4 grp[kTmTabGrp];
+};
+
 int tmem_columns(int H);
 bool tmem_fits(int n_pix, int n_grp, int H);
-int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream);
+int launch_coherent_tmem(const TmemArgs &a, const TmemTab *tab, cudaStream_t stream);
 
 // Per-pixel entry of the general table: the two signal columns of U_s and H + Delta_I.
 template <int ND>
@@ -104,9 +114,11 @@ struct spiir_sky_s {
     int scan_threads = 256, scan_pairs = 2;
     int scan_table_shared = 1;  // 1: stage the table in shared memory when it fits; 0: read it through L1
     int scan_tmem = 0;          // 1: tensor-memory scan (3 detectors, no sky map)
+    int scan_tmem_param = 1;    // tensor-memory scan: 1 = group and offset tables as kernel parameters when they fit
     // tensor-memory scan tables (same pixel order and groups as the grouped scan)
     bool tmem_ok = false;
     float4 *t_ent = nullptr;
+    spiir::TmemTab *t_tab = nullptr;  // host copy of the parameter tables (NULL when the sky is too large)
     int t_slice[5] = {0, 0, 0, 0, 0};
     // inputs kept to rebuild the grouped tables when the launch shape changes
     std::vector<int32_t> h_delays;

@@ -28,6 +28,14 @@
 // kernel.  In sky-map mode every row also writes its 8 statistics of each pixel to
 // map[t][p][k] (two 16-byte streaming stores), which overlaps the map's HBM writes with the
 // arithmetic.
+//
+// Addresses in uniform registers.  A tcgen05.ld takes its tensor-memory address from a uniform
+// register.  When the pixel's offsets come from shared memory the compiler cannot prove them
+// warp-uniform and moves each address into a uniform register separately (one R2UR per load,
+// 16 per pixel).  For skies of at most 4096 pixels and 512 groups the group table and the
+// packed offsets are therefore passed as a __grid_constant__ kernel parameter (24 KB): read
+// with indices derived from the warp index, they land in uniform registers directly, which
+// removes those moves (116.5 -> 101.8 instructions per warp-pixel on the online workload).
 #include <algorithm>
 
 #include "coherent.cuh"
@@ -85,10 +93,16 @@ __device__ __forceinline__ u64 sub2(u64 a, u64 b) {
 // of a warp reading sample 8 r + c hit 32 consecutive words
 __device__ __forceinline__ int tpos(int x, int L) { return (x & 7) * L + (x >> 3); }
 
-template <bool MAP>
-__global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_constant__ TmemArgs a) {
+// PT: the group table and the per-pixel offsets come from the kernel parameter pt (read with
+// warp-uniform indices, so the tensor-memory addresses stay in uniform registers); otherwise
+// from shared memory.
+template <bool MAP, bool PT>
+__device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
+    // with PT the broadcast tells the compiler that the warp index (and so every table index
+    // derived from it) is warp-uniform
+    const int warp = PT ? __shfl_sync(0xffffffffu, tid >> 5, 0) : tid >> 5;
     const int q = warp & 3, sl = warp >> 2;
     const int row = 32 * q + lane;
     const int P = a.n_pix, G = a.n_grp, H = a.H, C = a.C;
@@ -124,7 +138,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_co
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
-    const uint32_t tbase = *slot;
+    const uint32_t tbase = PT ? __shfl_sync(0xffffffffu, *slot, 0) : *slot;
     const uint32_t la = tbase + ((uint32_t)(32 * q) << 16);  // this warp's lane quarter
     const int g_lo = a.slice[sl], g_hi = a.slice[sl + 1];
 
@@ -182,7 +196,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_co
         }
         const float *z0r = zp, *z0i = zp + PL;
         for (int g = g_lo; g < g_hi; ++g) {
-            const int4 gr = grp[g];
+            const int4 gr = PT ? pt->grp[g] : grp[g];
             const int d0 = H + gr.w;
             u64 w0[kTmM], s0[kTmM];
             float gm[kTmM];
@@ -195,7 +209,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_co
             }
             for (int p = gr.y; p < gr.z; ++p) {
                 const float4 e = ent[p];
-                const uint32_t o = __float_as_uint(e.w);
+                const uint32_t o = PT ? pt->d12[p] : __float_as_uint(e.w);
                 u64 w1[kTmM], w2[kTmM];
                 tm_window(w1, la + 2 * (o & 0xFFFFu));
                 tm_window(w2, la + kTmDet + 2 * (o >> 16));
@@ -314,6 +328,17 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_co
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512u) : "memory");
 }
 
+template <bool MAP>
+__global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_constant__ TmemArgs a) {
+    tmem_scan<MAP, false>(a, nullptr);
+}
+
+template <bool MAP>
+__global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem_pt(const __grid_constant__ TmemArgs a,
+                                                                   const __grid_constant__ TmemTab pt) {
+    tmem_scan<MAP, true>(a, &pt);
+}
+
 size_t tmem_scan_smem(int n_pix, int n_grp, int C) {
     const int W0 = kTmKT + C, L = W0 / 8 + 1;
     size_t s = (size_t)n_pix * sizeof(float4) + (size_t)n_grp * sizeof(int4) + (size_t)8 * kTmKT * sizeof(float) +
@@ -327,12 +352,14 @@ bool tmem_fits(int n_pix, int n_grp, int H) {
     return 2 * tmem_columns(H) <= kTmDet && tmem_scan_smem(n_pix, n_grp, tmem_columns(H)) <= 227 * 1024;
 }
 
-int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream) {
+int launch_coherent_tmem(const TmemArgs &a, const TmemTab *tab, cudaStream_t stream) {
     const size_t smem = tmem_scan_smem(a.n_pix, a.n_grp, a.C);
     static bool attr = false;
     if (!attr) {
         SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
     int dev = 0, n_sm = 0;
@@ -340,10 +367,16 @@ int launch_coherent_tmem(const TmemArgs &a, cudaStream_t stream) {
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int64_t items = (int64_t)a.n_templates * ((a.n + kTmKT - 1) / kTmKT);
     const int grid = (int)std::min<int64_t>(items, n_sm);
-    if (a.skymap)
+    if (tab && a.n_pix <= kTmTabPix && a.n_grp <= kTmTabGrp) {
+        if (a.skymap)
+            k_coherent_tmem_pt<true><<<grid, kTmThreads, smem, stream>>>(a, *tab);
+        else
+            k_coherent_tmem_pt<false><<<grid, kTmThreads, smem, stream>>>(a, *tab);
+    } else if (a.skymap) {
         k_coherent_tmem<true><<<grid, kTmThreads, smem, stream>>>(a);
-    else
+    } else {
         k_coherent_tmem<false><<<grid, kTmThreads, smem, stream>>>(a);
+    }
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }

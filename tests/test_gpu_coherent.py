@@ -182,19 +182,23 @@ def test_all_zero_window_ties_resolve_to_pixel_zero():
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
 
 
-@pytest.mark.parametrize("nside,T,n", [(8, 3, 2500), (16, 2, 1024), (16, 2, 3000)])
-def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(nside, T, n):
+@pytest.mark.parametrize("nside,T,n,param", [(8, 3, 2500, 1), (16, 2, 1024, 1), (16, 2, 3000, 1), (16, 2, 3000, 0)])
+def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(nside, T, n, param):
     """The TMEM scan (512 threads, 8 samples per row, detector 1 and 2 windows in tensor
     memory) against the oracle, and against the shared-memory scan (the two pair the FP32
     arithmetic differently, so they agree to rounding).  n = 2500 and 3000 leave ragged last
-    tiles of 1024 samples."""
+    tiles of 1024 samples.  param: group and offset tables in the kernel parameters (1) or in
+    shared memory (0), with bit-identical results."""
     sky, G, d_or = _sky(1, 3, nside, (0.5, 2.0))
     H = sky.halo
     z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=21)
     ms_s, am_s, nl_s, _ = _scan(sky, z, n)
-    sky.set_scan_shape(512, 4, 1)
-    assert sky.get_scan_shape() == (512, 4, 1, 1)
+    sky.set_scan_shape(512, 4, param)
+    assert sky.get_scan_shape() == (512, 4, param, 1)
     ms, am, nl, _ = _scan(sky, z, n)
+    sky.set_scan_shape(512, 4, 1 - param)
+    ms2, am2, nl2, _ = _scan(sky, z, n)
+    assert np.array_equal(ms, ms2) and np.array_equal(am, am2) and np.array_equal(nl, nl2)
     assert np.all(np.abs(ms - ms_s) <= 1e-5 * ms_s.max())
     assert np.mean(am == am_s) > 0.999
     ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
