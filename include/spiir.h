@@ -429,6 +429,20 @@ int spiir_pipeline_run_host(spiir_pipeline_t pipe, const float *strain_host, int
                             float *max_stat_host, int32_t *argmax_host,
                             float *null_stat_host, void *stream);
 
+/* Asynchronous host-buffer step for streaming: the same work as spiir_pipeline_run_host,
+ * enqueued without waiting.  The strain is copied and the chunk processed on stream; the
+ * outputs are copied to the host buffers on the pipeline's own copy stream, so that they
+ * travel while the next submitted chunk is processed (two device staging sets alternate, and
+ * a set is reused only after its copies are done).  strain_host must stay unchanged, and the
+ * output buffers must stay valid and unread, until spiir_pipeline_wait returns; page-locked
+ * host memory is needed for the copies to overlap.  Chunks are processed in submission order.
+ * Errors: SPIIR_EINVAL, SPIIR_ENOMEM (first call: the second staging set), SPIIR_ECUDA. */
+int spiir_pipeline_submit_host(spiir_pipeline_t pipe, const float *strain_host, int64_t n,
+                               float *max_stat_host, int32_t *argmax_host,
+                               float *null_stat_host, void *stream);
+/* Block until every submitted step's outputs are in its host buffers. */
+int spiir_pipeline_wait(spiir_pipeline_t pipe);
+
 /* ------------------------------------------------------------------------------------
  * Batched multirate banks.  Several template banks of uneven size share one strain stream.
  * Every filter runs in one band b at the rate 1 / M_b of the strain (M_b a power of two;

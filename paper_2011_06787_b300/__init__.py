@@ -252,6 +252,21 @@ class Pipeline:
         check(native.lib().spiir_pipeline_run_host(self._h, _host_ptr(strain), n, _host_ptr(max_stat),
                                                    _host_ptr(argmax), _host_ptr(null_stat), _stream_ptr(stream)))
 
+    def submit_host(self, strain: np.ndarray, max_stat: np.ndarray, argmax: np.ndarray, null_stat: np.ndarray,
+                    stream=None):
+        """Enqueue one chunk with host buffers and return; its outputs land in the host buffers
+        by the next wait().  The buffers must stay alive and unread until then (page-locked for
+        overlap)."""
+        for a, dt in ((strain, np.float32), (max_stat, np.float32), (argmax, np.int32), (null_stat, np.float32)):
+            if a.dtype != dt or not a.flags.c_contiguous:
+                raise ValueError("host buffers must be C-contiguous with the documented dtypes")
+        n = strain.shape[1]
+        check(native.lib().spiir_pipeline_submit_host(self._h, _host_ptr(strain), n, _host_ptr(max_stat),
+                                                      _host_ptr(argmax), _host_ptr(null_stat), _stream_ptr(stream)))
+
+    def wait(self):
+        check(native.lib().spiir_pipeline_wait(self._h))
+
 
 class Batch:
     """Batched multirate banks (spiir_batch_*).  banks: list of (offsets, a1, b0, delay, band)

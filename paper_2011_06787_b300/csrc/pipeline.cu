@@ -19,12 +19,32 @@ struct spiir_pipeline_s {
     float *strain_dev = nullptr;
     float *ms_dev = nullptr, *nl_dev = nullptr;
     int32_t *am_dev = nullptr;
+    // asynchronous host-buffer steps: two staging sets alternate; the outputs of a step go to
+    // the host on the copy stream while the next step runs (set 0 is the staging above)
+    bool async_ready = false;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    float *strain2[2] = {nullptr, nullptr}, *ms2[2] = {nullptr, nullptr}, *nl2[2] = {nullptr, nullptr};
+    int32_t *am2[2] = {nullptr, nullptr};
+    int abuf = 0;
 };
 
 namespace spiir {
 
 static void pipe_free(spiir_pipeline_s *p) {
     if (!p) return;
+    if (p->copy) {
+        cudaStreamSynchronize(p->copy);
+        cudaStreamDestroy(p->copy);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (p->computed[b]) cudaEventDestroy(p->computed[b]);
+        if (p->copied[b]) cudaEventDestroy(p->copied[b]);
+    }
+    dev_free(p->strain2[1]);
+    dev_free(p->ms2[1]);
+    dev_free(p->nl2[1]);
+    dev_free(p->am2[1]);
     dev_free(p->zpad[0]);
     dev_free(p->zpad[1]);
     dev_free(p->strain_dev);
@@ -45,6 +65,28 @@ static int pipe_run(spiir_pipeline_s *p, const float *strain, int64_t spitch, in
         SPIIR_CUDA_TRY(cudaMemcpy2DAsync(p->zpad[nxt], p->pitch * sizeof(float2), z + n, p->pitch * sizeof(float2),
                                          2 * H * sizeof(float2), (size_t)T * nd, cudaMemcpyDeviceToDevice, s));
     p->cur = nxt;
+    return SPIIR_OK;
+}
+
+// Lazily created resources of the asynchronous host-buffer steps.
+static int async_init(spiir_pipeline_s *p) {
+    if (p->async_ready) return SPIIR_OK;
+    const int T = p->bank->T, nd = p->bank->n_det;
+    const int64_t m = p->max_chunk;
+    SPIIR_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        SPIIR_CUDA_TRY(cudaEventCreateWithFlags(&p->computed[b], cudaEventDisableTiming));
+        SPIIR_CUDA_TRY(cudaEventCreateWithFlags(&p->copied[b], cudaEventDisableTiming));
+    }
+    p->strain2[0] = p->strain_dev;
+    p->ms2[0] = p->ms_dev;
+    p->nl2[0] = p->nl_dev;
+    p->am2[0] = p->am_dev;
+    SPIIR_TRY(dev_alloc((void **)&p->strain2[1], sizeof(float) * nd * m, "strain staging"));
+    SPIIR_TRY(dev_alloc((void **)&p->ms2[1], sizeof(float) * T * m, "max staging"));
+    SPIIR_TRY(dev_alloc((void **)&p->nl2[1], sizeof(float) * T * m, "null staging"));
+    SPIIR_TRY(dev_alloc((void **)&p->am2[1], sizeof(int32_t) * T * m, "argmax staging"));
+    p->async_ready = true;
     return SPIIR_OK;
 }
 
@@ -114,11 +156,44 @@ extern "C" int spiir_pipeline_run_host(spiir_pipeline_t p, const float *strain_h
     if (n < 1 || n > p->max_chunk) return fail(SPIIR_EINVAL, "n = %lld outside [1, %lld]", (long long)n, (long long)p->max_chunk);
     cudaStream_t s = (cudaStream_t)stream;
     const int T = p->bank->T, nd = p->bank->n_det;
+    if (p->async_ready) SPIIR_CUDA_TRY(cudaStreamSynchronize(p->copy));  // staging set 0 is free
     SPIIR_CUDA_TRY(cudaMemcpyAsync(p->strain_dev, strain_host, sizeof(float) * nd * n, cudaMemcpyHostToDevice, s));
     SPIIR_TRY(pipe_run(p, p->strain_dev, n, n, p->ms_dev, p->am_dev, p->nl_dev, nullptr, s));
     SPIIR_CUDA_TRY(cudaMemcpyAsync(ms_host, p->ms_dev, sizeof(float) * T * n, cudaMemcpyDeviceToHost, s));
     SPIIR_CUDA_TRY(cudaMemcpyAsync(am_host, p->am_dev, sizeof(int32_t) * T * n, cudaMemcpyDeviceToHost, s));
     SPIIR_CUDA_TRY(cudaMemcpyAsync(nl_host, p->nl_dev, sizeof(float) * T * n, cudaMemcpyDeviceToHost, s));
     SPIIR_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_pipeline_submit_host(spiir_pipeline_t p, const float *strain_host, int64_t n, float *ms_host,
+                                          int32_t *am_host, float *nl_host, void *stream) {
+    clear_error();
+    if (!p) return fail(SPIIR_EINVAL, "pipeline is NULL");
+    if (!strain_host || !ms_host || !am_host || !nl_host) return fail(SPIIR_EINVAL, "NULL buffer");
+    if (n < 1 || n > p->max_chunk) return fail(SPIIR_EINVAL, "n = %lld outside [1, %lld]", (long long)n, (long long)p->max_chunk);
+    SPIIR_TRY(async_init(p));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int T = p->bank->T, nd = p->bank->n_det;
+    const int b = p->abuf;
+    // the staging set's previous outputs have reached the host (an event never recorded is
+    // complete)
+    SPIIR_CUDA_TRY(cudaStreamWaitEvent(s, p->copied[b], 0));
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(p->strain2[b], strain_host, sizeof(float) * nd * n, cudaMemcpyHostToDevice, s));
+    SPIIR_TRY(pipe_run(p, p->strain2[b], n, n, p->ms2[b], p->am2[b], p->nl2[b], nullptr, s));
+    SPIIR_CUDA_TRY(cudaEventRecord(p->computed[b], s));
+    SPIIR_CUDA_TRY(cudaStreamWaitEvent(p->copy, p->computed[b], 0));
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(ms_host, p->ms2[b], sizeof(float) * T * n, cudaMemcpyDeviceToHost, p->copy));
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(am_host, p->am2[b], sizeof(int32_t) * T * n, cudaMemcpyDeviceToHost, p->copy));
+    SPIIR_CUDA_TRY(cudaMemcpyAsync(nl_host, p->nl2[b], sizeof(float) * T * n, cudaMemcpyDeviceToHost, p->copy));
+    SPIIR_CUDA_TRY(cudaEventRecord(p->copied[b], p->copy));
+    p->abuf = 1 - b;
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_pipeline_wait(spiir_pipeline_t p) {
+    clear_error();
+    if (!p) return fail(SPIIR_EINVAL, "pipeline is NULL");
+    if (p->async_ready) SPIIR_CUDA_TRY(cudaStreamSynchronize(p->copy));
     return SPIIR_OK;
 }

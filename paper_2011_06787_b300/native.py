@@ -79,6 +79,8 @@ SIGNATURES = {
     "spiir_pipeline_reset": (_I, [_P, _P]),
     "spiir_pipeline_run": (_I, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P]),
     "spiir_pipeline_run_host": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
+    "spiir_pipeline_submit_host": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
+    "spiir_pipeline_wait": (_I, [_P]),
 }
 
 _lib = None
