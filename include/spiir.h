@@ -114,7 +114,7 @@ int spiir_bank_set_state(spiir_bank_t bank, const void *host, size_t bytes);
 
 /* Launch shape of the filter-bank kernel, a tuning knob: the filtered values do not depend on
  * it beyond the order of floating-point summation.  filters_per_lane in {4, 8, 16},
- * lanes_per_block in {128, 256}, steps_per_reduce in {16, 32}, tile a multiple of
+ * lanes_per_block in {128, 256}, steps_per_reduce in {16, 20, 32, 64}, tile a multiple of
  * steps_per_reduce up to 8192 (samples per staged strain window).  The streaming state is
  * kept.  Synchronises the device.  SPIIR_EUNSUPPORTED if a template does not fit or the
  * window does not fit in shared memory; the bank then keeps its previous shape.

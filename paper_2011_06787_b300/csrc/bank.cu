@@ -161,8 +161,9 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
             // pass 1: each warp sums its own rows per column, split at template boundaries;
             // piece j of the warp overwrites row 32*warp + j (a row it has already read).
             // Only rows written by the same warp are read, so a warp barrier suffices.
-            // Lane r owns column r; with R < 32 the remaining lanes have no column.
-            if (busy && wfirst >= 0 && lane < R) {
+            // With R < 32 some lanes have no column; with R = 64 each lane has two.
+            // Lane c owns columns c, c + 32, ... below R.
+            for (int col = lane; busy && wfirst >= 0 && col < R; col += 32) {
                 int j = 0;
                 for (int sg = wfirst; sg < nseg; ++sg) {
                     const int4 g = a.segs[seg0 + sg];
@@ -171,17 +172,17 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                     if (hi <= lo) break;
                     float2 acc = make_float2(0.f, 0.f);
 #ifdef SPIIR_CHECKED
-                    if ((warp * 32 + hi - 1) * (R + 1) + lane >= NL * (R + 1)) {
+                    if ((warp * 32 + hi - 1) * (R + 1) + col >= NL * (R + 1)) {
                         report_bounds(a.status, 8);
                         break;
                     }
 #endif
                     for (int i = lo; i < hi; ++i) {
-                        const float2 v = red[(warp * 32 + i) * (R + 1) + lane];
+                        const float2 v = red[(warp * 32 + i) * (R + 1) + col];
                         acc.x += v.x;
                         acc.y += v.y;
                     }
-                    red[(warp * 32 + j) * (R + 1) + lane] = acc;
+                    red[(warp * 32 + j) * (R + 1) + col] = acc;
                     ++j;
                 }
             }
@@ -267,7 +268,12 @@ static int launch_bank(const BankArgs &a, int n_cta, int n_det, size_t smem, cud
 
 template <int S, int NL>
 static int launch_bank_r(const BankArgs &a, int R, int n_cta, int n_det, size_t smem, cudaStream_t s) {
-    return R == 16 ? launch_bank<S, NL, 16>(a, n_cta, n_det, smem, s) : launch_bank<S, NL, 32>(a, n_cta, n_det, smem, s);
+    switch (R) {
+        case 16: return launch_bank<S, NL, 16>(a, n_cta, n_det, smem, s);
+        case 20: return launch_bank<S, NL, 20>(a, n_cta, n_det, smem, s);
+        case 64: return launch_bank<S, NL, 64>(a, n_cta, n_det, smem, s);
+        default: return launch_bank<S, NL, 32>(a, n_cta, n_det, smem, s);
+    }
 }
 
 template <int S>
@@ -806,7 +812,8 @@ extern "C" int spiir_bank_set_shape(spiir_bank_t b, int filters_per_lane, int la
     if (filters_per_lane != 4 && filters_per_lane != 8 && filters_per_lane != 16)
         return fail(SPIIR_EINVAL, "filters_per_lane must be 4, 8 or 16");
     if (lanes_per_block != 128 && lanes_per_block != 256) return fail(SPIIR_EINVAL, "lanes_per_block must be 128 or 256");
-    if (steps_per_reduce != 16 && steps_per_reduce != 32) return fail(SPIIR_EINVAL, "steps_per_reduce must be 16 or 32");
+    if (steps_per_reduce != 16 && steps_per_reduce != 20 && steps_per_reduce != 32 && steps_per_reduce != 64)
+        return fail(SPIIR_EINVAL, "steps_per_reduce must be 16, 20, 32 or 64");
     if (tile < steps_per_reduce || tile > 8192 || tile % steps_per_reduce != 0)
         return fail(SPIIR_EINVAL, "tile must be a multiple of steps_per_reduce in [steps_per_reduce, 8192]");
     int64_t fmax = 0;

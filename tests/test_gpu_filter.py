@@ -162,7 +162,7 @@ def test_online_full_size_sampled_templates():
 
 
 @pytest.mark.parametrize("shape", [(4, 128, 16, 512), (8, 128, 32, 1024), (8, 256, 16, 2048), (16, 256, 32, 1024),
-                                   (16, 128, 16, 64)])
+                                   (16, 128, 16, 64), (8, 128, 20, 1000), (4, 256, 20, 60), (8, 128, 64, 1024)])
 def test_every_launch_shape_matches_oracle(shape):
     torch = _torch()
     import paper_2011_06787_b300 as sp
@@ -194,7 +194,7 @@ def test_shape_rejections_keep_the_bank_usable():
     assert b.get_shape() == (8, 128, 32, 1024)  # the default for templates of up to 1024 filters
 
 
-@pytest.mark.parametrize("shape", [(8, 128, 16, 1024), (4, 256, 16, 512), (16, 128, 16, 1024)])
+@pytest.mark.parametrize("shape", [(8, 128, 16, 1024), (4, 256, 16, 512), (16, 128, 16, 1024), (8, 128, 20, 1000), (8, 128, 64, 1024)])
 def test_full_blocks_with_short_reduction_blocks(shape):
     # templates of 8 lanes fill every warp of every block, so the last warp reduces too
     torch = _torch()
