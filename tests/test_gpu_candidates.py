@@ -46,6 +46,15 @@ def _same_records(got, want):
     assert [v for *_, v in got] == [v for *_, v in want]  # the same FP32 |z|^2, bit for bit
 
 
+def _oracle_records(cand, cnt, z, off, n, thr, per_second):
+    """The oracle's candidates, after checking that the GPU selected exactly these.  The
+    oracle's side of every later comparison is built from them (never from GPU output)."""
+    import paper_2011_06787_b300 as sp
+    want = oracle.select_candidates(z, off, n, thr, per_second)
+    _same_records(sp.Selector.records(cand, cnt), want)
+    return want
+
+
 def test_selection_on_constructed_peaks():
     """The oracle pin's constructed case: maxima over templates, exact threshold, ties between
     templates and within a second, both sides of a second boundary."""
@@ -164,7 +173,7 @@ def test_foreground_points_match_oracle(n_det, nside, rate):
     T, n, off = 24, 3000, 2 * H + 3
     z = synth.complex_gaussian_snr(4, (T, n_det, off + n + 2 * H + 1), sub=n_det)
     sel, cand, cnt = _select(z, off, n, 3.5, 1024)
-    recs = sp.Selector.records(cand, cnt)
+    recs = _oracle_records(cand, cnt, z, off, n, 3.5, 1024)
     assert len(recs) > 20 and {r for r, *_ in recs} == set(range(n_det))
     ms, am, nl = sp.coherent_candidates(sky, _cuda(z), off, cand, cnt, 0, 1, 205)
     torch.cuda.synchronize()
@@ -204,7 +213,7 @@ def test_background_shifts_match_oracle_and_realign_a_shifted_source(rate):
     # a second, quiet candidate early in the span, where shift 5 reads before entry 0
     z[1, 0, off + 10] += 5.0
     sel, cand, cnt = _select(z, off, n, 4.0, 2048)
-    recs = sp.Selector.records(cand, cnt)
+    recs = _oracle_records(cand, cnt, z.astype(np.complex64), off, n, 4.0, 2048)
     assert (r, 2, k0) in [(a, b, c) for a, b, c, _ in recs] and (0, 1, 10) in [(a, b, c) for a, b, c, _ in recs]
     ms, am, nl = sp.coherent_candidates(sky, _cuda(z.astype(np.complex64)), off, cand, cnt, 0, n_sh, step)
     torch.cuda.synchronize()
@@ -240,7 +249,7 @@ def test_background_points_match_oracle_on_gaussian_snr(n_det, rate, n_sh):
     off = 2 * H + (n_sh // 2) * (n_det - 1) * step  # later shifts leave the buffer for early candidates
     z = synth.complex_gaussian_snr(7, (T, n_det, off + n + 2 * H), sub=10 + n_det)
     sel, cand, cnt = _select(z, off, n, 3.3, 512)
-    recs = sp.Selector.records(cand, cnt)
+    recs = _oracle_records(cand, cnt, z, off, n, 3.3, 512)
     assert len(recs) > 10
     ms, am, nl = sp.coherent_candidates(sky, _cuda(z), off, cand, cnt, 1, n_sh, step)
     torch.cuda.synchronize()
@@ -283,8 +292,7 @@ def test_online_full_size_candidates_and_background():
     fg = sp.coherent_candidates(sky16, zt, off, cand, cnt, 0, 1, step)
     bg = sp.coherent_candidates(sky8, zt, off, cand, cnt, 1, n_sh, step)
     torch.cuda.synchronize()
-    recs = sp.Selector.records(cand, cnt)
-    _same_records(recs, oracle.select_candidates(z, off, n, 4.0, 2048))
+    recs = _oracle_records(cand, cnt, z, off, n, 4.0, 2048)
     assert 300 < len(recs) <= 8192
     pick = list(range(0, len(recs), max(1, len(recs) // 12)))
     for which, (ms, am, nl), G, dd, s0, ns in ((0, fg, G16, d16, 0, 1), (1, bg, G8, d8, 1, n_sh)):

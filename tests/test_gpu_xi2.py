@@ -65,8 +65,9 @@ def test_xi2_of_a_template_shaped_window_is_near_zero():
 
 
 def test_network_average_on_a_coherent_scan():
-    """xi_C^2 gathered at the coherent argmax of a real scan, against the oracle's gather on
-    the same argmax and the oracle's per-detector statistic."""
+    """xi_C^2 gathered at the coherent argmax: the GPU gather and the oracle's gather of the
+    oracle's per-detector statistic, both at the oracle's own coherent argmax (the argmax of
+    the GPU scan agrees with it almost everywhere; the scan's parity is tested elsewhere)."""
     import torch
     import paper_2011_06787_b300 as sp
     det = synth.detectors(1, 3)
@@ -82,18 +83,23 @@ def test_network_average_on_a_coherent_scan():
     am = torch.empty((T, n), dtype=torch.int32, device="cuda")
     nl = torch.empty((T, n), device="cuda")
     sky.scan(_cuda(zs), n, ms, am, nl)
+    _, G, d_or = oracle.sky_geometry(det, sigma, 8, 2048.0)
+    _, am_or, _, _ = oracle.coherent(zs, G, d_or, H, n)
+    assert float(np.mean(am.cpu().numpy() == am_or)) > 0.99
     # xi^2 of samples -H .. n + H - 1 (entry H + k = sample k)
     xi = sp.xi2(_cuda(z), _cuda(A), Nj, n + 2 * H)
-    xc = sp.xi2_network(sky, xi, am, n).cpu().numpy()
+    xc = sp.xi2_network(sky, xi, _cuda(am_or.astype(np.int32)), n).cpu().numpy()
     xi_or = oracle.xi2(z, A, Nj, n + 2 * H)
-    xc_or = oracle.xi2_network(xi_or, tabs[0], am.cpu().numpy(), H)
+    xc_or = oracle.xi2_network(xi_or, d_or, am_or, H)
     assert np.max(np.abs(xc - xc_or) / np.maximum(xc_or, 1.0)) < XI_TOL
 
 
 def test_online_full_size_sampled_templates():
     """The online workload's SNR (1024 templates, 3 detectors, one 2048-sample chunk plus
     Nj = 175 samples of history and lookahead) through the GPU filter bank, then xi^2 for all
-    templates; the oracle recomputes a sample of templates from the same SNR."""
+    templates; the oracle filters the same strain for a sample of templates and computes their
+    xi^2.  The two SNRs agree to the filter bank's parity tolerance (1e-4 of the row maximum),
+    which xi^2 passes on amplified by about the ratio of |z| to the residuals it sums: 5e-4."""
     import torch
     import paper_2011_06787_b300 as sp
     Nj, n = 175, 2048
@@ -111,7 +117,8 @@ def test_online_full_size_sampled_templates():
     A[:] = _cuda(A_or[0])
     A[pick] = _cuda(A_or)
     xi = sp.xi2(zw, A, Nj, n).cpu().numpy()
-    xi_or = oracle.xi2(zw.cpu().numpy()[pick], A_or, Nj, n)
+    z_or, _, _ = oracle.filter_bank(x, sub.offsets, sub.a1, sub.b0, sub.delay)
+    xi_or = oracle.xi2(z_or[:, :, 2048 - Nj: 2048 + n + Nj], A_or, Nj, n)
     err = np.abs(xi[pick] - xi_or) / np.maximum(np.abs(xi_or), 1.0)
-    assert err.max() < XI_TOL, err.max()
+    assert err.max() < 5e-4, err.max()
     assert np.isfinite(xi).all()
