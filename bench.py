@@ -348,7 +348,7 @@ def run_gpu(args):
 
     cands = None
     if "candidates" in args.sections:
-        cands = candidates_rate(args, torch, sp, det, sigma, timed_loop)
+        cands = candidates_rate(args, torch, sp, det, sigma, timed_loop, bank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -440,13 +440,11 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     return out
 
 
-def xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop):
-    """Signal-consistency statistic (Sec. II.C.2) on the online workload: xi_I^2 for every
-    template, detector and sample of a chunk with Nj = 175 (351 taps), from each template's
-    own autocorrelation (responses of 6000 samples by the impulse forward, templates padded to
-    the largest filter count with zero filters), and xi_C^2 at the coherent argmax."""
-    Nj, nr = 175, 6000
-    T, dev = bank.n_templates, am.device
+def bank_autocorr(torch, sp, bank, Nj, dev, nr=6000):
+    """A [T][2 Nj + 1] of every template of the bank (impulse responses of nr samples through the
+    library's impulse forward, templates padded to the largest filter count with zero filters),
+    and the autocorrelation launch's time in ms."""
+    T = bank.n_templates
     F = int(np.diff(bank.offsets).max())
     a1 = np.zeros((T, F), np.complex64)
     b0 = np.zeros((T, F), np.complex64)
@@ -462,8 +460,18 @@ def xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop):
     A = sp.autocorr(u.contiguous(), Nj)
     e1.record()
     e1.synchronize()
-    ac_ms = e0.elapsed_time(e1)
     del u
+    return A, e0.elapsed_time(e1)
+
+
+def xi2_rate(args, torch, sp, b, bank, chunks, sky, am, n, timed_loop):
+    """Signal-consistency statistic (Sec. II.C.2) on the online workload: xi_I^2 for every
+    template, detector and sample of a chunk with Nj = 175 (351 taps), from each template's
+    own autocorrelation (responses of 6000 samples by the impulse forward, templates padded to
+    the largest filter count with zero filters), and xi_C^2 at the coherent argmax."""
+    Nj = 175
+    T, dev = bank.n_templates, am.device
+    A, ac_ms = bank_autocorr(torch, sp, bank, Nj, dev)
     # SNR of two chunks: entry Nj + k of each row is sample k of the xi^2 window
     z = torch.zeros((T, 3, 2 * n), dtype=torch.complex64, device=dev)
     b.reset()
@@ -517,19 +525,21 @@ def frontend_rate(args, torch, sp, timed_loop):
                          "frac": flops / (t * 1e-3) / 1e12 / peak, "flops_per_segment": flops}}
 
 
-def candidates_rate(args, torch, sp, det, sigma, timed_loop):
+def candidates_rate(args, torch, sp, det, sigma, timed_loop, bank):
     """Candidates and the time-shift background (Sec. II.C.1, II.C.3) for one second of the
     online workload: selection over 1024 templates x 3 detectors x 2048 samples (threshold 4),
     the zero-lag coherent statistic of every candidate on the nside-16 sky and 100 time shifts
-    of 0.1 s (205 samples) on the nside-8 sky.  The SNR is normalised complex Gaussian noise
-    (E|z|^2 = 2, seeded on the device) holding 20.5 s of history for the shifts."""
-    T, n, step, n_sh = 1024, 2048, 205, 100
+    of 0.1 s (205 samples) on the nside-8 sky, then xi_C^2 (Sec. II.C.2, Nj = 175, the bank's
+    own autocorrelations) at every candidate and shift.  The SNR is normalised complex Gaussian
+    noise (E|z|^2 = 2, seeded on the device) holding 20.5 s of history for the shifts."""
+    T, n, step, n_sh, Nj = 1024, 2048, 205, 100, 175
     dev = torch.cuda.current_device()
     sky16 = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 16, 2048.0))
     sky8 = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 8, 2048.0))
     H = max(sky16.halo, sky8.halo)
-    off = n_sh * 2 * step + 2 * H
-    pitch = off + n + 2 * H
+    off = n_sh * 2 * step + 2 * H + Nj
+    pitch = off + n + 2 * H + Nj
+    A, _ = bank_autocorr(torch, sp, bank, Nj, dev)
     g = torch.Generator(device="cuda").manual_seed(20110678)
     z = torch.randn((T, 3, pitch), dtype=torch.complex64, device=dev, generator=g) * math.sqrt(2.0)
     sel = sp.Selector(T, 3, n, 2048, 16384)
@@ -546,10 +556,22 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop):
         nonlocal bg
         bg = sp.coherent_candidates(sky8, z, off, sel.cand, sel.n_cand, 1, n_sh, step, out=bg)
 
+    xf = xb = None
+
+    def xi_fore(i):
+        nonlocal xf
+        xf = sp.xi2_candidates(sky16, z, off, A, Nj, sel.cand, sel.n_cand, fg[1], 0, 1, step)
+
+    def xi_back(i):
+        nonlocal xb
+        xb = sp.xi2_candidates(sky8, z, off, A, Nj, sel.cand, sel.n_cand, bg[1], 1, n_sh, step)
+
     def whole(i):
         select(i)
         fore(i)
         back(i)
+        xi_fore(i)
+        xi_back(i)
 
     whole(0)
     torch.cuda.synchronize()
@@ -558,7 +580,10 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop):
     t_sel = float(np.mean(timed_loop(select, steps)))
     t_fg = float(np.mean(timed_loop(fore, steps)))
     t_bg = float(np.mean(timed_loop(back, steps)))
+    t_xf = float(np.mean(timed_loop(xi_fore, steps)))
+    t_xb = float(np.mean(timed_loop(xi_back, steps)))
     t_all = float(np.mean(timed_loop(whole, steps)))
+    xi_fin = float(torch.nanmean(xf[:n_c]).item()) if n_c else None
     sp.device_status()
     sel_bytes = T * 3 * n * 8
     evals_fg, evals_bg = n_c * sky16.n_pix, n_c * n_sh * sky8.n_pix
@@ -566,11 +591,13 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop):
     peak_alu = 148 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     hbm = measured_peaks().get("hbm_gbs")
     out = {"workload": f"{T} templates x 3 det x {n} samples, threshold 4; foreground nside 16 ({sky16.n_pix} px), "
-                       f"background {n_sh} shifts x {step} samples on nside 8 ({sky8.n_pix} px); "
+                       f"background {n_sh} shifts x {step} samples on nside 8 ({sky8.n_pix} px); xi^2 Nj = {Nj}; "
                        f"SNR complex Gaussian E|z|^2 = 2 with {pitch} samples per row",
            "steps": steps, "candidates": n_c, "ms_per_second_of_data": t_all,
            "kernel_ms": {"select (k_select + k_compact)": t_sel, "foreground k_points": t_fg,
-                         "background k_points": t_bg},
+                         "background k_points": t_bg, "foreground k_xi2_points": t_xf,
+                         "background k_xi2_points": t_xb},
+           "mean_xi2_foreground": xi_fin,
            "pixel_evaluations_per_s": (evals_fg + evals_bg) / (t_all * 1e-3),
            "select_gbs": sel_bytes / (t_sel * 1e-3) / 1e9,
            "select_frac_of_measured_hbm": (sel_bytes / (t_sel * 1e-3) / 1e9 / hbm) if hbm else None,
@@ -578,7 +605,7 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop):
                         "achieved": flops_bg / (t_bg * 1e-3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
                         "frac": flops_bg / (t_bg * 1e-3) / 1e12 / peak_alu,
                         "flops_per_launch": flops_bg, "flops_per_pixel": K_POINT_FLOPS}}
-    del z, sel, fg, bg
+    del z, sel, fg, bg, xf, xb, A
     torch.cuda.empty_cache()
     return out
 

@@ -363,6 +363,24 @@ int spiir_coherent_candidates(spiir_sky_t sky, int n_templates, const float *snr
                               int n_shifts, int shift_step, float *max_dev, int32_t *argmax_dev,
                               float *null_dev, void *stream);
 
+/* xi^2 at candidates (Sec. II.C.2 at the points of spiir_coherent_candidates): for the first
+ * min(*n_cand_dev, max_cand) records of cand_dev and the shifts s = first_shift ..
+ * first_shift + n_shifts - 1, with p = argmax_dev[c][s - first_shift] the coherent argmax of the
+ * item (as spiir_coherent_candidates writes it), detector J of the candidate's template is read
+ * at x_J = snr_offset + k + Delta_J(p) - Delta_r(p) + shift_J, shift_J = -s c step for the c-th
+ * companion of the candidate's detector r (0 for r), and
+ *   xi_J^2 = sum_{j=-Nj}^{Nj} |z_J[x_J + j] - z_J[x_J] A_t[j]|^2 / sum_j (2 - 2 |A_t[j]|^2)
+ * with A_dev [T][2 n_lags + 1] as in spiir_xi2.  xi2_dev [max_cand][n_shifts] receives
+ * (1 / N_d) sum_J xi_J^2; xi2_det_dev, if not NULL, [max_cand][n_shifts][n_det] the
+ * per-detector values.  NaN where p is not a pixel of the sky, the record names a detector or
+ * template outside the sky or bank, or a read would leave [0, snr_pitch).  Rows past the count
+ * are not written.  One persistent launch on stream.  Errors: SPIIR_EINVAL. */
+int spiir_xi2_candidates(spiir_sky_t sky, int n_templates, const float *snr_dev, int64_t snr_pitch,
+                         int64_t snr_offset, const float *A_dev, int n_lags, const int32_t *cand_dev,
+                         const int32_t *n_cand_dev, int max_cand, int first_shift, int n_shifts,
+                         int shift_step, const int32_t *argmax_dev, float *xi2_dev,
+                         float *xi2_det_dev, void *stream);
+
 /* ------------------------------------------------------------------------------------
  * Impulse response and its adjoint, for refining IIR coefficients against target
  * templates (the overlap of Sec. II.B.1 Eq. (overlap) is the usual objective).

@@ -14,7 +14,7 @@ from . import native
 from .native import SpiirError, check
 
 __all__ = ["Bank", "Sky", "Pipeline", "Batch", "sky_tables", "autocorr", "xi2", "xi2_network", "Selector",
-           "coherent_candidates", "Frontend", "fir_lowpass", "whitening_kernel", "SpiirError", "device_status", "version"]
+           "coherent_candidates", "xi2_candidates", "Frontend", "fir_lowpass", "whitening_kernel", "SpiirError", "device_status", "version"]
 
 
 def _stream_ptr(stream=None):
@@ -511,3 +511,27 @@ class Frontend:
         check(native.lib().spiir_frontend_run(self._h, _dev_ptr(strain), strain.stride(0), n_in, _dev_ptr(out),
                                               out.stride(0), _stream_ptr(stream)))
         return out
+
+
+def xi2_candidates(sky, snr, offset: int, A, n_lags: int, cand, n_cand, argmax, first_shift: int = 0,
+                   n_shifts: int = 1, shift_step: int = 205, per_detector: bool = False, stream=None):
+    """xi_C^2 [max_cand][n_shifts] at the candidates' coherent argmax pixels (argmax as written by
+    coherent_candidates), with the same time shifts; also [max_cand][n_shifts][n_det] per detector
+    when per_detector.  snr [T][n_det][pitch] complex64 (entry offset + k = sample k), A
+    [T][2 n_lags + 1] complex64."""
+    import torch
+    _require_cuda(snr, torch.complex64, "snr")
+    _require_cuda(A, torch.complex64, "A")
+    _require_cuda(cand, torch.int32, "cand")
+    _require_cuda(argmax, torch.int32, "argmax")
+    if snr.dim() != 3 or not snr.is_contiguous() or not A.is_contiguous() or not argmax.is_contiguous():
+        raise ValueError("snr [T][n_det][pitch], A and argmax must be contiguous")
+    m = cand.shape[0]
+    xi = torch.full((m, n_shifts), float("nan"), dtype=torch.float32, device=snr.device)
+    xd = torch.full((m, n_shifts, snr.shape[1]), float("nan"), dtype=torch.float32, device=snr.device) \
+        if per_detector else None
+    check(native.lib().spiir_xi2_candidates(
+        sky.handle, snr.shape[0], _dev_ptr(snr), snr.shape[-1], int(offset), _dev_ptr(A), int(n_lags), _dev_ptr(cand),
+        _dev_ptr(n_cand), m, int(first_shift), int(n_shifts), int(shift_step), _dev_ptr(argmax), _dev_ptr(xi),
+        _dev_ptr(xd) if xd is not None else None, _stream_ptr(stream)))
+    return (xi, xd) if per_detector else xi

@@ -13,6 +13,7 @@
 // difference d = z[k + j] - z[k] A[j] and its squared modulus take three packed FP32 FMAs
 // against a broadcast table entry (-A.re, -A.im, A.im, -A.re).
 #include <algorithm>
+#include <climits>
 
 #include "coherent.cuh"
 
@@ -159,9 +160,156 @@ __global__ void k_xi2_network(const float *__restrict__ xi, int64_t pitch, const
     out[i] = s / n_det;
 }
 
+// xi^2 at candidate points (with the candidate scan of Sec. II.C.1 and the time shifts of
+// Sec. II.C.3), in a persistent grid of warps.  With p the coherent argmax of a (candidate,
+// shift) pair, detector J is read at x_J = e + Delta_J(p) - Delta_r(p) + shift_J (shift_J =
+// -s c_J step for the c-th companion of the candidate's detector r); the lanes stride the taps
+// j = -Nj .. Nj of each detector and the sums are reduced by shuffles.
+struct XiPointArgs {
+    const float2 *snr;  // [T][n_det][pitch], entry off + k is sample k
+    int64_t pitch, off;
+    int n_templates, n_det, n_pix;
+    const float2 *A;  // [T][2 Nj + 1]
+    int Nj;
+    const int4 *cand;
+    const int32_t *n_cand;
+    int max_cand, first_shift, n_shifts;
+    int64_t step;
+    const int32_t *argmax;  // [max_cand][n_shifts]
+    const int16_t *delays;  // [P][n_det]
+    float *xi2;             // [max_cand][n_shifts]
+    float *xi2_det;         // NULL or [max_cand][n_shifts][n_det]
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+constexpr int kXiPtShifts = 8;  // shifts per warp item
+
+// xi^2 of one detector row at sample x (entries x - Nj .. x + Nj), summed over the warp
+__device__ __forceinline__ float xi_num(const float2 *__restrict__ row, const float2 *__restrict__ At, int Nj, int lane) {
+    const float2 zc = row[Nj];
+    float num = 0.f;
+    for (int j = lane; j < 2 * Nj + 1; j += 32) {
+        const float2 v = row[j], A = At[j];
+        const float dr = v.x - (zc.x * A.x - zc.y * A.y);
+        const float di = v.y - (zc.x * A.y + zc.y * A.x);
+        num = fmaf(dr, dr, fmaf(di, di, num));
+    }
+    return warp_sum(num);
+}
+
+// One warp per (candidate, chunk of kXiPtShifts shifts).  The candidate's own detector r is
+// read at its sample for every pixel and shift, so its xi^2 is evaluated once per item; the
+// companions at each shift's argmax pixel.
+__global__ void __launch_bounds__(256) k_xi2_points(const __grid_constant__ XiPointArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int nc = min(*a.n_cand, a.max_cand);
+    const int n_chunks = (a.n_shifts + kXiPtShifts - 1) / kXiPtShifts;
+    const int64_t n_items = (int64_t)max(nc, 0) * n_chunks;
+    const int ntap = 2 * a.Nj + 1;
+    const float nan = __int_as_float(0x7fc00000);
+    for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items; item += warps) {
+        const int c = (int)(item / n_chunks), s0 = (int)(item % n_chunks) * kXiPtShifts;
+        const int s1 = min(a.n_shifts, s0 + kXiPtShifts);
+        const int4 cd = a.cand[c];
+        const int r = cd.x, t = cd.y;
+        const int64_t e = a.off + (int64_t)cd.z;
+        const bool rec_ok = r >= 0 && r < a.n_det && t >= 0 && t < a.n_templates && cd.z >= 0 && e - a.Nj >= 0 &&
+                            e + a.Nj < a.pitch;
+        const float2 *At = a.A + (int64_t)(rec_ok ? t : 0) * ntap;
+        // denominator sum_j (2 - 2 |A_t[j]|^2), shared by the detectors and shifts
+        float den = 0.f;
+        for (int j = lane; j < ntap; j += 32) {
+            const float2 v = At[j];
+            den += 2.f - 2.f * (v.x * v.x + v.y * v.y);
+        }
+        den = warp_sum(den);
+        const float xi_r = rec_ok ? xi_num(a.snr + ((int64_t)t * a.n_det + r) * a.pitch + e - a.Nj, At, a.Nj, lane) / den
+                                  : nan;
+        for (int si = s0; si < s1; ++si) {
+            const int64_t o = (int64_t)c * a.n_shifts + si;
+            const int p = a.argmax[o];
+            const int64_t s = (int64_t)a.first_shift + si;
+            bool ok = rec_ok && p >= 0 && p < a.n_pix;
+            float total = 0.f;
+            int comp = 0;
+            for (int J = 0; J < a.n_det && ok; ++J) {
+                float xi;
+                if (J == r) {
+                    xi = xi_r;
+                } else {
+                    const int64_t x = e + a.delays[(int64_t)p * a.n_det + J] - a.delays[(int64_t)p * a.n_det + r] -
+                                      s * (++comp) * a.step;
+                    if (x - a.Nj < 0 || x + a.Nj >= a.pitch) {
+                        ok = false;
+                        break;
+                    }
+                    xi = xi_num(a.snr + ((int64_t)t * a.n_det + J) * a.pitch + x - a.Nj, At, a.Nj, lane) / den;
+                }
+                total += xi;
+                if (a.xi2_det && lane == 0) a.xi2_det[o * a.n_det + J] = xi;
+            }
+            if (lane == 0) {
+                a.xi2[o] = ok ? total / a.n_det : nan;
+                if (!ok && a.xi2_det)
+                    for (int J = 0; J < a.n_det; ++J) a.xi2_det[o * a.n_det + J] = nan;
+            }
+        }
+    }
+}
+
 }  // namespace spiir
 
 using namespace spiir;
+
+extern "C" int spiir_xi2_candidates(spiir_sky_t sky, int T, const float *snr, int64_t pitch, int64_t off,
+                                    const float *A, int n_lags, const int32_t *cand, const int32_t *n_cand,
+                                    int max_cand, int first_shift, int n_shifts, int shift_step,
+                                    const int32_t *argmax, float *xi2, float *xi2_det, void *stream) {
+    clear_error();
+    if (!sky) return fail(SPIIR_EINVAL, "sky is NULL");
+    if (T < 1 || max_cand < 0 || n_shifts < 1 || first_shift < 0 || shift_step < 0 || off < 0 || pitch < 1)
+        return fail(SPIIR_EINVAL, "n_templates = %d, max_cand = %d, first_shift = %d, n_shifts = %d, shift_step = %d",
+                    T, max_cand, first_shift, n_shifts, shift_step);
+    if (n_lags < 0 || n_lags > kXiMaxLags) return fail(SPIIR_EINVAL, "n_lags = %d outside [0, %d]", n_lags, kXiMaxLags);
+    if ((int64_t)max_cand * n_shifts > INT_MAX) return fail(SPIIR_EINVAL, "max_cand x n_shifts above 2^31 - 1");
+    if (!snr || !A || !n_cand || (max_cand > 0 && (!cand || !argmax || !xi2))) return fail(SPIIR_EINVAL, "NULL pointer");
+    if (((uintptr_t)snr) % 8 || ((uintptr_t)A) % 8 || (cand && ((uintptr_t)cand) % 16))
+        return fail(SPIIR_EINVAL, "snr and A must be 8-byte aligned, cand 16-byte aligned");
+    if (max_cand == 0) return SPIIR_OK;
+    XiPointArgs a{};
+    a.snr = reinterpret_cast<const float2 *>(snr);
+    a.pitch = pitch;
+    a.off = off;
+    a.n_templates = T;
+    a.n_det = sky->n_det;
+    a.n_pix = sky->n_pix;
+    a.A = reinterpret_cast<const float2 *>(A);
+    a.Nj = n_lags;
+    a.cand = reinterpret_cast<const int4 *>(cand);
+    a.n_cand = n_cand;
+    a.max_cand = max_cand;
+    a.first_shift = first_shift;
+    a.n_shifts = n_shifts;
+    a.step = shift_step;
+    a.argmax = argmax;
+    a.delays = sky->d_delays;
+    a.xi2 = xi2;
+    a.xi2_det = xi2_det;
+    int dev = 0, n_sm = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t items = (int64_t)max_cand * ((n_shifts + kXiPtShifts - 1) / kXiPtShifts);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)n_sm * 8));
+    k_xi2_points<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
 
 extern "C" int spiir_autocorr(int T, const float *u, int64_t n_resp, int n_lags, float *A, void *stream) {
     clear_error();

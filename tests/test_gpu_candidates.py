@@ -311,3 +311,59 @@ def test_online_full_size_candidates_and_background():
         g_am = np.array([am[c, s] for c, s in rows])
         g_nl = np.array([nl[c, s] for c, s in rows])
         _assert_points_close(g_ms, g_am, g_nl, mo, ao, no, at)
+
+
+def _responses(T, F, nr, seed):
+    g = np.random.default_rng(seed)
+    a1 = (g.uniform(0.8, 0.98, (T, F)) * np.exp(1j * g.uniform(0, 2 * np.pi, (T, F)))).astype(np.complex64)
+    b0 = ((g.standard_normal((T, F)) + 1j * g.standard_normal((T, F))) / np.sqrt(2 * F)).astype(np.complex64)
+    d = g.integers(0, nr // 3, (T, F)).astype(np.int32)
+    off = np.arange(T + 1, dtype=np.int64) * F
+    return oracle.impulse_forward(off, a1.ravel(), b0.ravel(), d.ravel(), np.zeros(T * F, np.complex64), nr)
+
+
+@pytest.mark.parametrize("n_det,Nj,n_sh", [(3, 40, 6), (2, 175, 1), (4, 7, 9)])
+def test_xi2_at_candidates_matches_oracle(n_det, Nj, n_sh):
+    """xi_C^2 at each (candidate, shift) item at the oracle's coherent argmax, against the
+    oracle's xi^2 on a one-sample window at each detector's implied time; items whose reads
+    leave the buffer are NaN."""
+    import torch
+    import paper_2011_06787_b300 as sp
+    sky, G, d_or = _sky(3, n_det, 4)
+    H = sky.halo
+    T, n, step = 8, 1200, 37
+    off = 2 * H + Nj + (n_sh // 2) * (n_det - 1) * step
+    z = synth.complex_gaussian_snr(8, (T, n_det, off + n + 2 * H + Nj + 1), sub=n_det)
+    A = oracle.autocorr(_responses(T, 30, 1500, seed=n_det), Nj).astype(np.complex64)
+    sel, cand, cnt = _select(z, off, n, 3.2, 400)
+    recs = _oracle_records(cand, cnt, z, off, n, 3.2, 400)
+    assert len(recs) > 5
+    dmin = {(a, b): int(np.min(d_or[:, b] - d_or[:, a])) for a in range(n_det) for b in range(n_det)}
+    # the oracle's coherent argmax of every item (NaN items keep -1)
+    am = np.full((sel.max_cand, n_sh), -1, np.int32)
+    for c, (r, t, k, _) in enumerate(recs):
+        for si in range(n_sh):
+            shv = oracle.background_shifts(r, n_det, si, step)
+            if all(off + k + shv[J] + dmin[(r, J)] >= 0 for J in range(n_det)):
+                _, a_or, _ = oracle.coherent_points(z, G, d_or, np.array([[t, r, off + k]], np.int64), shv[None])
+                am[c, si] = a_or[0]
+    xi, xd = sp.xi2_candidates(sky, _cuda(z), off, _cuda(A), Nj, cand, cnt, _cuda(am), 0, n_sh, step, per_detector=True)
+    torch.cuda.synchronize()
+    xi, xd = xi.cpu().numpy(), xd.cpu().numpy()
+    n_nan = 0
+    for c, (r, t, k, _) in enumerate(recs):
+        for si in range(n_sh):
+            p = int(am[c, si])
+            shv = oracle.background_shifts(r, n_det, si, step)
+            xs = [off + k + int(d_or[p, J]) - int(d_or[p, r]) + int(shv[J]) for J in range(n_det)] if p >= 0 else []
+            if p < 0 or any(x - Nj < 0 for x in xs):
+                assert np.isnan(xi[c, si]) and np.isnan(xd[c, si]).all(), (c, si)
+                n_nan += 1
+                continue
+            want = [oracle.xi2(z[t:t + 1, J:J + 1, x - Nj: x + Nj + 1], A[t:t + 1], Nj, 1)[0, 0, 0]
+                    for J, x in enumerate(xs)]
+            np.testing.assert_allclose(xd[c, si], want, rtol=1e-4, atol=1e-4)
+            np.testing.assert_allclose(xi[c, si], np.mean(want), rtol=1e-4, atol=1e-4)
+    assert bool(np.all(np.isnan(xi[len(recs):])))
+    if n_sh > 1:
+        assert n_nan > 0
