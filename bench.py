@@ -411,6 +411,15 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     nl = torch.empty((T, chunk), device=dev)
     xs = [torch.from_numpy(synth.multirate_chunk(i, 3, chunk)).to(dev) for i in range(args.warmup + args.steps)]
     x = torch.empty((3, chunk), device=dev)
+    # the scan shape of this sky, tuned on Gaussian SNR of the batch's size (seeded)
+    if args.scan_shape:
+        sky.set_scan_shape(*[int(v) for v in args.scan_shape.split(",")])
+    elif not args.no_tune:
+        g = torch.Generator(device="cuda").manual_seed(20110678 + 2)
+        zr = torch.randn((T, 3, chunk + 2 * sky.halo), dtype=torch.complex64, device=dev, generator=g) * math.sqrt(2.0)
+        autotune.tune_scan(sky, zr, chunk, ms, am, nl)
+        del zr
+    scan_shape = list(sky.get_scan_shape()[:3])
     if args.batch_shape:
         shp = [int(v) for v in args.batch_shape.split(",")]
         batch.set_shape(*shp)
@@ -420,7 +429,7 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     out = {"workload": f"{len(banks)} banks, {T} templates, {F} filters over bands 2048/512/128 Hz, "
                        f"3 det, {chunk}-sample chunks, nside {c['nside']}",
            "updates_per_chunk": updates, "pixel_samples_per_chunk": T * chunk * sky.n_pix,
-           "persistent_work_items": items, "tuned_shape": tuned["shape"]}
+           "persistent_work_items": items, "tuned_shape": tuned["shape"], "scan_shape": scan_shape}
     for mode, name in ((0, "plain"), (1, "batched"), (2, "batched_graph")):
         batch.reset()
         for i in range(args.warmup):
