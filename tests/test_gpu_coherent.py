@@ -191,6 +191,35 @@ def test_every_scan_shape_matches_oracle(shape, n_det):
     assert np.all(np.abs(mp - sm_or) <= 1e-4 * sm_or.max(axis=-1, keepdims=True))
 
 
+@pytest.mark.parametrize("rate,shape", [(16384.0, (256, 2, 1)), (16384.0, (512, 1, 0)), (8192.0, (256, 1, 1))])
+def test_long_delays_take_the_fallback_layouts(rate, shape):
+    """Skies sampled at 8 and 16 kHz (|Delta| up to 173 and 346 samples): the tensor-memory scan
+    does not apply, and the shared-memory scan stages wider windows (or reads through L1);
+    results against the oracle as at 2048 Hz."""
+    import paper_2011_06787_b300 as sp
+    det = synth.detectors(1, 3)
+    sigma = synth.noise_weights(1, 3, 0.5, 2.0)
+    tabs = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 4, rate)
+    sky = sp.Sky(*tabs)
+    _, G, d_or = oracle.sky_geometry(det, sigma, 4, rate)
+    H = sky.halo
+    assert H == int(np.abs(d_or).max()) and H > 60
+    with pytest.raises(sp.SpiirError):
+        sky.set_scan_shape(512, 4, 1)
+    sky.set_scan_shape(*shape)
+    z = synth.complex_gaussian_snr(1, (2, 3, 1300 + 2 * H), sub=40)
+    ms, am, nl, _ = _scan(sky, z, 1300)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, 1300, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+
+
+def test_delays_beyond_the_limit_are_rejected():
+    import paper_2011_06787_b300 as sp
+    det = synth.detectors(1, 3)
+    with pytest.raises(sp.SpiirError):
+        sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, np.ones(3), 4, 49152.0))   # |Delta| = 1038 > 1024
+
+
 def test_general_kernel_for_non_orthonormal_tables():
     import paper_2011_06787_b300 as sp
     sky, G, d_or = _sky(1, 3, 4, (0.5, 2.0))
