@@ -220,6 +220,25 @@ def test_delays_beyond_the_limit_are_rejected():
         sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, np.ones(3), 4, 49152.0))   # |Delta| = 1038 > 1024
 
 
+def test_sky_map_moments_in_gaussian_noise():
+    """Statistical invariant on the GPU (App. A): with i.i.d. complex Gaussian SNR of
+    E|z_I|^2 = 2 the coherent statistic at a fixed pixel is chi^2 with 4 degrees of freedom,
+    mean 4 and variance 8; checked on the sky map of 1.2e6 pixel-samples."""
+    sky, G, d_or = _sky(1, 3, 4, (0.5, 2.0))
+    H = sky.halo
+    T, n = 3, 2048
+    z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=50)
+    _, _, _, mp = _scan(sky, z, n, skymap=True)
+    assert mp.size == T * 192 * n
+    # 6144 independent samples per pixel: the mean of a chi^2_4 has a standard error of 0.036
+    # at most (less after the average over correlated pixels), its variance about 0.2
+    assert abs(float(mp.mean()) - 4.0) < 0.1, mp.mean()
+    assert abs(float(mp.var()) - 8.0) < 0.8, mp.var()
+    # per pixel over samples: every pixel's statistic has the same distribution
+    per_pix = mp.mean(axis=(0, 2))
+    assert np.all(np.abs(per_pix - 4.0) < 0.35)
+
+
 def test_general_kernel_for_non_orthonormal_tables():
     import paper_2011_06787_b300 as sp
     sky, G, d_or = _sky(1, 3, 4, (0.5, 2.0))

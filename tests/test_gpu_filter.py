@@ -86,6 +86,25 @@ def test_edge_cases_empty_single_and_large_templates():
     assert_snr_close(z[1:], z_or[1:])
 
 
+def test_maximum_delay_carries_across_chunks():
+    """A filter at the largest supported delay (32768 samples, a 16 s strain window) answers an
+    impulse only in a later chunk, as b0 a1^(k - 5 - d); one sample more is rejected."""
+    import paper_2011_06787_b300 as sp
+    a = np.array([0.999 * np.exp(0.3j), 0.9 * np.exp(-1.1j)], np.complex64)
+    b = np.array([0.5 + 0.2j, 0.25 - 0.1j], np.complex64)
+    d = np.array([32768, 7], np.int32)
+    bank = synth.Bank(np.array([0, 2], np.int64), a, b, d)
+    x = np.zeros((1, 40000), np.float32)
+    x[0, 5] = 1.0
+    z, _ = _run_bank(bank, x, chunks=[20000, 20000])
+    k = np.arange(40000)
+    ref = sum(np.where(k >= 5 + dl, complex(bl) * complex(al) ** np.maximum(k - 5 - dl, 0), 0) for al, bl, dl in zip(a, b, d))
+    assert np.max(np.abs(z[0, 0] - ref)) <= 1e-5 * np.abs(ref).max()
+    assert abs(z[0, 0, 5 + 32768] - (b[0] + complex(b[1]) * complex(a[1]) ** 32768)) < 1e-6
+    with pytest.raises(sp.SpiirError):
+        sp.Bank(1, np.array([0, 1], np.int64), a[:1], b[:1], np.array([32769], np.int32))
+
+
 def test_impulse_response_closed_form_on_gpu():
     a = np.array([0.995 * np.exp(0.7j)], np.complex64)
     b = np.array([0.3 - 0.4j], np.complex64)
