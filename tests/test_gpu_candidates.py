@@ -117,6 +117,20 @@ def test_selection_of_quiet_data_is_empty_and_repeatable():
         assert sp.Selector.records(cand, cnt) == [(1, 5, 1234, 9.0)]
 
 
+def test_nan_snr_is_never_a_candidate():
+    """A NaN sample neither becomes a candidate nor hides the real maximum of its sample: the
+    records equal the oracle's on the same SNR with the NaN samples set to zero."""
+    import paper_2011_06787_b300 as sp
+    z = synth.complex_gaussian_snr(5, (12, 2, 3000), sub=3)
+    z[4, 0, 100] = np.nan
+    z[7, 1, 2000:2010] = np.nan + 1j * np.nan
+    z[3, 0, 100] = 9.0                     # the real maximum of sample 100 of detector 0
+    _, cand, cnt = _select(z, 0, 3000, 3.5, 1024)
+    clean = np.where(np.isnan(z), 0, z)
+    _same_records(sp.Selector.records(cand, cnt), oracle.select_candidates(clean, 0, 3000, 3.5, 1024))
+    assert (0, 3, 100) in [(a, b, c) for a, b, c, _ in sp.Selector.records(cand, cnt)]
+
+
 def test_selection_rejects_bad_arguments():
     import torch
     import paper_2011_06787_b300 as sp
