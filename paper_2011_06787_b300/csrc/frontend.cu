@@ -10,9 +10,9 @@
 //
 // Device mapping.  k_fe_decimate: one thread per output sample, the block's input window kept
 // in shared memory as M phase planes (sample i of the window in plane i mod M, row i / M) so
-// that consecutive outputs read consecutive words.  k_fe_whiten: a block computes 256 outputs
-// of one detector; a thread owns 8 consecutive outputs and one of 16 slices of the taps, slides
-// a 16-register window over the input, and the 16 partial sums of each output are added in a
+// that consecutive outputs read consecutive words.  k_fe_whiten: a block computes 128 outputs
+// of one detector; a thread owns 8 consecutive outputs and one of 64 slices of the taps, slides
+// a 16-register window over the input, and the 64 partial sums of each output are added in a
 // fixed order.  Both kernels read the previous segment's samples from a history buffer and
 // write the new history to the other buffer of a pair (the next call reads it), so no copy of
 // the input is made and blocks never race on the history.
@@ -36,10 +36,10 @@ struct spiir_frontend_s {
 namespace spiir {
 
 constexpr int kFeDecOut = 128;          // outputs per block of k_fe_decimate
-constexpr int kFeWhOut = 256;           // outputs per block of k_fe_whiten
+constexpr int kFeWhOut = 128;           // outputs per block of k_fe_whiten
 constexpr int kFeWhQ = 8;               // outputs per thread
-constexpr int kFeWhSlices = 16;         // tap slices
-constexpr int kFeWhThreads = (kFeWhOut / kFeWhQ) * kFeWhSlices;  // 512
+constexpr int kFeWhSlices = 64;         // tap slices
+constexpr int kFeWhThreads = (kFeWhOut / kFeWhQ) * kFeWhSlices;  // 1024
 constexpr int kFeTapAlign = kFeWhSlices * 8;                     // padded tap count granularity
 constexpr int kFeMaxLw = 16384 + 1;
 constexpr int kFeMaxLd = 8192;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kFeWhThreads) k_fe_whiten(const float *__restr
                                                            int L, float *__restrict__ y, int64_t y_pitch) {
     extern __shared__ float fe_smem[];
     const int det = blockIdx.y;
-    const int L1 = L - 1;                        // L is the padded tap count (a multiple of 128)
+    const int L1 = L - 1;                        // L is the padded tap count (a multiple of 512)
     const float *dr = dec + (int64_t)det * dec_pitch;
     const float *hr = hist_in + (int64_t)det * L1;
     const int64_t k0 = (int64_t)blockIdx.x * kFeWhOut;
