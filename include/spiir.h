@@ -424,6 +424,9 @@ int spiir_impulse_backward(int n_templates, int filters_per_template, const floa
  * SNR history of 2 H samples, coherent scan).  Output sample j of a call is geocentric
  * sample (stream position of the chunk start) + j - H: the coherent stage lags the
  * strain by H samples so that every detector's delayed SNR is available.
+ * The streaming state (bank states, strain and SNR history, staging buffers) is ordered only
+ * by the CUDA stream: every call on one pipeline must use the same stream, and one pipeline
+ * must not be driven from two host threads at once.
  * ---------------------------------------------------------------------------------- */
 
 /* bank and sky must have the same n_det and must outlive the pipeline.  max_chunk
