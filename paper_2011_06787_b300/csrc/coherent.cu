@@ -459,6 +459,8 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         m.null_stat = null_stat;
         m.skymap = skymap;
         m.map_vec = (n % 4 == 0 && ((uintptr_t)skymap % 16) == 0) ? 1 : 0;
+        // short chunks: several templates share a work item (their rows split the 128 lanes)
+        m.nsub = n <= 256 ? 4 : (n <= 512 ? 2 : 1);
         return launch_coherent_tmem(m, sky->scan_tmem_param ? sky->t_tab : nullptr, stream);
     }
     if (sky->grouped) {

@@ -55,6 +55,7 @@ struct TmemArgs {
     float *null_stat;
     float *skymap;          // NULL or [T][P][n]
     int map_vec;            // 1: n % 4 == 0 and skymap 16-byte aligned (vector stores)
+    int nsub;               // templates per work item (1, 2 or 4): 128 / nsub rows each
 };
 
 // Per-pixel delay offsets (delta_1 | delta_2 << 16) and the pixel groups of the tensor-memory

@@ -96,7 +96,7 @@ __device__ __forceinline__ int tpos(int x, int L) { return (x & 7) * L + (x >> 3
 // PT: the group table and the per-pixel offsets come from the kernel parameter pt (read with
 // warp-uniform indices, so the tensor-memory addresses stay in uniform registers); otherwise
 // from shared memory.
-template <bool MAP, bool PT>
+template <bool MAP, bool PT, int NSUB>
 __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -106,9 +106,15 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
     const int q = warp & 3, sl = warp >> 2;
     const int row = 32 * q + lane;
     const int P = a.n_pix, G = a.n_grp, H = a.H, C = a.C;
-    const int W0 = kTmKT + C;       // staged samples per plane
+    // nsub templates per work item: template s of the item owns rows s RPT .. (s + 1) RPT - 1
+    // and the tile segment s SEG .. s SEG + SEG - 1 (its 8 RPT samples plus the C-sample halo)
+    constexpr int nsub = NSUB, RPT = kTmRows / NSUB, KS = kTmM * RPT;
+    const int SEG = KS + C;
+    const int W0 = nsub * SEG;      // staged samples per plane
     const int L = W0 / 8 + 1;       // transposed plane stride (odd)
     const int PL = 8 * L;           // floats per staged plane
+    const int rsub = row / RPT;                          // this thread row's template in an item
+    const int rbase = rsub * SEG + kTmM * (row % RPT);   // tile position of the row's first sample
 
     float4 *ent = reinterpret_cast<float4 *>(smem);
     size_t off = (size_t)P * sizeof(float4);
@@ -142,23 +148,26 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
     const uint32_t la = tbase + ((uint32_t)(32 * q) << 16);  // this warp's lane quarter
     const int g_lo = a.slice[sl], g_hi = a.slice[sl + 1];
 
-    const int ntiles = (int)((a.n + kTmKT - 1) / kTmKT);
-    const int64_t n_items = (int64_t)a.n_templates * ntiles;
+    const int ntiles = (int)((a.n + KS - 1) / KS);
+    const int64_t n_items = (int64_t)((a.n_templates + nsub - 1) / nsub) * ntiles;
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int t = (int)(item / ntiles);
-        const int64_t k0 = (item % ntiles) * (int64_t)kTmKT;
+        const int t0 = (int)(item / ntiles) * nsub;      // the item's first template
+        const int64_t k0 = (item % ntiles) * (int64_t)KS;
         const int64_t lim = a.n + 2 * H - k0;  // staged entries past this are zero
+        const int trow = t0 + rsub;                      // this row's template
         // the previous item's TMEM and shared-memory reads are complete past this point
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
         for (int I = 0; I < 3; ++I) {
-            const float2 *src = a.snr + ((int64_t)t * 3 + I) * a.pitch + k0;
             float *re = zp + (2 * I) * PL, *im = re + PL;
-            for (int j = tid; j < W0; j += kTmThreads) {
-                const float2 v = (j < lim) ? src[j] : make_float2(0.f, 0.f);
-                re[tpos(j, L)] = v.x;
-                im[tpos(j, L)] = v.y;
+            for (int x = tid; x < W0; x += kTmThreads) {
+                const int s = x / SEG, j = x - s * SEG;
+                const int ts = t0 + s;
+                const float2 v = (ts < a.n_templates && j < lim) ? a.snr[((int64_t)ts * 3 + I) * a.pitch + k0 + j]
+                                                                 : make_float2(0.f, 0.f);
+                re[tpos(x, L)] = v.x;
+                im[tpos(x, L)] = v.y;
             }
         }
         __syncthreads();
@@ -173,7 +182,7 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                 float v[8];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    const int x = 8 * row + c0 + m;
+                    const int x = rbase + c0 + m;
                     v[2 * m] = re[tpos(x, L)];
                     v[2 * m + 1] = im[tpos(x, L)];
                 }
@@ -202,7 +211,7 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
             float gm[kTmM];
 #pragma unroll
             for (int m = 0; m < kTmM; ++m) {
-                const int x = 8 * row + d0 + m;
+                const int x = rbase + d0 + m;
                 w0[m] = pack2(z0r[tpos(x, L)], z0i[tpos(x, L)]);
                 s0[m] = mul2(w0[m], w0[m]);
                 gm[m] = -INFINITY;
@@ -224,11 +233,11 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                     v[m] = __fadd_rn(d.x, d.y);
                     gm[m] = fmaxf(gm[m], v[m]);
                 }
-                if (MAP) {
+                if (MAP && trow < a.n_templates) {
                     // the row's 8 samples of this pixel: one contiguous 1 KB segment per warp,
                     // written with the streaming (evict-first) hint
-                    const int64_t kr = k0 + 8 * row;
-                    float *mrow = a.skymap + ((int64_t)t * P + orig[p]) * a.n + kr;
+                    const int64_t kr = k0 + kTmM * (row % RPT);
+                    float *mrow = a.skymap + ((int64_t)trow * P + orig[p]) * a.n + kr;
                     if (a.map_vec && kr + kTmM <= a.n) {
                         __stcs(reinterpret_cast<float4 *>(mrow), make_float4(v[0], v[1], v[2], v[3]));
                         __stcs(reinterpret_cast<float4 *>(mrow) + 1, make_float4(v[4], v[5], v[6], v[7]));
@@ -253,8 +262,14 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         __syncthreads();
         // merge the slices and resolve the argmax (lowest original pixel index among equal maxima)
         for (int j = tid; j < kTmKT; j += kTmThreads) {
-            if (k0 + j >= a.n) continue;
-            const int cj = (j & 7) * kTmRows + (j >> 3);  // sample j = 8 row + m sits at [m][row]
+            // slot j = 8 row + m: template t0 + row / RPT, its sample k0 + 8 (row % RPT) + m, tile
+            // position xj
+            const int jr = j >> 3, js = jr / RPT;
+            const int jk = kTmM * (jr - js * RPT) + (j & 7);
+            const int xj = js * SEG + jk;
+            const int tj = t0 + js;
+            if (tj >= a.n_templates || k0 + jk >= a.n) continue;
+            const int cj = (j & 7) * kTmRows + jr;  // slot j sits at [m][row]
             float B = cb_best[cj];
             for (int s = 1; s < 4; ++s) B = fmaxf(B, cb_best[s * kTmKT + cj]);
             int hits = 0;
@@ -274,9 +289,9 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                 const uint32_t o = __float_as_uint(e.w);
                 const int d1 = (int)(o & 0xFFFFu), d2 = (int)(o >> 16);
                 const float *r0 = zp, *r1 = zp + 2 * PL, *r2 = zp + 4 * PL;
-                const float w0r = r0[tpos(j + d0, L)], w0i = r0[PL + tpos(j + d0, L)];
-                const float w1r = r1[tpos(j + d1, L)], w1i = r1[PL + tpos(j + d1, L)];
-                const float w2r = r2[tpos(j + d2, L)], w2i = r2[PL + tpos(j + d2, L)];
+                const float w0r = r0[tpos(xj + d0, L)], w0i = r0[PL + tpos(xj + d0, L)];
+                const float w1r = r1[tpos(xj + d1, L)], w1i = r1[PL + tpos(xj + d1, L)];
+                const float w2r = r2[tpos(xj + d2, L)], w2i = r2[PL + tpos(xj + d2, L)];
                 const float Ar = __fmaf_rn(w2r, w2r, __fmaf_rn(w1r, w1r, __fmul_rn(w0r, w0r)));
                 const float Ai = __fmaf_rn(w2i, w2i, __fmaf_rn(w1i, w1i, __fmul_rn(w0i, w0i)));
                 const float nr = __fmaf_rn(e.z, w2r, __fmaf_rn(e.y, w1r, __fmul_rn(e.x, w0r)));
@@ -316,7 +331,7 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                 }
             }
             if (arg == 0x7fffffff) arg = 0;  // only when every statistic is NaN
-            const int64_t o = (int64_t)t * a.n + k0 + j;
+            const int64_t o = (int64_t)tj * a.n + k0 + jk;
             a.max_stat[o] = B;
             a.argmax[o] = arg;
             a.null_stat[o] = nul;
@@ -328,19 +343,43 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512u) : "memory");
 }
 
-template <bool MAP>
+template <bool MAP, int NSUB>
 __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_constant__ TmemArgs a) {
-    tmem_scan<MAP, false>(a, nullptr);
+    tmem_scan<MAP, false, NSUB>(a, nullptr);
 }
 
-template <bool MAP>
+template <bool MAP, int NSUB>
 __global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem_pt(const __grid_constant__ TmemArgs a,
                                                                    const __grid_constant__ TmemTab pt) {
-    tmem_scan<MAP, true>(a, &pt);
+    tmem_scan<MAP, true, NSUB>(a, &pt);
 }
 
-size_t tmem_scan_smem(int n_pix, int n_grp, int C) {
-    const int W0 = kTmKT + C, L = W0 / 8 + 1;
+template <int NSUB>
+static int launch_tmem_nsub(const TmemArgs &a, const TmemTab *tab, int grid, size_t smem, cudaStream_t stream) {
+    static bool attr = false;
+    if (!attr) {
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<false, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<true, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<false, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<true, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    if (tab && a.n_pix <= kTmTabPix && a.n_grp <= kTmTabGrp) {
+        if (a.skymap)
+            k_coherent_tmem_pt<true, NSUB><<<grid, kTmThreads, smem, stream>>>(a, *tab);
+        else
+            k_coherent_tmem_pt<false, NSUB><<<grid, kTmThreads, smem, stream>>>(a, *tab);
+    } else if (a.skymap) {
+        k_coherent_tmem<true, NSUB><<<grid, kTmThreads, smem, stream>>>(a);
+    } else {
+        k_coherent_tmem<false, NSUB><<<grid, kTmThreads, smem, stream>>>(a);
+    }
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
+}
+
+size_t tmem_scan_smem(int n_pix, int n_grp, int C, int nsub) {
+    const int W0 = kTmKT + nsub * C, L = W0 / 8 + 1;
     size_t s = (size_t)n_pix * sizeof(float4) + (size_t)n_grp * sizeof(int4) + (size_t)8 * kTmKT * sizeof(float) +
                (size_t)6 * 8 * L * sizeof(float) + ((size_t)n_pix * sizeof(uint16_t) + 15) / 16 * 16 + 16;
     return std::max(s, (size_t)kTmMinSmem);
@@ -349,36 +388,23 @@ size_t tmem_scan_smem(int n_pix, int n_grp, int C) {
 int tmem_columns(int H) { return (2 * H + kTmM + 15) / 16 * 16; }
 
 bool tmem_fits(int n_pix, int n_grp, int H) {
-    return 2 * tmem_columns(H) <= kTmDet && tmem_scan_smem(n_pix, n_grp, tmem_columns(H)) <= 227 * 1024;
+    // sized for four templates per work item (the largest staged tile)
+    return 2 * tmem_columns(H) <= kTmDet && tmem_scan_smem(n_pix, n_grp, tmem_columns(H), 4) <= 227 * 1024;
 }
 
 int launch_coherent_tmem(const TmemArgs &a, const TmemTab *tab, cudaStream_t stream) {
-    const size_t smem = tmem_scan_smem(a.n_pix, a.n_grp, a.C);
-    static bool attr = false;
-    if (!attr) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr = true;
-    }
+    if (a.nsub != 1 && a.nsub != 2 && a.nsub != 4) return fail(SPIIR_EINVAL, "templates per item = %d", a.nsub);
+    const size_t smem = tmem_scan_smem(a.n_pix, a.n_grp, a.C, a.nsub);
     int dev = 0, n_sm = 0;
     SPIIR_CUDA_TRY(cudaGetDevice(&dev));
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t items = (int64_t)a.n_templates * ((a.n + kTmKT - 1) / kTmKT);
+    const int64_t items = (int64_t)((a.n_templates + a.nsub - 1) / a.nsub) * ((a.n + kTmKT / a.nsub - 1) / (kTmKT / a.nsub));
     const int grid = (int)std::min<int64_t>(items, n_sm);
-    if (tab && a.n_pix <= kTmTabPix && a.n_grp <= kTmTabGrp) {
-        if (a.skymap)
-            k_coherent_tmem_pt<true><<<grid, kTmThreads, smem, stream>>>(a, *tab);
-        else
-            k_coherent_tmem_pt<false><<<grid, kTmThreads, smem, stream>>>(a, *tab);
-    } else if (a.skymap) {
-        k_coherent_tmem<true><<<grid, kTmThreads, smem, stream>>>(a);
-    } else {
-        k_coherent_tmem<false><<<grid, kTmThreads, smem, stream>>>(a);
+    switch (a.nsub) {
+        case 1: return launch_tmem_nsub<1>(a, tab, grid, smem, stream);
+        case 2: return launch_tmem_nsub<2>(a, tab, grid, smem, stream);
+        default: return launch_tmem_nsub<4>(a, tab, grid, smem, stream);
     }
-    SPIIR_CUDA_TRY(cudaGetLastError());
-    return SPIIR_OK;
 }
 
 }  // namespace spiir

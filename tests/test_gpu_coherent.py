@@ -267,13 +267,16 @@ def test_all_zero_window_ties_resolve_to_pixel_zero():
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
 
 
-@pytest.mark.parametrize("nside,T,n,param", [(8, 3, 2500, 1), (16, 2, 1024, 1), (16, 2, 3000, 1), (16, 2, 3000, 0)])
+@pytest.mark.parametrize("nside,T,n,param", [(8, 3, 2500, 1), (16, 2, 1024, 1), (16, 2, 3000, 1), (16, 2, 3000, 0),
+                                              (16, 3, 512, 1), (8, 5, 300, 1), (16, 3, 256, 1), (8, 7, 100, 0)])
 def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(nside, T, n, param):
     """The TMEM scan (512 threads, 8 samples per row, detector 1 and 2 windows in tensor
     memory) against the oracle, and against the shared-memory scan (the two pair the FP32
     arithmetic differently, so they agree to rounding).  n = 2500 and 3000 leave ragged last
-    tiles of 1024 samples.  param: group and offset tables in the kernel parameters (1) or in
-    shared memory (0), with bit-identical results."""
+    tiles of 1024 samples; chunks of at most 512 (256) samples put 2 (4) templates in one work
+    item, here with template counts that leave the last item partly empty.  param: group and
+    offset tables in the kernel parameters (1) or in shared memory (0), with bit-identical
+    results."""
     sky, G, d_or = _sky(1, 3, nside, (0.5, 2.0))
     H = sky.halo
     z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=21)
@@ -303,6 +306,19 @@ def test_tensor_memory_scan_ties_and_sky_map():
     # with a sky map (n = 2100: vector stores, a ragged last tile)
     ms2, am2, nl2, mp = _scan(sky, z, 2100, skymap=True)
     assert_coherent_close(ms2, am2, nl2, ms_or, am_or, nl_or, sm_or)
+    mp = np.transpose(mp, (0, 2, 1))
+    assert np.all(np.abs(mp - sm_or) <= 1e-4 * np.maximum(sm_or.max(axis=-1, keepdims=True), 1e-30))
+
+
+@pytest.mark.parametrize("n,T", [(200, 5), (512, 3)])
+def test_tensor_memory_sky_map_with_several_templates_per_item(n, T):
+    sky, G, d_or = _sky(1, 3, 8, (0.5, 2.0))
+    sky.set_scan_shape(512, 4, 1)
+    H = sky.halo
+    z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=60 + n)
+    ms, am, nl, mp = _scan(sky, z, n, skymap=True)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
     mp = np.transpose(mp, (0, 2, 1))
     assert np.all(np.abs(mp - sm_or) <= 1e-4 * np.maximum(sm_or.max(axis=-1, keepdims=True), 1e-30))
 
