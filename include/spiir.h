@@ -463,6 +463,11 @@ int spiir_pipeline_submit_host(spiir_pipeline_t pipe, const float *strain_host, 
                                float *null_stat_host, void *stream);
 /* Block until every submitted step's outputs are in its host buffers. */
 int spiir_pipeline_wait(spiir_pipeline_t pipe);
+/* The same with a host-side limit: SPIIR_OK once every submitted step is complete, or
+ * SPIIR_ETIMEOUT (nothing is cancelled; the steps keep running and a later wait collects them)
+ * when timeout_s seconds pass first, so that a caller can detect a stalled stream without
+ * blocking.  Errors: SPIIR_EINVAL, SPIIR_ETIMEOUT, SPIIR_ECUDA. */
+int spiir_pipeline_wait_for(spiir_pipeline_t pipe, double timeout_s);
 
 /* ------------------------------------------------------------------------------------
  * Batched multirate banks.  Several template banks of uneven size share one strain stream.

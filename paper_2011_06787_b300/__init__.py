@@ -267,6 +267,15 @@ class Pipeline:
     def wait(self):
         check(native.lib().spiir_pipeline_wait(self._h))
 
+    def wait_for(self, timeout_s: float) -> bool:
+        """True once every submitted step is complete; False if timeout_s passed first (the
+        steps keep running)."""
+        rc = native.lib().spiir_pipeline_wait_for(self._h, float(timeout_s))
+        if rc == native.ETIMEOUT:
+            return False
+        check(rc)
+        return True
+
 
 class Batch:
     """Batched multirate banks (spiir_batch_*).  banks: list of (offsets, a1, b0, delay, band)

@@ -16,6 +16,8 @@
 // launch, upsampling, coherent scan and history updates -- is captured once into a CUDA graph
 // and replayed per chunk.  Plain path: one bank per (bank, band) with its own launches, one
 // upsampling and one coherent launch per bank.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cmath>
@@ -586,6 +588,11 @@ extern "C" int spiir_batch_set_shape(spiir_batch_t B, int filters_per_lane, int 
 extern "C" int spiir_batch_run(spiir_batch_t B, int mode, const float *strain, float *ms, int32_t *am, float *nl,
                                void *stream) {
     clear_error();
+    // host-side range per chunk for profilers (a no-op without one)
+    struct Range {
+        Range() { nvtxRangePushA("spiir.batch_chunk"); }
+        ~Range() { nvtxRangePop(); }
+    } range;
     if (!B) return fail(SPIIR_EINVAL, "batch is NULL");
     if (!strain || !ms || !am || !nl) return fail(SPIIR_EINVAL, "NULL buffer");
     if (mode < 0 || mode > 2) return fail(SPIIR_EINVAL, "mode %d not in {0, 1, 2}", mode);

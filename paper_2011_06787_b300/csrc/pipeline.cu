@@ -2,7 +2,11 @@
 // history -> coherent scan.  Output sample j of a call is geocentric sample
 // (chunk start) + j - H, so that the SNR of every detector at k + Delta_I(p) is
 // available when the scan runs.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <chrono>
+#include <thread>
 
 #include "bank.cuh"
 #include "coherent.cuh"
@@ -54,12 +58,25 @@ static void pipe_free(spiir_pipeline_s *p) {
     delete p;
 }
 
+// Host-side NVTX range (a no-op unless a profiler is attached), closed at scope exit.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 static int pipe_run(spiir_pipeline_s *p, const float *strain, int64_t spitch, int64_t n, float *ms, int32_t *am,
                     float *nl, float *map, cudaStream_t s) {
+    NvtxRange chunk("spiir.chunk");
     const int T = p->bank->T, nd = p->bank->n_det, H = p->H;
     float2 *z = p->zpad[p->cur];
-    SPIIR_TRY(bank_filter(p->bank, strain, spitch, n, z + 2 * H, p->pitch, s));
-    SPIIR_TRY(coherent_scan(p->sky, z, p->pitch, T, n, ms, am, nl, map, s));
+    {
+        NvtxRange r("spiir.filter_bank");
+        SPIIR_TRY(bank_filter(p->bank, strain, spitch, n, z + 2 * H, p->pitch, s));
+    }
+    {
+        NvtxRange r("spiir.coherent_scan");
+        SPIIR_TRY(coherent_scan(p->sky, z, p->pitch, T, n, ms, am, nl, map, s));
+    }
     const int nxt = 1 - p->cur;
     if (H > 0)
         SPIIR_CUDA_TRY(cudaMemcpy2DAsync(p->zpad[nxt], p->pitch * sizeof(float2), z + n, p->pitch * sizeof(float2),
@@ -196,4 +213,23 @@ extern "C" int spiir_pipeline_wait(spiir_pipeline_t p) {
     if (!p) return fail(SPIIR_EINVAL, "pipeline is NULL");
     if (p->async_ready) SPIIR_CUDA_TRY(cudaStreamSynchronize(p->copy));
     return SPIIR_OK;
+}
+
+extern "C" int spiir_pipeline_wait_for(spiir_pipeline_t p, double timeout_s) {
+    clear_error();
+    if (!p) return fail(SPIIR_EINVAL, "pipeline is NULL");
+    if (!(timeout_s >= 0.0)) return fail(SPIIR_EINVAL, "timeout_s = %g", timeout_s);
+    if (!p->async_ready) return SPIIR_OK;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(p->copy);
+        if (e == cudaSuccess) return SPIIR_OK;
+        if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+            return fail(SPIIR_ECUDA, "cudaStreamQuery failed: %s", cudaGetErrorString(e));
+        }
+        if (std::chrono::steady_clock::now() >= deadline)
+            return fail(SPIIR_ETIMEOUT, "submitted steps not complete after %g s", timeout_s);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
 }

@@ -82,6 +82,7 @@ SIGNATURES = {
     "spiir_pipeline_run_host": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
     "spiir_pipeline_submit_host": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
     "spiir_pipeline_wait": (_I, [_P]),
+    "spiir_pipeline_wait_for": (_I, [_P, _D]),
 }
 
 _lib = None

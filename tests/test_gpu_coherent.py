@@ -170,6 +170,36 @@ def test_asynchronous_host_steps_match_synchronous_ones():
             np.testing.assert_array_equal(a, b)
 
 
+def test_timed_wait_reports_unfinished_steps_without_blocking():
+    """A host-side limit on collecting submitted steps: with several full online chunks queued,
+    a 1 ms limit returns before the work is done (the steps keep running), and an unlimited wait
+    then collects them; the outputs equal the synchronous path's."""
+    import time
+    import torch
+    import paper_2011_06787_b300 as sp
+    sky, _, _ = _sky(1, 3, 16, (0.5, 2.0))
+    sky.set_scan_shape(512, 4, 1)
+    bank = synth.online_bank()
+    chunks = [np.ascontiguousarray(synth.online_chunk(i)) for i in range(4)]
+    T, n = bank.n_templates, 2048
+    outs = [tuple(torch.empty((T, n), dtype=dt).pin_memory().numpy() for dt in (torch.float32, torch.int32, torch.float32))
+            for _ in chunks]
+    pipe = sp.Pipeline(sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay), sky, max_chunk=n)
+    assert pipe.wait_for(0.0)          # nothing submitted yet
+    for c, o in zip(chunks, outs):
+        pipe.submit_host(c, *o)
+    t0 = time.perf_counter()
+    assert not pipe.wait_for(1e-3)     # about 18 ms of GPU work is queued
+    assert time.perf_counter() - t0 < 0.5
+    assert pipe.wait_for(60.0)
+    ref = sp.Pipeline(sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay), sky, max_chunk=n)
+    for c, o in zip(chunks, outs):
+        r = tuple(np.empty_like(a) for a in o)
+        ref.run_host(c, *r)
+        for a, b in zip(o, r):
+            np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("shape", [(256, 1, 1), (256, 2, 1), (512, 1, 0), (512, 2, 0), (256, 2, 0), (512, 4, 1)])
 @pytest.mark.parametrize("n_det", [2, 3])
 def test_every_scan_shape_matches_oracle(shape, n_det):
