@@ -88,21 +88,22 @@ static int pipe_run(spiir_pipeline_s *p, const float *strain, int64_t spitch, in
 // Lazily created resources of the asynchronous host-buffer steps.
 static int async_init(spiir_pipeline_s *p) {
     if (p->async_ready) return SPIIR_OK;
+    // each resource is created once; a call that failed part-way resumes where it stopped
     const int T = p->bank->T, nd = p->bank->n_det;
     const int64_t m = p->max_chunk;
-    SPIIR_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking));
+    if (!p->copy) SPIIR_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking));
     for (int b = 0; b < 2; ++b) {
-        SPIIR_CUDA_TRY(cudaEventCreateWithFlags(&p->computed[b], cudaEventDisableTiming));
-        SPIIR_CUDA_TRY(cudaEventCreateWithFlags(&p->copied[b], cudaEventDisableTiming));
+        if (!p->computed[b]) SPIIR_CUDA_TRY(cudaEventCreateWithFlags(&p->computed[b], cudaEventDisableTiming));
+        if (!p->copied[b]) SPIIR_CUDA_TRY(cudaEventCreateWithFlags(&p->copied[b], cudaEventDisableTiming));
     }
     p->strain2[0] = p->strain_dev;
     p->ms2[0] = p->ms_dev;
     p->nl2[0] = p->nl_dev;
     p->am2[0] = p->am_dev;
-    SPIIR_TRY(dev_alloc((void **)&p->strain2[1], sizeof(float) * nd * m, "strain staging"));
-    SPIIR_TRY(dev_alloc((void **)&p->ms2[1], sizeof(float) * T * m, "max staging"));
-    SPIIR_TRY(dev_alloc((void **)&p->nl2[1], sizeof(float) * T * m, "null staging"));
-    SPIIR_TRY(dev_alloc((void **)&p->am2[1], sizeof(int32_t) * T * m, "argmax staging"));
+    if (!p->strain2[1]) SPIIR_TRY(dev_alloc((void **)&p->strain2[1], sizeof(float) * nd * m, "strain staging"));
+    if (!p->ms2[1]) SPIIR_TRY(dev_alloc((void **)&p->ms2[1], sizeof(float) * T * m, "max staging"));
+    if (!p->nl2[1]) SPIIR_TRY(dev_alloc((void **)&p->nl2[1], sizeof(float) * T * m, "null staging"));
+    if (!p->am2[1]) SPIIR_TRY(dev_alloc((void **)&p->am2[1], sizeof(int32_t) * T * m, "argmax staging"));
     p->async_ready = true;
     return SPIIR_OK;
 }

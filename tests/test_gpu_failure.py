@@ -100,3 +100,47 @@ def test_injected_allocation_failures_fail_the_create_calls_cleanly():
         L.spiir_debug_fail_allocs(0)
     _tiny_filter_check()
     sp.device_status()
+
+
+def test_injected_failures_in_the_first_asynchronous_step_are_resumable():
+    """The second staging set of the asynchronous host-buffer steps is allocated on the first
+    submission: failing each of its allocations in turn makes that call fail with SPIIR_ENOMEM,
+    and the next call resumes the setup and processes the chunk as the synchronous call does."""
+    import torch
+    import paper_2011_06787_b300 as sp
+    from paper_2011_06787_b300 import native
+    L = native.lib()
+    w = synth.tiny_workload()
+    bank, det = w["bank"], w["det"]
+    sky = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, w["sigma"], 4, 2048.0))
+    x = np.ascontiguousarray(w["strain"][:, :1024])
+    T = bank.n_templates
+    pin = lambda dt: torch.empty((T, 1024), dtype=dt).pin_memory().numpy()
+    pipe = sp.Pipeline(sp.Bank(2, bank.offsets, bank.a1, bank.b0, bank.delay), sky, max_chunk=1024)
+    out = (pin(torch.float32), pin(torch.int32), pin(torch.float32))
+    try:
+        # each call makes only the allocations still missing: failing the first allocation of
+        # the first call, then the second of the next three, walks the four staging allocations
+        # (each call completes one more of them before the injected failure)
+        for k, site in zip((1, 2, 2, 2), ("strain", "max", "null", "argmax")):
+            L.spiir_debug_fail_alloc_at(k)
+            with pytest.raises(sp.SpiirError) as e:
+                pipe.submit_host(x, *out)
+            assert e.value.code == native.ENOMEM
+            assert f"for {site} staging" in str(e.value), str(e.value)
+        # the four failures hit strain, max, null and argmax staging in that order; without an
+        # injected failure the fifth call completes the setup (the argmax staging) and runs
+        L.spiir_debug_fail_alloc_at(0)
+        pipe.submit_host(x, *out)
+        pipe.wait()
+    finally:
+        L.spiir_debug_fail_alloc_at(0)
+    pipe.reset()
+    pipe.submit_host(x, *out)
+    pipe.wait()
+    ref = sp.Pipeline(sp.Bank(2, bank.offsets, bank.a1, bank.b0, bank.delay), sky, max_chunk=1024)
+    r = (pin(torch.float32), pin(torch.int32), pin(torch.float32))
+    ref.run_host(x, *r)
+    for a, b in zip(out, r):
+        np.testing.assert_array_equal(a, b)
+    sp.device_status()
