@@ -548,6 +548,22 @@ def test_network_average_reads_each_detector_at_its_arrival_time():
             assert out[t, k] == expect
 
 
+def test_network_xi2_of_linear_per_detector_values():
+    """With xi_I^2 at sample x equal to I + x / 1000, the network value at sample k and pixel p
+    is the mean over detectors of I + (k + Delta_I(p)) / 1000: a closed form that fails for a
+    wrong halo offset, a wrong delay sign or detector, or a wrong divisor."""
+    g = _rng(33)
+    T, n_det, n, H, P = 2, 3, 50, 7, 11
+    delays = g.integers(-H, H + 1, (P, n_det))
+    x = np.arange(n + 2 * H) - H
+    xi = np.stack([np.stack([I + x / 1000.0 for I in range(n_det)]) for _ in range(T)])
+    am = g.integers(0, P, (T, n))
+    got = oracle.xi2_network(xi, delays, am, H)
+    k = np.arange(n)
+    want = np.mean([[I + (k + delays[am[t], I]) / 1000.0 for I in range(n_det)] for t in range(T)], axis=1)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
 # ---------------------------------------------------------------------------------------------
 # Candidate selection and the candidate-driven scan (Sec. II.C.1), time-shift background
 # (Sec. II.C.3)
