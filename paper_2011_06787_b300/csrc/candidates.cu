@@ -18,11 +18,17 @@
 // Candidate-driven scan.  A candidate (detector r, template t, sample k) is evaluated at every
 // pixel p with detector r read at its own sample and each other detector J at
 // k + Delta_J(p) - Delta_r(p) + shift_J, shift_J = -s c_J step for time shift s (c_J = 1, 2, ...
-// the companions of r in detector order; s = 0 is the foreground).  One block per
-// (candidate, shift) item in a persistent grid: it stages each detector's window of the SNR
-// (the range of Delta_J - Delta_r over the sky) in shared memory, its threads loop over pixels
-// with the arithmetic of the all-sky scan, and a block reduction keeps the largest statistic
-// (the lowest pixel among equals) and the null stream at that pixel.
+// the companions of r in detector order; s = 0 is the foreground).
+//   k_points_chunked (skies whose windows fit 192 samples): one block per (candidate, chunk of
+//              16 shifts, or 1 at zero lag, 8 for four detectors) in a persistent grid.  The
+//              companions' windows of the chunk's shifts sit in shared memory, and the next
+//              item's windows are copied (cp.async) while the current one is evaluated; the
+//              reference detector's term is formed once per pixel; the lanes keep a maximum per
+//              shift and a butterfly of shuffles plus a shared-memory pass reduce them.
+//   k_points:  the general form, one block per (candidate, shift), for wide windows or large
+//              tables.
+// Both keep the largest statistic (the lowest pixel among equals) and the null stream at that
+// pixel, with the arithmetic of the all-sky scan.
 #include <algorithm>
 #include <climits>
 #include <cmath>

@@ -18,7 +18,9 @@
 // warp-uniform column address serves all 32 rows of a warp for any pixel, and every sample is
 // one aligned two-column load that lands as an FP32 pair.
 //
-// Work item: one template and 1024 output samples.  Block: 512 threads = 16 warps, one block
+// Work item: one template and 1024 output samples (for chunks of at most 512 or 256 samples,
+// 2 or 4 templates whose thread rows split the 128 lanes, each with its own segment of the
+// staged tile).  Block: 512 threads = 16 warps, one block
 // per SM (shared memory above half the SM's capacity keeps a second block off the SM, so the
 // 512-column TMEM allocation never waits).  Warp w reads TMEM lanes 32 (w % 4) .. + 31 (the
 // quarter its hardware position allows) and evaluates pixel slice w / 4: the sorted pixel
