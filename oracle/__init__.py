@@ -20,8 +20,8 @@ Contents, each a plain restatement of the paper in double precision:
 * ``impulse_forward`` / ``impulse_backward``  bank impulse response and its adjoint
 * ``overlap_loss``       1 - O with O from Sec. II.B.1 Eq. (overlap) (modulus reading)
 * ``fir_taps`` / ``decimate`` / ``upsample_linear`` / ``multirate_bank``
-                         multirate split of the bank (not in the paper; definition in
-                         the design notes, "parity unpinned" by the paper)
+                         multirate split of the bank (not in the paper; its definition is
+                         stated in the docstrings below)
 * ``autocorr`` / ``xi2`` / ``xi2_network``  Sec. II.C.2: template autocorrelation, xi_I^2 per
                          sample, network average at the coherent argmax
 * ``select_candidates`` / ``coherent_points`` / ``background_shifts``  Sec. II.C.1 and II.C.3:
@@ -29,10 +29,11 @@ Contents, each a plain restatement of the paper in double precision:
 * ``lowpass_taps`` / ``whitening_kernel`` / ``fir`` / ``frontend``  Sec. II.A: 16384 -> 2048 Hz
                          FIR down-sampling and whitening (Eq. (whiten)) as a time-domain FIR
 
-Functions with no pin beyond their own definition: the multirate split
-(``fir_taps``, ``decimate``, ``upsample_linear``, ``multirate_bank``) is parity
-unpinned by the paper; it is pinned only by identities (M = 1 is the identity,
-unit DC gain, exact reproduction of ramps).
+The multirate split (``fir_taps``, ``decimate``, ``upsample_linear``, ``multirate_bank``) is
+defined here, not by the paper.  Its pins are the library routines each step reduces to
+(scipy ``firwin`` and the Hann window for the taps, ``upfirdn`` for the decimation, numpy
+``interp`` for the upsampling, ``lfilter`` for the one-pole filters of a band) and identities
+(M = 1 is the identity, unit DC gain, exact reproduction of ramps).
 """
 from __future__ import annotations
 

@@ -415,7 +415,7 @@ def test_adjoint_matches_fp64_finite_differences():
 
 
 # ---------------------------------------------------------------------------------------------
-# Multirate split (not in the paper; pinned by identities only)
+# Multirate split (not in the paper): identities, and the library routines each step reduces to
 
 
 def test_fir_has_unit_dc_gain_and_attenuates_above_cutoff():
@@ -452,6 +452,80 @@ def test_linear_upsample_reproduces_ramp_with_one_sample_lag():
     k = np.arange(40)
     np.testing.assert_allclose(z[0, M:], (k[M:] / M - 1) * (1 + 0.5j), rtol=1e-14)
     assert last[0] == zb[0, -1]
+
+
+def _hann_half_sample(n):
+    # the window sampled at i + 1/2: the odd samples of the periodic Hann window of length 2n
+    import scipy.signal as ss
+    return ss.windows.hann(2 * n, sym=False)[1::2]
+
+
+def test_fir_taps_equal_scipy_sinc_times_half_sample_hann():
+    import scipy.signal as ss
+    for M in (2, 4, 16):
+        # firwin with a boxcar window and no scaling is the ideal low-pass 2 fc sinc(2 fc (i - c))
+        box = ss.firwin(32, 0.8 / M, window="boxcar", scale=False)
+        ref = box * _hann_half_sample(32)
+        np.testing.assert_allclose(oracle.fir_taps(M), ref / ref.sum(), rtol=0, atol=1e-15)
+
+
+def test_decimate_equals_scipy_upfirdn():
+    import scipy.signal as ss
+    g = _rng(41)
+    x = g.standard_normal((2, 768))
+    for M, taps in ((4, None), (16, None), (3, g.standard_normal(7))):
+        h = oracle.fir_taps(M) if taps is None else taps
+        y, _ = oracle.decimate(x, M, taps)
+        ref = ss.upfirdn(h, x, up=1, down=M, axis=-1)[:, : 768 // M]
+        np.testing.assert_allclose(y, ref, rtol=0, atol=1e-13)
+
+
+def test_linear_upsample_equals_numpy_interp():
+    g = _rng(42)
+    for M in (2, 4, 16):
+        zb = g.standard_normal((3, 12)) + 1j * g.standard_normal((3, 12))
+        prev = g.standard_normal(3) + 1j * g.standard_normal(3)
+        z, last = oracle.upsample_linear(zb, M, prev=prev)
+        k = np.arange(12 * M)
+        for r in range(3):
+            # output k sits at low-rate position k / M - 1 (one low-rate sample of lag), prev at -1
+            fp = np.concatenate([[prev[r]], zb[r]])
+            xp = np.arange(-1, 12)
+            ref = np.interp(k / M - 1, xp, fp.real) + 1j * np.interp(k / M - 1, xp, fp.imag)
+            np.testing.assert_allclose(z[r], ref, rtol=0, atol=1e-14)
+        np.testing.assert_array_equal(last, zb[:, -1])
+
+
+def test_multirate_bank_equals_upfirdn_lfilter_interp_per_filter():
+    # z_t = sum over the template's filters of: decimate (upfirdn), one-pole IIR on the delayed
+    # low-rate input (lfilter), linear upsampling (interp); the bank is linear in its filters
+    import scipy.signal as ss
+    g = _rng(43)
+    n_det, n, factors = 2, 1024, (1, 4, 16)
+    x = g.standard_normal((n_det, n))
+    offsets = np.array([0, 5, 12])
+    F = offsets[-1]
+    a1 = g.uniform(0.6, 0.98, F) * np.exp(1j * g.uniform(-2.5, 2.5, F))
+    b0 = (g.standard_normal(F) + 1j * g.standard_normal(F)) / np.sqrt(2 * F)
+    band = g.integers(0, 3, F)
+    delay = np.array([g.integers(0, 40 if factors[b] == 1 else 10) for b in band])
+    z = oracle.multirate_bank(x, offsets, a1, b0, delay, band, factors)
+    ref = np.zeros((2, n_det, n), dtype=np.complex128)
+    for t in range(2):
+        for l in range(offsets[t], offsets[t + 1]):
+            M = factors[band[l]]
+            for I in range(n_det):
+                xb = x[I] if M == 1 else ss.upfirdn(oracle.fir_taps(M), x[I], down=M)[: n // M]
+                xd = np.concatenate([np.zeros(delay[l]), xb])[: xb.size]
+                yb = ss.lfilter([b0[l]], [1.0, -a1[l]], xd.astype(np.complex128))
+                if M == 1:
+                    ref[t, I] += yb
+                else:
+                    k = np.arange(n)
+                    fp = np.concatenate([[0.0], yb])
+                    xp = np.arange(-1, yb.size)
+                    ref[t, I] += np.interp(k / M - 1, xp, fp.real) + 1j * np.interp(k / M - 1, xp, fp.imag)
+    np.testing.assert_allclose(z, ref, rtol=0, atol=1e-11)
 
 
 # ---------------------------------------------------------------------------------------------
