@@ -34,6 +34,20 @@ namespace spiir {
 // Shared-memory layout of one block: the mbarrier at offset 0, the strain window at
 // kBankSmemHead, the reduction buffer at a.red_offset.
 
+// Pairwise sum of N packed pairs (N a power of two).
+template <int N>
+__device__ __forceinline__ u64 tree_sum2(const u64 (&v)[N]) {
+    u64 w[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[i] = v[i];
+#pragma unroll
+    for (int h = N / 2; h >= 1; h /= 2) {
+#pragma unroll
+        for (int i = 0; i < h; ++i) w[i] = add2(w[i], w[i + h]);
+    }
+    return w[0];
+}
+
 // One block's work: template block `cta` of bank `a` for detector `det` over the whole call.
 // Returns false when a bounded wait ran out (every thread of the block returns false).
 template <int S, int NL, int R>
@@ -128,7 +142,6 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                 for (int s = 0; s < S; ++s) xp[s] = xw + dof[s] + kb;
                 float2 *rrow = red + tid * (R + 1);
                 auto step = [&](int r) {
-                    u64 accr = 0, acci = 0;
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         const u64 X = pack2(xp[2 * p][r], xp[2 * p + 1][r]);
@@ -138,15 +151,10 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                         const u64 ni_ = fma2(aim[p], yre[p], u);        // + a.im y.re
                         yre[p] = nr_;
                         yim[p] = ni_;
-                        if (p == 0) {
-                            accr = nr_;
-                            acci = ni_;
-                        } else {
-                            accr = add2(accr, nr_);
-                            acci = add2(acci, ni_);
-                        }
                     }
-                    const float2 ar = unpack2(accr), ai = unpack2(acci);
+                    // the lane's sum over its S filters as a pairwise tree (shorter dependency
+                    // chains than a running sum)
+                    const float2 ar = unpack2(tree_sum2<NP>(yre)), ai = unpack2(tree_sum2<NP>(yim));
                     rrow[r] = make_float2(ar.x + ar.y, ai.x + ai.y);
                 };
                 if (nr == R) {
