@@ -204,14 +204,17 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
             }
         }
         __syncthreads();
+        // per sample: the maximum, the first group attaining it, the second one (tie bit set),
+        // and whether a third one does (multi bit set)
         float best[NQ];
-        int bg[NQ];
+        int bg[NQ], bg2[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             best[q] = -INFINITY;
             bg[q] = 0;
+            bg2[q] = 0;
         }
-        unsigned tie = 0;
+        unsigned tie = 0, multi = 0;
         for (int g = 0; g < G; ++g) {
             const int4 gr = grp[g];
             u64 w0r[PPT], w0i[PPT], s0[PPT];
@@ -309,7 +312,10 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
                     best[q] = gm[q];
                     bg[q] = g;
                     tie &= ~(1u << q);
+                    multi &= ~(1u << q);
                 } else if (gm[q] == best[q]) {
+                    if (tie >> q & 1u) multi |= 1u << q;
+                    bg2[q] = g;
                     tie |= 1u << q;
                 }
             }
@@ -320,10 +326,11 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
             if (k0 + k >= a.n) continue;
             int arg = 0x7fffffff;
             float nul = 0.f;
-            int g_lo = bg[q], g_hi = bg[q] + 1;
+            int g_lo = bg[q], g_hi = bg[q] + 1, g_two = -1;
             if (tie >> q & 1u) {
                 // equal maxima in different groups: pixel 0, the lowest index, wins if it
-                // attains the maximum (the all-zero window); otherwise rescan every group
+                // attains the maximum (the all-zero window); otherwise the two groups that attain
+                // it are rescanned, or every group when a third one does too
                 const float4 e = ent[a.q0];
                 const unsigned o = __float_as_uint(e.w);
                 float v, tt;
@@ -332,12 +339,15 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
                     arg = 0;
                     nul = tt;
                     g_hi = g_lo;
-                } else {
+                } else if (multi >> q & 1u) {
                     g_lo = 0;
                     g_hi = G;
+                } else {
+                    g_two = bg2[q];
                 }
             }
-            for (int g = g_lo; g < g_hi; ++g) {
+            for (int gi = g_lo; gi < g_hi + (g_two >= 0); ++gi) {
+                const int g = gi < g_hi ? gi : g_two;
                 const int4 gr = grp[g];
                 for (int p = gr.y; p < gr.z; ++p) {
                     const float4 e = ent[p];

@@ -130,6 +130,10 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
     off += (size_t)6 * PL * sizeof(float);
     uint16_t *orig = reinterpret_cast<uint16_t *>(smem + off);
     off += ((size_t)P * sizeof(uint16_t) + 15) / 16 * 16;
+    int *tie_slots = reinterpret_cast<int *>(smem + off);  // slots left to pass 2 of the merge
+    off += (size_t)kTmKT * sizeof(int);
+    int *n_tie = reinterpret_cast<int *>(smem + off);
+    off += 16;
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem + off);
 
     for (int i = tid; i < P; i += kTmThreads) {
@@ -161,6 +165,7 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
+        if (tid == 0) *n_tie = 0;  // read again only after the barrier that ends the staging
         for (int I = 0; I < 3; ++I) {
             float *re = zp + (2 * I) * PL, *im = re + PL;
             for (int x = tid; x < W0; x += kTmThreads) {
@@ -263,15 +268,56 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         }
         __syncthreads();
         // merge the slices and resolve the argmax (lowest original pixel index among equal maxima)
-        for (int j = tid; j < kTmKT; j += kTmThreads) {
-            // slot j = 8 row + m: template t0 + row / RPT, its sample k0 + 8 (row % RPT) + m, tile
-            // position xj
+        // slot j = 8 row + m: template t0 + row / RPT, its sample k0 + 8 (row % RPT) + m, tile
+        // position xj; it sits at [m][row] of the slice maxima
+        auto slot_of = [&](int j, int &jk, int &xj, int &tj, int &cj) {
             const int jr = j >> 3, js = jr / RPT;
-            const int jk = kTmM * (jr - js * RPT) + (j & 7);
-            const int xj = js * SEG + jk;
-            const int tj = t0 + js;
+            jk = kTmM * (jr - js * RPT) + (j & 7);
+            xj = js * SEG + jk;
+            tj = t0 + js;
+            cj = (j & 7) * kTmRows + jr;
+        };
+        // the statistic of sorted pixel p (detector-0 offset d0) at tile position xj, recomputed
+        // in scalar arithmetic, and its null stream
+        auto stat = [&](int p, int d0, int xj, float &v, float &tt) {
+            const float4 e = ent[p];
+            const uint32_t o = __float_as_uint(e.w);
+            const int d1 = (int)(o & 0xFFFFu), d2 = (int)(o >> 16);
+            const float *r0 = zp, *r1 = zp + 2 * PL, *r2 = zp + 4 * PL;
+            const float w0r = r0[tpos(xj + d0, L)], w0i = r0[PL + tpos(xj + d0, L)];
+            const float w1r = r1[tpos(xj + d1, L)], w1i = r1[PL + tpos(xj + d1, L)];
+            const float w2r = r2[tpos(xj + d2, L)], w2i = r2[PL + tpos(xj + d2, L)];
+            const float Ar = __fmaf_rn(w2r, w2r, __fmaf_rn(w1r, w1r, __fmul_rn(w0r, w0r)));
+            const float Ai = __fmaf_rn(w2i, w2i, __fmaf_rn(w1i, w1i, __fmul_rn(w0i, w0i)));
+            const float nr = __fmaf_rn(e.z, w2r, __fmaf_rn(e.y, w1r, __fmul_rn(e.x, w0r)));
+            const float ni = __fmaf_rn(e.z, w2i, __fmaf_rn(e.y, w1i, __fmul_rn(e.x, w0i)));
+            tt = __fmaf_rn(ni, ni, __fmul_rn(nr, nr));
+            v = __fadd_rn(__fsub_rn(Ar, __fmul_rn(nr, nr)), __fsub_rn(Ai, __fmul_rn(ni, ni)));
+        };
+        // the candidate pixel with the largest recomputed statistic, lowest index among equals
+        // (the compiler may contract the packed multiply-subtract of the main loop, so its value
+        // and the recomputed one can differ in the last bit)
+        auto take = [&](float v, int op, float tt, float &bv, int &arg, float &nul) {
+            if (v > bv || (v == bv && op < arg)) {
+                bv = v;
+                arg = op;
+                nul = tt;
+            }
+        };
+        auto store = [&](int tj, int jk, float B, int arg, float nul) {
+            if (arg == 0x7fffffff) arg = 0;  // only when every statistic is NaN
+            const int64_t o = (int64_t)tj * a.n + k0 + jk;
+            a.max_stat[o] = B;
+            a.argmax[o] = arg;
+            a.null_stat[o] = nul;
+        };
+        // pass 1, one thread per slot: a maximum attained by one group is resolved by rescanning
+        // that group; one attained by several groups either by pixel 0 (the all-zero window) or,
+        // else, by pass 2
+        for (int j = tid; j < kTmKT; j += kTmThreads) {
+            int jk, xj, tj, cj;
+            slot_of(j, jk, xj, tj, cj);
             if (tj >= a.n_templates || k0 + jk >= a.n) continue;
-            const int cj = (j & 7) * kTmRows + jr;  // slot j sits at [m][row]
             float B = cb_best[cj];
             for (int s = 1; s < 4; ++s) B = fmaxf(B, cb_best[s * kTmKT + cj]);
             int hits = 0;
@@ -283,60 +329,54 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                     tie |= cb_grp[s * kTmKT + cj] >> 31;
                 }
             }
-            int lo = (int)gsel, hi = (int)gsel + 1;
             int arg = 0x7fffffff;
-            float nul = 0.f;
-            auto stat = [&](int p, int d0, float &v, float &tt) {
-                const float4 e = ent[p];
-                const uint32_t o = __float_as_uint(e.w);
-                const int d1 = (int)(o & 0xFFFFu), d2 = (int)(o >> 16);
-                const float *r0 = zp, *r1 = zp + 2 * PL, *r2 = zp + 4 * PL;
-                const float w0r = r0[tpos(xj + d0, L)], w0i = r0[PL + tpos(xj + d0, L)];
-                const float w1r = r1[tpos(xj + d1, L)], w1i = r1[PL + tpos(xj + d1, L)];
-                const float w2r = r2[tpos(xj + d2, L)], w2i = r2[PL + tpos(xj + d2, L)];
-                const float Ar = __fmaf_rn(w2r, w2r, __fmaf_rn(w1r, w1r, __fmul_rn(w0r, w0r)));
-                const float Ai = __fmaf_rn(w2i, w2i, __fmaf_rn(w1i, w1i, __fmul_rn(w0i, w0i)));
-                const float nr = __fmaf_rn(e.z, w2r, __fmaf_rn(e.y, w1r, __fmul_rn(e.x, w0r)));
-                const float ni = __fmaf_rn(e.z, w2i, __fmaf_rn(e.y, w1i, __fmul_rn(e.x, w0i)));
-                tt = __fmaf_rn(ni, ni, __fmul_rn(nr, nr));
-                v = __fadd_rn(__fsub_rn(Ar, __fmul_rn(nr, nr)), __fsub_rn(Ai, __fmul_rn(ni, ni)));
-            };
+            float nul = 0.f, bv = -INFINITY;
             if (hits > 1 || tie) {
-                // equal maxima in several groups: pixel 0, the lowest index, wins if it attains
-                // the maximum (the all-zero window); otherwise every group is rescanned
                 float v, tt;
-                stat(a.q0, H + grp[a.g0].w, v, tt);
+                stat(a.q0, H + grp[a.g0].w, xj, v, tt);
                 if (v == B) {
-                    arg = 0;
-                    nul = tt;
-                    hi = lo;
+                    store(tj, jk, B, 0, tt);
                 } else {
-                    lo = 0;
-                    hi = G;
+                    tie_slots[atomicAdd(n_tie, 1)] = j;
                 }
+                continue;
             }
-            // the candidate pixel with the largest recomputed statistic, lowest index among
-            // equals (the compiler may contract the packed multiply-subtract of the main loop,
-            // so its value and the recomputed one can differ in the last bit)
-            float bv = -INFINITY;
-            for (int g = lo; g < hi; ++g) {
+            const int4 gr = grp[gsel];
+            for (int p = gr.y; p < gr.z; ++p) {
+                float v, tt;
+                stat(p, H + gr.w, xj, v, tt);
+                take(v, orig[p], tt, bv, arg, nul);
+            }
+            store(tj, jk, B, arg, nul);
+        }
+        __syncthreads();
+        // pass 2, one warp per slot whose maximum several groups attain (exact FP32 ties between
+        // the top pixels occur about once per million samples): the lanes share the groups, and
+        // a butterfly combines their best pixels under the same rule
+        for (int e = warp; e < *n_tie; e += kTmThreads / 32) {
+            const int j = tie_slots[e];
+            int jk, xj, tj, cj;
+            slot_of(j, jk, xj, tj, cj);
+            float B = cb_best[cj];
+            for (int s = 1; s < 4; ++s) B = fmaxf(B, cb_best[s * kTmKT + cj]);
+            int arg = 0x7fffffff;
+            float nul = 0.f, bv = -INFINITY;
+            for (int g = lane; g < G; g += 32) {
                 const int4 gr = grp[g];
                 for (int p = gr.y; p < gr.z; ++p) {
                     float v, tt;
-                    stat(p, H + gr.w, v, tt);
-                    const int op = orig[p];
-                    if (v > bv || (v == bv && op < arg)) {
-                        bv = v;
-                        arg = op;
-                        nul = tt;
-                    }
+                    stat(p, H + gr.w, xj, v, tt);
+                    take(v, orig[p], tt, bv, arg, nul);
                 }
             }
-            if (arg == 0x7fffffff) arg = 0;  // only when every statistic is NaN
-            const int64_t o = (int64_t)tj * a.n + k0 + jk;
-            a.max_stat[o] = B;
-            a.argmax[o] = arg;
-            a.null_stat[o] = nul;
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, bv, m);
+                const int oa = __shfl_xor_sync(0xffffffffu, arg, m);
+                const float on = __shfl_xor_sync(0xffffffffu, nul, m);
+                take(ov, oa, on, bv, arg, nul);
+            }
+            if (lane == 0) store(tj, jk, B, arg, nul);
         }
     }
     tm_fence_before();
@@ -383,7 +423,8 @@ static int launch_tmem_nsub(const TmemArgs &a, const TmemTab *tab, int grid, siz
 size_t tmem_scan_smem(int n_pix, int n_grp, int C, int nsub) {
     const int W0 = kTmKT + nsub * C, L = W0 / 8 + 1;
     size_t s = (size_t)n_pix * sizeof(float4) + (size_t)n_grp * sizeof(int4) + (size_t)8 * kTmKT * sizeof(float) +
-               (size_t)6 * 8 * L * sizeof(float) + ((size_t)n_pix * sizeof(uint16_t) + 15) / 16 * 16 + 16;
+               (size_t)6 * 8 * L * sizeof(float) + ((size_t)n_pix * sizeof(uint16_t) + 15) / 16 * 16 +
+               (size_t)kTmKT * sizeof(int) + 16 + 16;
     return std::max(s, (size_t)kTmMinSmem);
 }
 

@@ -94,6 +94,41 @@ def test_argmax_ties_take_lowest_pixel():
     assert np.all(am == 0) and np.allclose(ms, 2.0) and np.allclose(nl, 1.0)
 
 
+@pytest.mark.parametrize("copies", [2, 3])
+@pytest.mark.parametrize("shape", [(512, 4, 1), (512, 4, 0), (256, 2, 1), (256, 2, 0)])
+def test_exact_ties_across_groups_take_lowest_pixel(copies, shape):
+    """Every pixel of the first third (half) has copies whose detector-0 delay is 1 or 2
+    samples later, so they sit in other detector-0 groups.  Detector 0 is silent, so each pixel
+    and its copies have bit-identical statistics: every sample's maximum is attained in 2 (3)
+    groups, and the lowest original index, the original pixel, must win."""
+    import paper_2011_06787_b300 as sp
+    det = synth.detectors(1, 3)
+    sigma = synth.noise_weights(1, 3, 0.5, 2.0)
+    d, us, un = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 8, 2048.0)
+    _, G, d_or = oracle.sky_geometry(det, sigma, 8, 2048.0)
+    m = d.shape[0] // copies
+    idx = np.concatenate([np.arange(m)] * copies)
+    shift = np.repeat(np.arange(copies), m).astype(np.int32)
+    d2, d2_or = d[idx].copy(), d_or[idx].copy()
+    d2[:, 0] += shift
+    d2_or[:, 0] += shift
+    sky = sp.Sky(d2, us[idx], un[idx])
+    sky.set_scan_shape(*shape)
+    assert sky.get_scan_shape()[:3] == shape
+    H, n, T = sky.halo, 1300, 2
+    z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=71).astype(np.complex64)
+    z[:, 0, :] = 0
+    ms, am, nl, _ = _scan(sky, z, n)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G[idx], d2_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    assert np.all(am < m)
+    # where the best original pixel leads the next distinct one clearly, it is the oracle's
+    top = np.sort(sm_or[:, :, :m], axis=-1)
+    clear = top[..., -1] - top[..., -2] > 1e-4 * top[..., -1]
+    assert clear.mean() > 0.5
+    np.testing.assert_array_equal(am[clear], am_or[clear])
+
+
 def _pipeline_stream(bank, sky, strain, chunk, host=False):
     import torch
     import paper_2011_06787_b300 as sp
