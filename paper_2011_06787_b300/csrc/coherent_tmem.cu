@@ -351,8 +351,9 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         }
         __syncthreads();
         // pass 2, one warp per slot whose maximum several groups attain (exact FP32 ties between
-        // the top pixels occur about once per million samples): the lanes share the groups, and
-        // a butterfly combines their best pixels under the same rule
+        // the top pixels of two groups, of the order of once per few million samples of noise):
+        // the lanes share the groups, and a butterfly combines their best pixels under the same
+        // rule
         for (int e = warp; e < *n_tie; e += kTmThreads / 32) {
             const int j = tie_slots[e];
             int jk, xj, tj, cj;
