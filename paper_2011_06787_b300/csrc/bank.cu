@@ -171,26 +171,28 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
             // Only rows written by the same warp are read, so a warp barrier suffices.
             // With R < 32 some lanes have no column; with R = 64 each lane has two.
             // Lane c owns columns c, c + 32, ... below R.
+            // The (re, im) partial sums are added as packed pairs, rows in order (the same
+            // rounding as two scalar additions).
+            u64 *red2 = reinterpret_cast<u64 *>(red);
             for (int col = lane; busy && wfirst >= 0 && col < R; col += 32) {
+                u64 *colp = red2 + (warp * 32) * (R + 1) + col;
                 int j = 0;
                 for (int sg = wfirst; sg < nseg; ++sg) {
                     const int4 g = a.segs[seg0 + sg];
                     const int lo = max(g.y, warp * 32) - warp * 32;
                     const int hi = min(g.z, warp * 32 + 32) - warp * 32;
                     if (hi <= lo) break;
-                    float2 acc = make_float2(0.f, 0.f);
 #ifdef SPIIR_CHECKED
                     if ((warp * 32 + hi - 1) * (R + 1) + col >= NL * (R + 1)) {
                         report_bounds(a.status, 8);
                         break;
                     }
 #endif
-                    for (int i = lo; i < hi; ++i) {
-                        const float2 v = red[(warp * 32 + i) * (R + 1) + col];
-                        acc.x += v.x;
-                        acc.y += v.y;
-                    }
-                    red[(warp * 32 + j) * (R + 1) + col] = acc;
+                    u64 acc = 0;  // (+0, +0)
+                    const u64 *rp = colp + lo * (R + 1);
+#pragma unroll 8
+                    for (int i = lo; i < hi; ++i, rp += R + 1) acc = add2(acc, *rp);
+                    colp[j * (R + 1)] = acc;
                     ++j;
                 }
             }
@@ -200,12 +202,9 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                 const int sg = o / R, r = o % R;
                 if (r >= nr) continue;
                 const int4 g = a.segs[seg0 + sg];
-                float2 acc = make_float2(0.f, 0.f);
-                for (int w = g.y >> 5; w <= (g.z - 1) >> 5; ++w) {
-                    const float2 v = red[(w * 32 + (sg - a.wfirst[cta * NW + w])) * (R + 1) + r];
-                    acc.x += v.x;
-                    acc.y += v.y;
-                }
+                u64 acc = 0;
+                for (int w = g.y >> 5; w <= (g.z - 1) >> 5; ++w)
+                    acc = add2(acc, red2[(w * 32 + (sg - a.wfirst[cta * NW + w])) * (R + 1) + r]);
                 float2 *zrow = a.z + ((int64_t)g.x * a.n_det + det) * a.zpitch;
 #ifdef SPIIR_CHECKED
                 if (((int64_t)g.x * a.n_det + det) * a.zpitch + k0 + kb + r >= a.z_elems) {
@@ -213,7 +212,7 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                     continue;
                 }
 #endif
-                zrow[k0 + kb + r] = acc;
+                zrow[k0 + kb + r] = unpack2(acc);
             }
             __syncthreads();
         }
