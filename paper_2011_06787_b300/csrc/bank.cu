@@ -48,6 +48,10 @@ __device__ __forceinline__ u64 tree_sum2(const u64 (&v)[N]) {
     return w[0];
 }
 
+// Row stride (float2 entries) of the per-step sums in the reduction buffer: R + 2, even, so
+// that the sums of steps 2i and 2i + 1 of a row form one aligned 16-byte store.
+__host__ __device__ constexpr int bank_red_stride(int R) { return R + 2; }
+
 // One block's work: template block `cta` of bank `a` for detector `det` over the whole call.
 // Returns false when a bounded wait ran out (every thread of the block returns false).
 template <int S, int NL, int R>
@@ -140,8 +144,9 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                 const float *xp[S];
 #pragma unroll
                 for (int s = 0; s < S; ++s) xp[s] = xw + dof[s] + kb;
-                float2 *rrow = red + tid * (R + 1);
-                auto step = [&](int r) {
+                constexpr int RS = bank_red_stride(R);
+                float2 *rrow = red + tid * RS;
+                auto step = [&](int r) -> float2 {
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         const u64 X = pack2(xp[2 * p][r], xp[2 * p + 1][r]);
@@ -155,14 +160,17 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                     // the lane's sum over its S filters as a pairwise tree (shorter dependency
                     // chains than a running sum)
                     const float2 ar = unpack2(tree_sum2<NP>(yre)), ai = unpack2(tree_sum2<NP>(yim));
-                    rrow[r] = make_float2(ar.x + ar.y, ai.x + ai.y);
+                    return make_float2(ar.x + ar.y, ai.x + ai.y);
                 };
                 if (nr == R) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) step(r);
+                    for (int r = 0; r < R; r += 2) {
+                        const float2 s0 = step(r), s1 = step(r + 1);
+                        *reinterpret_cast<float4 *>(rrow + r) = make_float4(s0.x, s0.y, s1.x, s1.y);
+                    }
                 } else {
 #pragma unroll 1
-                    for (int r = 0; r < nr; ++r) step(r);
+                    for (int r = 0; r < nr; ++r) rrow[r] = step(r);
                 }
             }
             __syncwarp();
@@ -175,7 +183,8 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
             // rounding as two scalar additions).
             u64 *red2 = reinterpret_cast<u64 *>(red);
             for (int col = lane; busy && wfirst >= 0 && col < R; col += 32) {
-                u64 *colp = red2 + (warp * 32) * (R + 1) + col;
+                constexpr int RS = bank_red_stride(R);
+                u64 *colp = red2 + (warp * 32) * RS + col;
                 int j = 0;
                 for (int sg = wfirst; sg < nseg; ++sg) {
                     const int4 g = a.segs[seg0 + sg];
@@ -183,16 +192,16 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                     const int hi = min(g.z, warp * 32 + 32) - warp * 32;
                     if (hi <= lo) break;
 #ifdef SPIIR_CHECKED
-                    if ((warp * 32 + hi - 1) * (R + 1) + col >= NL * (R + 1)) {
+                    if ((warp * 32 + hi - 1) * RS + col >= NL * RS) {
                         report_bounds(a.status, 8);
                         break;
                     }
 #endif
                     u64 acc = 0;  // (+0, +0)
-                    const u64 *rp = colp + lo * (R + 1);
+                    const u64 *rp = colp + lo * RS;
 #pragma unroll 8
-                    for (int i = lo; i < hi; ++i, rp += R + 1) acc = add2(acc, *rp);
-                    colp[j * (R + 1)] = acc;
+                    for (int i = lo; i < hi; ++i, rp += RS) acc = add2(acc, *rp);
+                    colp[j * RS] = acc;
                     ++j;
                 }
             }
@@ -204,7 +213,7 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                 const int4 g = a.segs[seg0 + sg];
                 u64 acc = 0;
                 for (int w = g.y >> 5; w <= (g.z - 1) >> 5; ++w)
-                    acc = add2(acc, red2[(w * 32 + (sg - a.wfirst[cta * NW + w])) * (R + 1) + r]);
+                    acc = add2(acc, red2[(w * 32 + (sg - a.wfirst[cta * NW + w])) * bank_red_stride(R) + r]);
                 float2 *zrow = a.z + ((int64_t)g.x * a.n_det + det) * a.zpitch;
 #ifdef SPIIR_CHECKED
                 if (((int64_t)g.x * a.n_det + det) * a.zpitch + k0 + kb + r >= a.z_elems) {
@@ -301,7 +310,7 @@ size_t bank_red_offset(const spiir_bank_s *b) {
 }
 
 size_t bank_smem_bytes(const spiir_bank_s *b) {
-    return bank_red_offset(b) + (size_t)b->NL * (b->R + 1) * sizeof(float2);
+    return bank_red_offset(b) + (size_t)b->NL * bank_red_stride(b->R) * sizeof(float2);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1051,7 +1060,7 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
                     kStaticScratchBytes);
     BankArgs a{};
     a.red_offset = kBankSmemHead + (size_t)(((D_pad + tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
-    const size_t smem = a.red_offset + (size_t)NL * (R + 1) * sizeof(float2);
+    const size_t smem = a.red_offset + (size_t)NL * bank_red_stride(R) * sizeof(float2);
     if (smem > (size_t)kBankMaxSmem) return fail(SPIIR_EUNSUPPORTED, "strain window does not fit in shared memory");
     unsigned char *base = nullptr;
     SPIIR_TRY(static_scratch_address(&base));
