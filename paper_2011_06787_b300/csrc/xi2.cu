@@ -24,6 +24,12 @@ constexpr int kXiMaxLags = 1024;
 
 __device__ __forceinline__ int xpos(int x, int L) { return (x & 7) * L + (x >> 3); }
 
+// Plane stride of the transposed tile, a compile-time constant so that the 8 planes of the
+// sliding-window reads sit at immediate offsets: at least (1024 + 2 Nj + 8) / 8 + 1, odd.
+constexpr int xi_plane_stride(int n_lags) { return ((kXiKT + 2 * n_lags + kXiM) / 8 + 1) | 1; }
+constexpr int kXiLSmall = xi_plane_stride(192), kXiLMax = xi_plane_stride(kXiMaxLags);
+
+template <int L>
 __global__ void __launch_bounds__(kXiThreads) k_xi2(const float2 *__restrict__ snr, int64_t pitch,
                                                     const float2 *__restrict__ A, int Nj, int64_t n, int n_det,
                                                     float *__restrict__ out, int64_t opitch) {
@@ -31,8 +37,7 @@ __global__ void __launch_bounds__(kXiThreads) k_xi2(const float2 *__restrict__ s
     const int t = blockIdx.z, I = blockIdx.y, tid = threadIdx.x;
     const int64_t k0 = (int64_t)blockIdx.x * kXiKT;
     const int ntap = 2 * Nj + 1;
-    const int W = kXiKT + 2 * Nj + kXiM;  // staged samples
-    const int L = W / 8 + 1;
+    const int W = kXiKT + 2 * Nj + kXiM;  // staged samples (W / 8 + 1 <= L, checked by the host)
     float4 *tab = reinterpret_cast<float4 *>(smem);           // [ntap]
     float2 *zt = reinterpret_cast<float2 *>(tab + ntap);      // [8 L] transposed tile
     __shared__ float den_part[kXiThreads / 32];
@@ -335,17 +340,19 @@ extern "C" int spiir_xi2(int T, int n_det, const float *snr, int64_t snr_pitch, 
     if (xi2_pitch < n) return fail(SPIIR_EINVAL, "xi2_pitch %lld < n", (long long)xi2_pitch);
     if (((uintptr_t)snr) % 8 || ((uintptr_t)A) % 8) return fail(SPIIR_EINVAL, "snr and A must be 8-byte aligned");
     const int ntap = 2 * n_lags + 1;
-    const int W = kXiKT + 2 * n_lags + kXiM, L = W / 8 + 1;
+    const int L = xi_plane_stride(n_lags) <= kXiLSmall ? kXiLSmall : kXiLMax;
     const size_t smem = (size_t)ntap * sizeof(float4) + (size_t)8 * L * sizeof(float2);
     static bool attr = false;
     if (!attr) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_xi2, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_xi2<kXiLSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_xi2<kXiLMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
         attr = true;
     }
     const dim3 grid((unsigned)((n + kXiKT - 1) / kXiKT), (unsigned)n_det, (unsigned)T);
-    k_xi2<<<grid, kXiThreads, smem, (cudaStream_t)stream>>>(reinterpret_cast<const float2 *>(snr), snr_pitch,
-                                                             reinterpret_cast<const float2 *>(A), n_lags, n, n_det,
-                                                             xi2, xi2_pitch);
+    auto kern = L == kXiLSmall ? k_xi2<kXiLSmall> : k_xi2<kXiLMax>;
+    kern<<<grid, kXiThreads, smem, (cudaStream_t)stream>>>(reinterpret_cast<const float2 *>(snr), snr_pitch,
+                                                          reinterpret_cast<const float2 *>(A), n_lags, n, n_det, xi2,
+                                                          xi2_pitch);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }
