@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "coherent.cuh"
@@ -462,7 +463,10 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
             best[i] = -1.f;
             arg[i] = INT_MAX;
         }
-        if (cur.okmask) {
+        // the pixel loop for the first NA shifts of the chunk (NA a power of two): a short last
+        // chunk (100 shifts in chunks of 16 end with 4) evaluates only the shifts it has
+        auto scan = [&](auto na) {
+            constexpr int NA = decltype(na)::value;
             for (int p = tid; p < a.n_pix; p += kPtThreads) {
                 // the entry's fields of detectors r and Jq[q] at run-time offsets (a select over
                 // a register copy of the entry would be turned back into a local-memory array)
@@ -480,7 +484,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
                     wq[q] = reinterpret_cast<const float *>(win + q * kPtWP + (ep->off[cur.Jq[q]] - offr - cur.dmn[q]));
                 }
 #pragma unroll
-                for (int i = 0; i < S; ++i) {
+                for (int i = 0; i < NA; ++i) {
                     u64 y0 = yb0, y1 = yb1;
 #pragma unroll
                     for (int q = 0; q < NC; ++q) {
@@ -496,6 +500,15 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
                     }
                 }
             }
+        };
+        if (cur.okmask) {
+            constexpr int S4 = S >= 4 ? S / 4 : 1, S2 = S >= 2 ? S / 2 : 1;
+            if (cur.ns <= S4)
+                scan(std::integral_constant<int, S4>{});
+            else if (cur.ns <= S2)
+                scan(std::integral_constant<int, S2>{});
+            else
+                scan(std::integral_constant<int, S>{});
         }
         warp_reduce_shifts<S>(best, arg, lane);
         if ((lane & ((32 >> kLog) - 1)) == 0) {
