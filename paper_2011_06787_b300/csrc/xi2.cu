@@ -268,6 +268,111 @@ __global__ void __launch_bounds__(256) k_xi2_points(const __grid_constant__ XiPo
     }
 }
 
+// xi^2 numerator of one detector row with the template's taps of this lane in registers: all
+// NT loads of the row are issued at once (one memory round trip per row).  Taps past the last
+// one are zero and add nothing.
+template <int NT>
+__device__ __forceinline__ float xi_num_reg(const float2 *__restrict__ row, const float2 (&Ar)[NT], int ntap, int Nj,
+                                            int lane) {
+    const float2 zc = row[Nj];
+    float2 v[NT];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        const int j = lane + 32 * i;
+        v[i] = j < ntap ? row[j] : make_float2(0.f, 0.f);
+    }
+    float num = 0.f;
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        const float dr = v[i].x - (zc.x * Ar[i].x - zc.y * Ar[i].y);
+        const float di = v[i].y - (zc.x * Ar[i].y + zc.y * Ar[i].x);
+        num = fmaf(dr, dr, fmaf(di, di, num));
+    }
+    return warp_sum(num);
+}
+
+// The same statistic as k_xi2_points for templates of at most 32 NT taps and at most 4
+// detectors, with the dependent loads batched: the template's taps and the denominator once per
+// item, then lane i loads shift s0 + i's argmax pixel and that pixel's delays, which the shift
+// loop takes by shuffles.
+template <int NT>
+__global__ void __launch_bounds__(256) k_xi2_points_reg(const __grid_constant__ XiPointArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int nc = min(*a.n_cand, a.max_cand);
+    const int n_chunks = (a.n_shifts + kXiPtShifts - 1) / kXiPtShifts;
+    const int64_t n_items = (int64_t)max(nc, 0) * n_chunks;
+    const int ntap = 2 * a.Nj + 1, nd = a.n_det;
+    const float nan = __int_as_float(0x7fc00000);
+    for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items; item += warps) {
+        const int c = (int)(item / n_chunks), s0 = (int)(item % n_chunks) * kXiPtShifts;
+        const int s1 = min(a.n_shifts, s0 + kXiPtShifts);
+        const int4 cd = a.cand[c];
+        const int r = cd.x, t = cd.y;
+        const int64_t e = a.off + (int64_t)cd.z;
+        const bool rec_ok = r >= 0 && r < nd && t >= 0 && t < a.n_templates && cd.z >= 0 && e - a.Nj >= 0 &&
+                            e + a.Nj < a.pitch;
+        const float2 *At = a.A + (int64_t)(rec_ok ? t : 0) * ntap;
+        float2 Ar[NT];
+        float den = 0.f;
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            const int j = lane + 32 * i;
+            Ar[i] = j < ntap ? At[j] : make_float2(0.f, 0.f);
+            den += j < ntap ? 2.f - 2.f * (Ar[i].x * Ar[i].x + Ar[i].y * Ar[i].y) : 0.f;
+        }
+        den = warp_sum(den);
+        // lane i: the argmax pixel of shift s0 + i and its delays
+        int pl = -1, dl[4] = {0, 0, 0, 0};
+        if (lane < s1 - s0) {
+            pl = a.argmax[(int64_t)c * a.n_shifts + s0 + lane];
+            if (pl >= 0 && pl < a.n_pix) {
+#pragma unroll
+                for (int J = 0; J < 4; ++J)
+                    if (J < nd) dl[J] = a.delays[(int64_t)pl * nd + J];
+            }
+        }
+        const float xi_r =
+            rec_ok ? xi_num_reg<NT>(a.snr + ((int64_t)t * nd + r) * a.pitch + e - a.Nj, Ar, ntap, a.Nj, lane) / den : nan;
+        for (int si = s0; si < s1; ++si) {
+            const int64_t o = (int64_t)c * a.n_shifts + si;
+            const int p = __shfl_sync(0xffffffffu, pl, si - s0);
+            int dJ[4], d_r = 0;
+#pragma unroll
+            for (int J = 0; J < 4; ++J) {
+                dJ[J] = __shfl_sync(0xffffffffu, dl[J], si - s0);
+                d_r = (J == r) ? dJ[J] : d_r;
+            }
+            const int64_t s = (int64_t)a.first_shift + si;
+            bool ok = rec_ok && p >= 0 && p < a.n_pix;
+            float total = 0.f;
+            int comp = 0;
+#pragma unroll
+            for (int J = 0; J < 4; ++J) {
+                if (J >= nd || !ok) break;
+                float xi;
+                if (J == r) {
+                    xi = xi_r;
+                } else {
+                    const int64_t x = e + dJ[J] - d_r - s * (++comp) * a.step;
+                    if (x - a.Nj < 0 || x + a.Nj >= a.pitch) {
+                        ok = false;
+                        break;
+                    }
+                    xi = xi_num_reg<NT>(a.snr + ((int64_t)t * nd + J) * a.pitch + x - a.Nj, Ar, ntap, a.Nj, lane) / den;
+                }
+                total += xi;
+                if (a.xi2_det && lane == 0) a.xi2_det[o * nd + J] = xi;
+            }
+            if (lane == 0) {
+                a.xi2[o] = ok ? total / nd : nan;
+                if (!ok && a.xi2_det)
+                    for (int J = 0; J < nd; ++J) a.xi2_det[o * nd + J] = nan;
+            }
+        }
+    }
+}
+
 }  // namespace spiir
 
 using namespace spiir;
@@ -311,7 +416,17 @@ extern "C" int spiir_xi2_candidates(spiir_sky_t sky, int T, const float *snr, in
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const int64_t items = (int64_t)max_cand * ((n_shifts + kXiPtShifts - 1) / kXiPtShifts);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)n_sm * 8));
-    k_xi2_points<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    const int nt = (2 * n_lags + 1 + 31) / 32;  // taps per lane
+    if (a.n_det <= 4 && nt <= 4)
+        k_xi2_points_reg<4><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    else if (a.n_det <= 4 && nt <= 8)
+        k_xi2_points_reg<8><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    else if (a.n_det <= 4 && nt <= 12)
+        k_xi2_points_reg<12><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    else if (a.n_det <= 4 && nt <= 16)
+        k_xi2_points_reg<16><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    else
+        k_xi2_points<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }
