@@ -127,6 +127,11 @@ def test_exact_ties_across_groups_take_lowest_pixel(copies, shape):
     clear = top[..., -1] - top[..., -2] > 1e-4 * top[..., -1]
     assert clear.mean() > 0.5
     np.testing.assert_array_equal(am[clear], am_or[clear])
+    # the sky-map instances resolve the ties identically, and the map holds the copies' equal values
+    ms2, am2, nl2, mp = _scan(sky, z, n, skymap=True)
+    assert np.array_equal(ms2, ms) and np.array_equal(am2, am) and np.array_equal(nl2, nl)
+    for c in range(1, copies):
+        assert np.array_equal(mp[:, c * m:(c + 1) * m], mp[:, :m])
 
 
 def _pipeline_stream(bank, sky, strain, chunk, host=False):
