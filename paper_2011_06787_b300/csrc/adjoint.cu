@@ -352,7 +352,9 @@ __device__ __forceinline__ void bwd_block(const float4 *gq, int s0i, int rl, Pai
         const u64 nli = fma2(ar, lam.im, fma2(nai, lam.re, pack2(gk.z, gk.w)));
         lam = {nlr, nli};
         bsr = fma2(nlr, yp[r].re, fma2(nli, yp[r].im, bsr));
-        bsi = fma2(nli, yp[r].re, fma2(neg2(nlr), yp[r].im, bsi));
+        // - nlr y.im as a multiply-subtract, which the compiler folds into one packed FMA with a
+        // negated product (an explicit sign flip would cost an integer operation per step)
+        bsi = fma2(nli, yp[r].re, sub2(bsi, mul2(nlr, yp[r].im)));
         if (CHECK) {
             if (ed[0] == s0i + r) gbv[0] = make_float2(unpack2(nlr).x, unpack2(nli).x);
             if (ed[1] == s0i + r) gbv[1] = make_float2(unpack2(nlr).y, unpack2(nli).y);

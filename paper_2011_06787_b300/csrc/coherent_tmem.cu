@@ -85,11 +85,6 @@ __device__ __forceinline__ void tm_st8(uint32_t addr, const float (&v)[8]) {
                  : "memory");
 }
 
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-    u64 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 
 // shared-memory SNR planes, transposed by 8: element x at (x % 8) * L + x / 8, so the 32 rows
 // of a warp reading sample 8 r + c hit 32 consecutive words
