@@ -72,8 +72,10 @@ __global__ void __launch_bounds__(kXiThreads) k_xi2(const float2 *__restrict__ s
         acc[m] = 0;
     }
     // tap s (j = s - Nj): logical window element m (sample m of this thread) is w[(m + s) % 8];
-    // afterwards w[s % 8] takes the element that enters at the next tap
-    auto tap = [&](int s, int u) {
+    // afterwards w[s % 8] takes the element that enters at the next tap, tile position
+    // base + s + 8.  With s = 8 i + u that position lies in plane u at offset tid + i + 1, so
+    // the 8 taps of a group read zg[u L] from one pointer with constant offsets.
+    auto tap = [&](int s, int u, const float2 *zg) {
         const float4 e = tab[s];
         const u64 M1 = pack2(e.x, e.y), M2 = pack2(e.z, e.w);
 #pragma unroll
@@ -81,17 +83,21 @@ __global__ void __launch_bounds__(kXiThreads) k_xi2(const float2 *__restrict__ s
             const u64 d = fma2(z0i[m], M2, fma2(z0r[m], M1, w[(m + u) & 7]));
             acc[m] = fma2(d, d, acc[m]);
         }
-        const float2 v = zt[xpos(base + s + kXiM, L)];
+        const float2 v = zg[u * L];
         w[u] = pack2(v.x, v.y);
     };
     int s = 0;
     for (; s + 8 <= ntap; s += 8) {
+        const float2 *zg = zt + tid + (s >> 3) + 1;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) tap(s + u, u);
+        for (int u = 0; u < 8; ++u) tap(s + u, u, zg);
     }
+    {
+        const float2 *zg = zt + tid + (s >> 3) + 1;
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-        if (s + u < ntap) tap(s + u, u);
+        for (int u = 0; u < 8; ++u)
+            if (s + u < ntap) tap(s + u, u, zg);
+    }
 
     float *orow = out + ((int64_t)t * n_det + I) * opitch + k0 + base;
     const float rden = 1.f / den;
