@@ -336,7 +336,9 @@ def _responses(T, F, nr, seed):
     return oracle.impulse_forward(off, a1.ravel(), b0.ravel(), d.ravel(), np.zeros(T * F, np.complex64), nr)
 
 
-@pytest.mark.parametrize("n_det,Nj,n_sh", [(3, 40, 6), (2, 175, 1), (4, 7, 9)])
+# taps per lane 3, 11, 1, 7 and 13 take the register forms (4, 12, 4, 8 and 16 taps per lane),
+# 601 taps the general kernel; 9 and 10 shifts leave a ragged last group of 8
+@pytest.mark.parametrize("n_det,Nj,n_sh", [(3, 40, 6), (2, 175, 1), (4, 7, 9), (4, 100, 10), (3, 200, 9), (3, 300, 3)])
 def test_xi2_at_candidates_matches_oracle(n_det, Nj, n_sh):
     """xi_C^2 at each (candidate, shift) item at the oracle's coherent argmax, against the
     oracle's xi^2 on a one-sample window at each detector's implied time; items whose reads
