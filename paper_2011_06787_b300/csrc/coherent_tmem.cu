@@ -27,7 +27,9 @@
 // groups are cut into four slices of nearly equal pixel count.  Per sample the four slice
 // maxima are merged in shared memory; the sample's winning group is then rescanned in scalar
 // arithmetic to find the lowest pixel index attaining the maximum, as in the shared-memory
-// kernel.  In sky-map mode every row also writes its 8 statistics of each pixel to
+// kernel.  A maximum that several groups attain exactly (unless pixel 0, the all-zero window,
+// settles it) is left to a second pass in which a whole warp rescans the sky for that sample.
+// In sky-map mode every row also writes its 8 statistics of each pixel to
 // map[t][p][k] (two 16-byte streaming stores), which overlaps the map's HBM writes with the
 // arithmetic.
 //
