@@ -309,7 +309,7 @@ def run_gpu(args):
     peak_max = n_sm * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12          # TFLOP/s at max clock
     peak_run = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     shape = tuple(sky.get_scan_shape()[:3])
-    if shape[:2] == (512, 4):
+    if shape[:2] in ((512, 4), (256, 4)):
         # tensor-memory scan; with the third value 1 the sky's tables travel as kernel parameters
         coh_name = "k_coherent_tmem_pt" if shape[2] == 1 and P <= 4096 else "k_coherent_tmem"
         coh_src = ["paper_2011_06787_b300/csrc/coherent_tmem.cu", "paper_2011_06787_b300/csrc/coherent.cuh"]

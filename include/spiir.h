@@ -197,11 +197,14 @@ int spiir_sky_info(spiir_sky_t sky, int *n_det, int *n_pix, int *halo);
  * device.  grouped (output) is 1 when the grouped scan applies: 2 or 3 detectors, an
  * orthonormal U with a rank-2 signal plane, at most 65535 pixels.  Default 256 threads,
  * 2 pairs, table in shared memory.
- * threads = 512 with pairs = 4 selects the tensor-memory scan (3 detectors, max |Delta| <= 60,
- * pixel table within shared memory): each of 128 thread rows keeps the detector-1 and -2 SNR
- * windows of its 8 consecutive samples in tensor memory (one block per SM, 512 columns).
- * It pairs the FP32 arithmetic differently from the shared-memory scan, so the two agree to
- * rounding; with a sky map each thread writes its 8 samples of a pixel as one 32-byte segment.
+ * pairs = 4 selects the tensor-memory scan (3 detectors, pixel table within shared memory):
+ * each of 128 thread rows keeps the detector-1 and -2 SNR windows of its consecutive samples
+ * in tensor memory (one block per SM, 512 columns); threads = 512 gives 8 samples per row
+ * (max |Delta| <= 60), threads = 256 gives 16 (max |Delta| <= 56, whole 2048-sample chunks per
+ * work item, fewer per-pixel overheads per sample with half the warps).  Both pair the FP32
+ * arithmetic differently from the shared-memory scan, so they agree with it to rounding and
+ * with each other bit for bit; with a sky map each thread writes its samples of a pixel as
+ * one contiguous segment.
  * For this shape the third value selects where the pixel groups and per-pixel delay offsets
  * are read: 1 (default) from the kernel's parameter space when the sky has at most 4096
  * pixels and 512 groups (warp-uniform reads, so the tensor-memory addresses stay in uniform

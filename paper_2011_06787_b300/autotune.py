@@ -13,7 +13,7 @@ import os
 
 BANK_SHAPES = [(8, 256, 32, 1024), (8, 128, 32, 1024), (8, 128, 64, 1024), (8, 128, 20, 1000), (4, 256, 16, 1024), (4, 128, 16, 1024),
                (8, 256, 16, 1024), (8, 128, 16, 2048), (16, 256, 32, 1024), (16, 128, 16, 1024)]
-SCAN_SHAPES = [(512, 4, 1), (512, 4, 0), (256, 2, 1), (256, 2, 0), (512, 1, 0), (256, 1, 0), (512, 2, 0), (512, 1, 1)]
+SCAN_SHAPES = [(512, 4, 1), (256, 4, 1), (512, 4, 0), (256, 4, 0), (256, 2, 1), (256, 2, 0), (512, 1, 0), (256, 1, 0), (512, 2, 0), (512, 1, 1)]
 
 _cache: dict = {}
 

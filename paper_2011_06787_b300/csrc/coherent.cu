@@ -463,14 +463,15 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         m.q0 = sky->g_q0;
         m.g0 = sky->g_g0;
         for (int i = 0; i < 5; ++i) m.slice[i] = sky->t_slice[i];
-        m.C = tmem_columns(sky->halo);
+        m.mw = sky->scan_tmem_mw;
+        m.C = tmem_columns(sky->halo, m.mw);
         m.max_stat = max_stat;
         m.argmax = argmax;
         m.null_stat = null_stat;
         m.skymap = skymap;
         m.map_vec = (n % 4 == 0 && ((uintptr_t)skymap % 16) == 0) ? 1 : 0;
         // short chunks: several templates share a work item (their rows split the 128 lanes)
-        m.nsub = n <= 256 ? 4 : (n <= 512 ? 2 : 1);
+        m.nsub = tmem_templates_per_item(n, m.mw);
         return launch_coherent_tmem(m, sky->scan_tmem_param ? sky->t_tab : nullptr, stream);
     }
     if (sky->grouped) {
@@ -633,7 +634,7 @@ static int build_grouped(spiir_sky_s *s, const int32_t *delays, const float *u_s
     s->n_grp = (int)grp.size();
     // tensor-memory scan: raw offsets delta_I = H + Delta_I, and four slices of consecutive
     // groups holding nearly equal numbers of pixels
-    if (nd == 3 && tmem_fits(P, s->n_grp, H)) {
+    if (nd == 3 && tmem_fits(P, s->n_grp, H, 8)) {
         std::vector<float4> te(ent);
         for (int q = 0; q < P; ++q) {
             const int p = order[q];
@@ -758,19 +759,22 @@ extern "C" int spiir_coherent_scan(spiir_sky_t s, const float *snr, int64_t pitc
 extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs, int table_in_shared) {
     clear_error();
     if (!s) return fail(SPIIR_EINVAL, "sky is NULL");
-    if (threads == 512 && pairs == 4) {
-        // tensor-memory scan; the shared-memory kernel keeps its shape for sky-map requests
-        if (!s->tmem_ok)
+    if ((threads == 512 || threads == 256) && pairs == 4) {
+        // tensor-memory scan, 8 samples per thread row with 512 threads or 16 with 256; the
+        // shared-memory kernel keeps its shape for sky-map requests
+        const int mw = threads == 512 ? 8 : 16;
+        if (!s->tmem_ok || !tmem_fits(s->n_pix, s->n_grp, s->halo, mw))
             return fail(SPIIR_EUNSUPPORTED, "tensor-memory scan needs 3 detectors, an orthonormal basis, "
-                                            "|Delta| <= 60 and a table that fits in shared memory");
+                                            "|Delta| <= %d and a table that fits in shared memory", mw == 8 ? 60 : 56);
         if (table_in_shared != 0 && table_in_shared != 1)
             return fail(SPIIR_EINVAL, "the third value of the tensor-memory shape must be 0 or 1");
         s->scan_tmem = 1;
         s->scan_tmem_param = table_in_shared;
+        s->scan_tmem_mw = mw;
         return SPIIR_OK;
     }
     if ((threads != 256 && threads != 512) || (pairs != 1 && pairs != 2) || (table_in_shared != 0 && table_in_shared != 1))
-        return fail(SPIIR_EINVAL, "threads must be 256 or 512, pairs 1 or 2 (or 512 and 4), table_in_shared 0 or 1");
+        return fail(SPIIR_EINVAL, "threads must be 256 or 512, pairs 1, 2 or 4 (tensor memory), table_in_shared 0 or 1");
     s->scan_tmem = 0;
     s->scan_table_shared = table_in_shared;
     if (!s->grouped) {
@@ -805,7 +809,7 @@ extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs, i
 
 extern "C" int spiir_sky_get_scan_shape(spiir_sky_t s, int *threads, int *pairs, int *table_in_shared, int *grouped) {
     if (!s) return fail(SPIIR_EINVAL, "sky is NULL");
-    if (threads) *threads = s->scan_tmem ? 512 : s->scan_threads;
+    if (threads) *threads = s->scan_tmem ? (s->scan_tmem_mw == 16 ? 256 : 512) : s->scan_threads;
     if (pairs) *pairs = s->scan_tmem ? 4 : s->scan_pairs;
     if (table_in_shared) *table_in_shared = s->scan_tmem ? s->scan_tmem_param : s->scan_table_shared;
     if (grouped) *grouped = s->grouped ? 1 : 0;

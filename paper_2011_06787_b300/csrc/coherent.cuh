@@ -56,6 +56,7 @@ struct TmemArgs {
     float *skymap;          // NULL or [T][P][n]
     int map_vec;            // 1: n % 4 == 0 and skymap 16-byte aligned (vector stores)
     int nsub;               // templates per work item (1, 2 or 4): 128 / nsub rows each
+    int mw;                 // consecutive samples per thread row: 8 (512 threads) or 16 (256)
 };
 
 // Per-pixel delay offsets (delta_1 | delta_2 << 16) and the pixel groups of the tensor-memory
@@ -68,8 +69,9 @@ struct TmemTab {
     int4 grp[kTmTabGrp];
 };
 
-int tmem_columns(int H);
-bool tmem_fits(int n_pix, int n_grp, int H);
+int tmem_columns(int H, int mw);
+bool tmem_fits(int n_pix, int n_grp, int H, int mw);
+int tmem_templates_per_item(int64_t n, int mw);
 int launch_coherent_tmem(const TmemArgs &a, const TmemTab *tab, cudaStream_t stream);
 
 // Per-pixel entry of the general table: the two signal columns of U_s and H + Delta_I.
@@ -116,6 +118,7 @@ struct spiir_sky_s {
     int scan_table_shared = 1;  // 1: stage the table in shared memory when it fits; 0: read it through L1
     int scan_tmem = 0;          // 1: tensor-memory scan (3 detectors, no sky map)
     int scan_tmem_param = 1;    // tensor-memory scan: 1 = group and offset tables as kernel parameters when they fit
+    int scan_tmem_mw = 8;       // tensor-memory scan: samples per thread row, 8 (512 threads) or 16 (256)
     // tensor-memory scan tables (same pixel order and groups as the grouped scan)
     bool tmem_ok = false;
     float4 *t_ent = nullptr;

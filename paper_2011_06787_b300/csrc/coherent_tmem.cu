@@ -46,39 +46,45 @@
 
 namespace spiir {
 
-constexpr int kTmThreads = 512;
 constexpr int kTmRows = 128;                // TMEM lanes = thread rows
-constexpr int kTmM = 8;                     // consecutive samples per row
-constexpr int kTmKT = kTmRows * kTmM;       // samples per work item
 constexpr int kTmDet = 256;                 // TMEM columns per detector (2 detectors, 512 columns)
 constexpr int kTmMinSmem = 120 * 1024;      // keeps a second block off the SM
+// MW consecutive samples per thread row: 8 with 512 threads (4 pixel slices of 4 warps) or 16
+// with 256 threads (2 slices), so that a work item covers 128 MW samples either way
+constexpr int tm_threads(int MW) { return MW == 8 ? 512 : 256; }
 
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Two-column TMEM load (real, imaginary) of sample M of the window at addr, for this warp's
-// 32 lanes.  The column 2 M after addr is even whenever addr is.
-template <int M>
-__device__ __forceinline__ void tl2(u64 (&w)[8], uint32_t addr) {
+// Two-column TMEM load (real, imaginary) of sample K of the window at addr, for this warp's
+// 32 lanes.  The column 2 K after addr is even whenever addr is.
+template <int K, int MW>
+__device__ __forceinline__ void tl2(u64 (&w)[MW], uint32_t addr) {
     uint32_t lo, hi;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2+%3];"
                  : "=r"(lo), "=r"(hi)
-                 : "r"(addr), "n"(2 * M)
+                 : "r"(addr), "n"(2 * K)
                  : "memory");
-    asm("mov.b64 %0, {%1, %2};" : "=l"(w[M]) : "r"(lo), "r"(hi));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(w[K]) : "r"(lo), "r"(hi));
 }
 
-__device__ __forceinline__ void tm_window(u64 (&w)[8], uint32_t addr) {
+template <int MW>
+__device__ __forceinline__ void tm_window(u64 (&w)[MW], uint32_t addr) {
     tl2<0>(w, addr), tl2<1>(w, addr), tl2<2>(w, addr), tl2<3>(w, addr);
     tl2<4>(w, addr), tl2<5>(w, addr), tl2<6>(w, addr), tl2<7>(w, addr);
+    if constexpr (MW == 16) {
+        tl2<8>(w, addr), tl2<9>(w, addr), tl2<10>(w, addr), tl2<11>(w, addr);
+        tl2<12>(w, addr), tl2<13>(w, addr), tl2<14>(w, addr), tl2<15>(w, addr);
+    }
 }
 
 // Completes every outstanding TMEM load of the thread; the empty statements after it pin the
 // loaded registers behind the wait.
-__device__ __forceinline__ void tm_wait_ld(u64 (&a)[8], u64 (&b)[8]) {
+template <int MW>
+__device__ __forceinline__ void tm_wait_ld(u64 (&a)[MW], u64 (&b)[MW]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int m = 0; m < 8; ++m) asm volatile("" : "+l"(a[m]), "+l"(b[m]));
+    for (int m = 0; m < MW; ++m) asm volatile("" : "+l"(a[m]), "+l"(b[m]));
 }
 
 __device__ __forceinline__ void tm_st8(uint32_t addr, const float (&v)[8]) {
@@ -95,8 +101,9 @@ __device__ __forceinline__ int tpos(int x, int L) { return (x & 7) * L + (x >> 3
 // PT: the group table and the per-pixel offsets come from the kernel parameter pt (read with
 // warp-uniform indices, so the tensor-memory addresses stay in uniform registers); otherwise
 // from shared memory.
-template <bool MAP, bool PT, int NSUB>
+template <bool MAP, bool PT, int NSUB, int MW>
 __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) {
+    constexpr int NT = tm_threads(MW), SL = NT / 128, KT = kTmRows * MW;  // threads, slices, slots
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31;
     // with PT the broadcast tells the compiler that the warp index (and so every table index
@@ -106,38 +113,38 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
     const int row = 32 * q + lane;
     const int P = a.n_pix, G = a.n_grp, H = a.H, C = a.C;
     // nsub templates per work item: template s of the item owns rows s RPT .. (s + 1) RPT - 1
-    // and the tile segment s SEG .. s SEG + SEG - 1 (its 8 RPT samples plus the C-sample halo)
-    constexpr int nsub = NSUB, RPT = kTmRows / NSUB, KS = kTmM * RPT;
+    // and the tile segment s SEG .. s SEG + SEG - 1 (its MW RPT samples plus the C-sample halo)
+    constexpr int nsub = NSUB, RPT = kTmRows / NSUB, KS = MW * RPT;
     const int SEG = KS + C;
     const int W0 = nsub * SEG;      // staged samples per plane
     const int L = W0 / 8 + 1;       // transposed plane stride (odd)
     const int PL = 8 * L;           // floats per staged plane
     const int rsub = row / RPT;                          // this thread row's template in an item
-    const int rbase = rsub * SEG + kTmM * (row % RPT);   // tile position of the row's first sample
+    const int rbase = rsub * SEG + MW * (row % RPT);     // tile position of the row's first sample
 
     float4 *ent = reinterpret_cast<float4 *>(smem);
     size_t off = (size_t)P * sizeof(float4);
     int4 *grp = reinterpret_cast<int4 *>(smem + off);
     off += (size_t)G * sizeof(int4);
     float *cb_best = reinterpret_cast<float *>(smem + off);
-    off += (size_t)4 * kTmKT * sizeof(float);
+    off += (size_t)SL * KT * sizeof(float);
     unsigned *cb_grp = reinterpret_cast<unsigned *>(smem + off);
-    off += (size_t)4 * kTmKT * sizeof(unsigned);
+    off += (size_t)SL * KT * sizeof(unsigned);
     float *zp = reinterpret_cast<float *>(smem + off);  // [3 detectors][re, im][PL]
     off += (size_t)6 * PL * sizeof(float);
     uint16_t *orig = reinterpret_cast<uint16_t *>(smem + off);
     off += ((size_t)P * sizeof(uint16_t) + 15) / 16 * 16;
     int *tie_slots = reinterpret_cast<int *>(smem + off);  // slots left to pass 2 of the merge
-    off += (size_t)kTmKT * sizeof(int);
+    off += (size_t)KT * sizeof(int);
     int *n_tie = reinterpret_cast<int *>(smem + off);
     off += 16;
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem + off);
 
-    for (int i = tid; i < P; i += kTmThreads) {
+    for (int i = tid; i < P; i += NT) {
         ent[i] = a.ent[i];
         orig[i] = a.orig[i];
     }
-    for (int i = tid; i < G; i += kTmThreads) grp[i] = a.grp[i];
+    for (int i = tid; i < G; i += NT) grp[i] = a.grp[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
                      "r"(512u)
@@ -149,7 +156,8 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
     tm_fence_after();
     const uint32_t tbase = PT ? __shfl_sync(0xffffffffu, *slot, 0) : *slot;
     const uint32_t la = tbase + ((uint32_t)(32 * q) << 16);  // this warp's lane quarter
-    const int g_lo = a.slice[sl], g_hi = a.slice[sl + 1];
+    // the host cuts the groups into 4 slices; with 2 slices each takes two of them
+    const int g_lo = a.slice[sl * (4 / SL)], g_hi = a.slice[(sl + 1) * (4 / SL)];
 
     const int ntiles = (int)((a.n + KS - 1) / KS);
     const int64_t n_items = (int64_t)((a.n_templates + nsub - 1) / nsub) * ntiles;
@@ -165,7 +173,7 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         if (tid == 0) *n_tie = 0;  // read again only after the barrier that ends the staging
         for (int I = 0; I < 3; ++I) {
             float *re = zp + (2 * I) * PL, *im = re + PL;
-            for (int x = tid; x < W0; x += kTmThreads) {
+            for (int x = tid; x < W0; x += NT) {
                 const int s = x / SEG, j = x - s * SEG;
                 const int ts = t0 + s;
                 const float2 v = (ts < a.n_templates && j < lim) ? a.snr[((int64_t)ts * 3 + I) * a.pitch + k0 + j]
@@ -175,14 +183,14 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
             }
         }
         __syncthreads();
-        // TMEM windows: warp slice sl fills detector 1 + (sl & 1), window half sl >> 1; four
-        // samples (8 columns) per store
-        {
-            const int I = 1 + (sl & 1);
+        // TMEM windows: unit u = 0..3 is detector 1 + (u & 1), window half u >> 1; warp slice
+        // sl fills units sl, sl + SL, ...; four samples (8 columns) per store
+        for (int u = sl; u < 4; u += SL) {
+            const int I = 1 + (u & 1);
             const float *re = zp + (2 * I) * PL, *im = re + PL;
             const uint32_t base = la + (uint32_t)((I - 1) * kTmDet);
             const int h = C / 2;
-            for (int c0 = (sl >> 1) * h; c0 < (sl >> 1) * h + h; c0 += 4) {
+            for (int c0 = (u >> 1) * h; c0 < (u >> 1) * h + h; c0 += 4) {
                 float v[8];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
@@ -192,18 +200,18 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                 }
                 tm_st8(base + 2 * c0, v);
             }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tm_fence_before();
         __syncthreads();
         tm_fence_after();
 
         // running maximum and winning group of this thread's samples within its slice, kept in
         // shared memory at [slice][m][row] (updated once per group)
-        float *my_best = cb_best + sl * kTmKT + row;
-        unsigned *my_grp = cb_grp + sl * kTmKT + row;
+        float *my_best = cb_best + sl * KT + row;
+        unsigned *my_grp = cb_grp + sl * KT + row;
 #pragma unroll
-        for (int m = 0; m < kTmM; ++m) {
+        for (int m = 0; m < MW; ++m) {
             my_best[m * kTmRows] = -INFINITY;
             my_grp[m * kTmRows] = 0;
         }
@@ -211,10 +219,10 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         for (int g = g_lo; g < g_hi; ++g) {
             const int4 gr = PT ? pt->grp[g] : grp[g];
             const int d0 = H + gr.w;
-            u64 w0[kTmM], s0[kTmM];
-            float gm[kTmM];
+            u64 w0[MW], s0[MW];
+            float gm[MW];
 #pragma unroll
-            for (int m = 0; m < kTmM; ++m) {
+            for (int m = 0; m < MW; ++m) {
                 const int x = rbase + d0 + m;
                 w0[m] = pack2(z0r[tpos(x, L)], z0i[tpos(x, L)]);
                 s0[m] = mul2(w0[m], w0[m]);
@@ -223,14 +231,14 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
             for (int p = gr.y; p < gr.z; ++p) {
                 const float4 e = ent[p];
                 const uint32_t o = PT ? pt->d12[p] : __float_as_uint(e.w);
-                u64 w1[kTmM], w2[kTmM];
+                u64 w1[MW], w2[MW];
                 tm_window(w1, la + 2 * (o & 0xFFFFu));
                 tm_window(w2, la + kTmDet + 2 * (o >> 16));
                 tm_wait_ld(w1, w2);
                 const u64 N0 = pack2(e.x, e.x), N1 = pack2(e.y, e.y), N2 = pack2(e.z, e.z);
-                float v[kTmM];
+                float v[MW];
 #pragma unroll
-                for (int m = 0; m < kTmM; ++m) {
+                for (int m = 0; m < MW; ++m) {
                     const u64 A = fma2(w2[m], w2[m], fma2(w1[m], w1[m], s0[m]));
                     const u64 nw = fma2(N2, w2[m], fma2(N1, w1[m], mul2(N0, w0[m])));
                     const float2 d = unpack2(sub2(A, mul2(nw, nw)));
@@ -238,22 +246,23 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                     gm[m] = fmaxf(gm[m], v[m]);
                 }
                 if (MAP && trow < a.n_templates) {
-                    // the row's 8 samples of this pixel: one contiguous 1 KB segment per warp,
-                    // written with the streaming (evict-first) hint
-                    const int64_t kr = k0 + kTmM * (row % RPT);
+                    // the row's MW samples of this pixel: one contiguous segment per warp, written
+                    // with the streaming (evict-first) hint
+                    const int64_t kr = k0 + MW * (row % RPT);
                     float *mrow = a.skymap + ((int64_t)trow * P + orig[p]) * a.n + kr;
-                    if (a.map_vec && kr + kTmM <= a.n) {
-                        __stcs(reinterpret_cast<float4 *>(mrow), make_float4(v[0], v[1], v[2], v[3]));
-                        __stcs(reinterpret_cast<float4 *>(mrow) + 1, make_float4(v[4], v[5], v[6], v[7]));
+                    if (a.map_vec && kr + MW <= a.n) {
+#pragma unroll
+                        for (int m = 0; m < MW; m += 4)
+                            __stcs(reinterpret_cast<float4 *>(mrow + m), make_float4(v[m], v[m + 1], v[m + 2], v[m + 3]));
                     } else {
 #pragma unroll
-                        for (int m = 0; m < kTmM; ++m)
+                        for (int m = 0; m < MW; ++m)
                             if (kr + m < a.n) __stcs(mrow + m, v[m]);
                     }
                 }
             }
 #pragma unroll
-            for (int m = 0; m < kTmM; ++m) {
+            for (int m = 0; m < MW; ++m) {
                 const float b = my_best[m * kTmRows];
                 if (gm[m] > b) {
                     my_best[m * kTmRows] = gm[m];
@@ -265,14 +274,14 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         }
         __syncthreads();
         // merge the slices and resolve the argmax (lowest original pixel index among equal maxima)
-        // slot j = 8 row + m: template t0 + row / RPT, its sample k0 + 8 (row % RPT) + m, tile
-        // position xj; it sits at [m][row] of the slice maxima
+        // slot j = MW row + m: template t0 + row / RPT, its sample k0 + MW (row % RPT) + m,
+        // tile position xj; it sits at [m][row] of the slice maxima
         auto slot_of = [&](int j, int &jk, int &xj, int &tj, int &cj) {
-            const int jr = j >> 3, js = jr / RPT;
-            jk = kTmM * (jr - js * RPT) + (j & 7);
+            const int jr = j / MW, js = jr / RPT;
+            jk = MW * (jr - js * RPT) + j % MW;
             xj = js * SEG + jk;
             tj = t0 + js;
-            cj = (j & 7) * kTmRows + jr;
+            cj = (j % MW) * kTmRows + jr;
         };
         // the statistic of sorted pixel p (detector-0 offset d0) at tile position xj, recomputed
         // in scalar arithmetic, and its null stream
@@ -311,19 +320,19 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         // pass 1, one thread per slot: a maximum attained by one group is resolved by rescanning
         // that group; one attained by several groups either by pixel 0 (the all-zero window) or,
         // else, by pass 2
-        for (int j = tid; j < kTmKT; j += kTmThreads) {
+        for (int j = tid; j < KT; j += NT) {
             int jk, xj, tj, cj;
             slot_of(j, jk, xj, tj, cj);
             if (tj >= a.n_templates || k0 + jk >= a.n) continue;
             float B = cb_best[cj];
-            for (int s = 1; s < 4; ++s) B = fmaxf(B, cb_best[s * kTmKT + cj]);
+            for (int s = 1; s < SL; ++s) B = fmaxf(B, cb_best[s * KT + cj]);
             int hits = 0;
             unsigned gsel = 0, tie = 0;
-            for (int s = 0; s < 4; ++s) {
-                if (cb_best[s * kTmKT + cj] == B) {
+            for (int s = 0; s < SL; ++s) {
+                if (cb_best[s * KT + cj] == B) {
                     ++hits;
-                    gsel = cb_grp[s * kTmKT + cj] & 0x7FFFFFFFu;
-                    tie |= cb_grp[s * kTmKT + cj] >> 31;
+                    gsel = cb_grp[s * KT + cj] & 0x7FFFFFFFu;
+                    tie |= cb_grp[s * KT + cj] >> 31;
                 }
             }
             int arg = 0x7fffffff;
@@ -351,12 +360,12 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         // the top pixels of two groups, of the order of once per few million samples of noise):
         // the lanes share the groups, and a butterfly combines their best pixels under the same
         // rule
-        for (int e = warp; e < *n_tie; e += kTmThreads / 32) {
+        for (int e = warp; e < *n_tie; e += NT / 32) {
             const int j = tie_slots[e];
             int jk, xj, tj, cj;
             slot_of(j, jk, xj, tj, cj);
             float B = cb_best[cj];
-            for (int s = 1; s < 4; ++s) B = fmaxf(B, cb_best[s * kTmKT + cj]);
+            for (int s = 1; s < SL; ++s) B = fmaxf(B, cb_best[s * KT + cj]);
             int arg = 0x7fffffff;
             float nul = 0.f, bv = -INFINITY;
             for (int g = lane; g < G; g += 32) {
@@ -383,68 +392,84 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512u) : "memory");
 }
 
-template <bool MAP, int NSUB>
-__global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem(const __grid_constant__ TmemArgs a) {
-    tmem_scan<MAP, false, NSUB>(a, nullptr);
+template <bool MAP, int NSUB, int MW>
+__global__ void __launch_bounds__(tm_threads(MW), 1) k_coherent_tmem(const __grid_constant__ TmemArgs a) {
+    tmem_scan<MAP, false, NSUB, MW>(a, nullptr);
 }
 
-template <bool MAP, int NSUB>
-__global__ void __launch_bounds__(kTmThreads, 1) k_coherent_tmem_pt(const __grid_constant__ TmemArgs a,
-                                                                   const __grid_constant__ TmemTab pt) {
-    tmem_scan<MAP, true, NSUB>(a, &pt);
+template <bool MAP, int NSUB, int MW>
+__global__ void __launch_bounds__(tm_threads(MW), 1) k_coherent_tmem_pt(const __grid_constant__ TmemArgs a,
+                                                                       const __grid_constant__ TmemTab pt) {
+    tmem_scan<MAP, true, NSUB, MW>(a, &pt);
 }
 
-template <int NSUB>
+template <int NSUB, int MW>
 static int launch_tmem_nsub(const TmemArgs &a, const TmemTab *tab, int grid, size_t smem, cudaStream_t stream) {
+    constexpr int NT = tm_threads(MW);
     static bool attr = false;
     if (!attr) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<false, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<true, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<false, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<true, NSUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<false, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<true, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<false, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<true, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
     if (tab && a.n_pix <= kTmTabPix && a.n_grp <= kTmTabGrp) {
         if (a.skymap)
-            k_coherent_tmem_pt<true, NSUB><<<grid, kTmThreads, smem, stream>>>(a, *tab);
+            k_coherent_tmem_pt<true, NSUB, MW><<<grid, NT, smem, stream>>>(a, *tab);
         else
-            k_coherent_tmem_pt<false, NSUB><<<grid, kTmThreads, smem, stream>>>(a, *tab);
+            k_coherent_tmem_pt<false, NSUB, MW><<<grid, NT, smem, stream>>>(a, *tab);
     } else if (a.skymap) {
-        k_coherent_tmem<true, NSUB><<<grid, kTmThreads, smem, stream>>>(a);
+        k_coherent_tmem<true, NSUB, MW><<<grid, NT, smem, stream>>>(a);
     } else {
-        k_coherent_tmem<false, NSUB><<<grid, kTmThreads, smem, stream>>>(a);
+        k_coherent_tmem<false, NSUB, MW><<<grid, NT, smem, stream>>>(a);
     }
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }
 
-size_t tmem_scan_smem(int n_pix, int n_grp, int C, int nsub) {
-    const int W0 = kTmKT + nsub * C, L = W0 / 8 + 1;
-    size_t s = (size_t)n_pix * sizeof(float4) + (size_t)n_grp * sizeof(int4) + (size_t)8 * kTmKT * sizeof(float) +
+size_t tmem_scan_smem(int n_pix, int n_grp, int C, int nsub, int mw) {
+    const int KT = kTmRows * mw, SL = tm_threads(mw) / 128;
+    const int W0 = KT + nsub * C, L = W0 / 8 + 1;
+    size_t s = (size_t)n_pix * sizeof(float4) + (size_t)n_grp * sizeof(int4) + (size_t)2 * SL * KT * sizeof(float) +
                (size_t)6 * 8 * L * sizeof(float) + ((size_t)n_pix * sizeof(uint16_t) + 15) / 16 * 16 +
-               (size_t)kTmKT * sizeof(int) + 16 + 16;
+               (size_t)KT * sizeof(int) + 16 + 16;
     return std::max(s, (size_t)kTmMinSmem);
 }
 
-int tmem_columns(int H) { return (2 * H + kTmM + 15) / 16 * 16; }
+int tmem_columns(int H, int mw) { return (2 * H + mw + 15) / 16 * 16; }
 
-bool tmem_fits(int n_pix, int n_grp, int H) {
+bool tmem_fits(int n_pix, int n_grp, int H, int mw) {
     // sized for four templates per work item (the largest staged tile)
-    return 2 * tmem_columns(H) <= kTmDet && tmem_scan_smem(n_pix, n_grp, tmem_columns(H), 4) <= 227 * 1024;
+    return 2 * tmem_columns(H, mw) <= kTmDet && tmem_scan_smem(n_pix, n_grp, tmem_columns(H, mw), 4, mw) <= 227 * 1024;
+}
+
+int tmem_templates_per_item(int64_t n, int mw) {
+    const int64_t ks = (int64_t)kTmRows * mw;  // samples of a one-template item
+    return n <= ks / 4 ? 4 : (n <= ks / 2 ? 2 : 1);
 }
 
 int launch_coherent_tmem(const TmemArgs &a, const TmemTab *tab, cudaStream_t stream) {
     if (a.nsub != 1 && a.nsub != 2 && a.nsub != 4) return fail(SPIIR_EINVAL, "templates per item = %d", a.nsub);
-    const size_t smem = tmem_scan_smem(a.n_pix, a.n_grp, a.C, a.nsub);
+    if (a.mw != 8 && a.mw != 16) return fail(SPIIR_EINVAL, "samples per row = %d", a.mw);
+    const size_t smem = tmem_scan_smem(a.n_pix, a.n_grp, a.C, a.nsub, a.mw);
     int dev = 0, n_sm = 0;
     SPIIR_CUDA_TRY(cudaGetDevice(&dev));
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t items = (int64_t)((a.n_templates + a.nsub - 1) / a.nsub) * ((a.n + kTmKT / a.nsub - 1) / (kTmKT / a.nsub));
+    const int64_t ks = (int64_t)kTmRows * a.mw / a.nsub;  // samples of one template per item
+    const int64_t items = (int64_t)((a.n_templates + a.nsub - 1) / a.nsub) * ((a.n + ks - 1) / ks);
     const int grid = (int)std::min<int64_t>(items, n_sm);
+    if (a.mw == 16) {
+        switch (a.nsub) {
+            case 1: return launch_tmem_nsub<1, 16>(a, tab, grid, smem, stream);
+            case 2: return launch_tmem_nsub<2, 16>(a, tab, grid, smem, stream);
+            default: return launch_tmem_nsub<4, 16>(a, tab, grid, smem, stream);
+        }
+    }
     switch (a.nsub) {
-        case 1: return launch_tmem_nsub<1>(a, tab, grid, smem, stream);
-        case 2: return launch_tmem_nsub<2>(a, tab, grid, smem, stream);
-        default: return launch_tmem_nsub<4>(a, tab, grid, smem, stream);
+        case 1: return launch_tmem_nsub<1, 8>(a, tab, grid, smem, stream);
+        case 2: return launch_tmem_nsub<2, 8>(a, tab, grid, smem, stream);
+        default: return launch_tmem_nsub<4, 8>(a, tab, grid, smem, stream);
     }
 }
 

@@ -95,7 +95,7 @@ def test_argmax_ties_take_lowest_pixel():
 
 
 @pytest.mark.parametrize("copies", [2, 3])
-@pytest.mark.parametrize("shape", [(512, 4, 1), (512, 4, 0), (256, 2, 1), (256, 2, 0)])
+@pytest.mark.parametrize("shape", [(512, 4, 1), (512, 4, 0), (256, 4, 1), (256, 2, 1), (256, 2, 0)])
 def test_exact_ties_across_groups_take_lowest_pixel(copies, shape):
     """Every pixel of the first third (half) has copies whose detector-0 delay is 1 or 2
     samples later, so they sit in other detector-0 groups.  Detector 0 is silent, so each pixel
@@ -337,24 +337,26 @@ def test_all_zero_window_ties_resolve_to_pixel_zero():
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
 
 
+@pytest.mark.parametrize("threads", [512, 256])
 @pytest.mark.parametrize("nside,T,n,param", [(8, 3, 2500, 1), (16, 2, 1024, 1), (16, 2, 3000, 1), (16, 2, 3000, 0),
-                                              (16, 3, 512, 1), (8, 5, 300, 1), (16, 3, 256, 1), (8, 7, 100, 0)])
-def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(nside, T, n, param):
-    """The TMEM scan (512 threads, 8 samples per row, detector 1 and 2 windows in tensor
-    memory) against the oracle, and against the shared-memory scan (the two pair the FP32
+                                              (16, 3, 512, 1), (8, 5, 300, 1), (16, 3, 256, 1), (8, 7, 100, 0),
+                                              (16, 2, 2048, 1), (8, 5, 1000, 0)])
+def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(threads, nside, T, n, param):
+    """The TMEM scan (512 threads with 8 samples per row, or 256 with 16; detector 1 and 2
+    windows in tensor memory) against the oracle, and against the shared-memory scan (the two pair the FP32
     arithmetic differently, so they agree to rounding).  n = 2500 and 3000 leave ragged last
-    tiles of 1024 samples; chunks of at most 512 (256) samples put 2 (4) templates in one work
-    item, here with template counts that leave the last item partly empty.  param: group and
+    tiles of 1024 (2048) samples; short chunks put 2 or 4 templates in one work item, here with
+    template counts that leave the last item partly empty.  param: group and
     offset tables in the kernel parameters (1) or in shared memory (0), with bit-identical
     results."""
     sky, G, d_or = _sky(1, 3, nside, (0.5, 2.0))
     H = sky.halo
     z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=21)
     ms_s, am_s, nl_s, _ = _scan(sky, z, n)
-    sky.set_scan_shape(512, 4, param)
-    assert sky.get_scan_shape() == (512, 4, param, 1)
+    sky.set_scan_shape(threads, 4, param)
+    assert sky.get_scan_shape() == (threads, 4, param, 1)
     ms, am, nl, _ = _scan(sky, z, n)
-    sky.set_scan_shape(512, 4, 1 - param)
+    sky.set_scan_shape(threads, 4, 1 - param)
     ms2, am2, nl2, _ = _scan(sky, z, n)
     assert np.array_equal(ms, ms2) and np.array_equal(am, am2) and np.array_equal(nl, nl2)
     assert np.all(np.abs(ms - ms_s) <= 1e-5 * ms_s.max())
@@ -363,9 +365,25 @@ def test_tensor_memory_scan_matches_oracle_and_shared_memory_scan(nside, T, n, p
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
 
 
-def test_tensor_memory_scan_ties_and_sky_map():
-    sky, G, d_or = _sky(1, 3, 16, (0.5, 2.0))
+@pytest.mark.parametrize("nside,T,n", [(16, 3, 2048), (8, 4, 700), (16, 5, 300)])
+def test_tensor_memory_scan_forms_agree_bit_for_bit(nside, T, n):
+    """8 samples per thread row (512 threads) and 16 (256 threads) evaluate every pixel and
+    sample with the same arithmetic, so their maxima, argmax and null agree exactly."""
+    sky, _, _ = _sky(1, 3, nside, (0.5, 2.0))
+    H = sky.halo
+    z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=90 + n)
     sky.set_scan_shape(512, 4, 1)
+    a = _scan(sky, z, n)
+    sky.set_scan_shape(256, 4, 1)
+    b = _scan(sky, z, n)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("threads", [512, 256])
+def test_tensor_memory_scan_ties_and_sky_map(threads):
+    sky, G, d_or = _sky(1, 3, 16, (0.5, 2.0))
+    sky.set_scan_shape(threads, 4, 1)
     H = sky.halo
     z = np.zeros((2, 3, 2100 + 2 * H), np.complex64)
     z[1, :, 900:] = synth.complex_gaussian_snr(1, (3, z.shape[2] - 900), sub=14)
@@ -381,9 +399,10 @@ def test_tensor_memory_scan_ties_and_sky_map():
 
 
 @pytest.mark.parametrize("n,T", [(200, 5), (512, 3)])
-def test_tensor_memory_sky_map_with_several_templates_per_item(n, T):
+@pytest.mark.parametrize("threads", [512, 256])
+def test_tensor_memory_sky_map_with_several_templates_per_item(n, T, threads):
     sky, G, d_or = _sky(1, 3, 8, (0.5, 2.0))
-    sky.set_scan_shape(512, 4, 1)
+    sky.set_scan_shape(threads, 4, 1)
     H = sky.halo
     z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=60 + n)
     ms, am, nl, mp = _scan(sky, z, n, skymap=True)
