@@ -595,6 +595,8 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop, bank):
     xi_fin = float(torch.nanmean(xf[:n_c]).item()) if n_c else None
     sp.device_status()
     sel_bytes = T * 3 * n * 8
+    Wx = 2 * Nj + 1
+    xb_bytes = n_c * 8 * (Wx + sum(min(n_sh * Wx, (n_sh - 1) * c * step + Wx) for c in (1, 2)))
     evals_fg, evals_bg = n_c * sky16.n_pix, n_c * n_sh * sky8.n_pix
     flops_bg = evals_bg * K_POINT_FLOPS
     peak_alu = 148 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -610,6 +612,12 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop, bank):
            "pixel_evaluations_per_s": (evals_fg + evals_bg) / (t_all * 1e-3),
            "select_gbs": sel_bytes / (t_sel * 1e-3) / 1e9,
            "select_frac_of_measured_hbm": (sel_bytes / (t_sel * 1e-3) / 1e9 / hbm) if hbm else None,
+           # xi^2 under the shifts: companion c of a candidate reads n_sh windows of 2 Nj + 1
+           # samples, c step apart (overlapping when c step < 2 Nj + 1), and the reference detector
+           # one window; each sample read once from HBM at best
+           "xi2_background_unique_bytes": xb_bytes,
+           "xi2_background_gbs": xb_bytes / (t_xb * 1e-3) / 1e9,
+           "xi2_background_frac_of_measured_hbm": (xb_bytes / (t_xb * 1e-3) / 1e9 / hbm) if hbm else None,
            "roofline": {"kernel": "k_points (background)", "bound": "alu",
                         "achieved": flops_bg / (t_bg * 1e-3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
                         "frac": flops_bg / (t_bg * 1e-3) / 1e12 / peak_alu,
