@@ -134,6 +134,40 @@ def test_exact_ties_across_groups_take_lowest_pixel(copies, shape):
         assert np.array_equal(mp[:, c * m:(c + 1) * m], mp[:, :m])
 
 
+@pytest.mark.parametrize("shape", [(256, 2, 1), (512, 1, 0), (512, 4, 1), (512, 4, 0), (256, 4, 1)])
+@pytest.mark.parametrize("n", [1, 3, 13])
+def test_few_output_samples(shape, n):
+    """One, three and thirteen output samples: partial thread rows and items, through every
+    kind of scan."""
+    sky, G, d_or = _sky(1, 3, 8, (0.5, 2.0))
+    sky.set_scan_shape(*shape)
+    H = sky.halo
+    z = synth.complex_gaussian_snr(1, (2, 3, n + 2 * H), sub=110 + n)
+    ms, am, nl, _ = _scan(sky, z, n)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+
+
+def test_scan_rejects_bad_arguments_and_stays_usable():
+    import torch
+    import paper_2011_06787_b300 as sp
+    sky, G, d_or = _sky(1, 3, 4, (0.5, 2.0))
+    H, n, T = sky.halo, 64, 2
+    z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=120)
+    zt = torch.from_numpy(z.astype(np.complex64)).cuda()
+    out = [torch.empty((T, n), dtype=dt, device="cuda") for dt in (torch.float32, torch.int32, torch.float32)]
+    L = sp.native.lib()
+    ptr = lambda t: sp._dev_ptr(t)
+    # n < 1, no templates, rows shorter than n + 2 H, NULL outputs
+    for T_, n_, pitch in ((T, 0, n + 2 * H), (0, n, n + 2 * H), (T, n, n + 2 * H - 1)):
+        rc = L.spiir_coherent_scan(sky._h, ptr(zt), pitch, T_, n_, ptr(out[0]), ptr(out[1]), ptr(out[2]), None, None)
+        assert rc != 0
+    assert L.spiir_coherent_scan(sky._h, ptr(zt), n + 2 * H, T, n, None, ptr(out[1]), ptr(out[2]), None, None) != 0
+    ms, am, nl, _ = _scan(sky, z, n)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+
+
 def _pipeline_stream(bank, sky, strain, chunk, host=False):
     import torch
     import paper_2011_06787_b300 as sp
