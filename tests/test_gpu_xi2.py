@@ -37,10 +37,10 @@ def test_autocorr_matches_oracle(Nj):
     np.testing.assert_allclose(A[:, Nj], 1.0, atol=1e-6)
 
 
-@pytest.mark.parametrize("Nj,n", [(3, 700), (4, 1024), (175, 2500), (60, 3000)])
+@pytest.mark.parametrize("Nj,n", [(3, 700), (4, 1024), (175, 2500), (60, 3000), (5, 1), (175, 1), (2, 9)])
 def test_xi2_matches_oracle(Nj, n):
-    """Ragged last tiles (n not a multiple of 1024) and tap counts below, at and above one
-    unrolled group of 8."""
+    """Ragged last tiles (n not a multiple of 1024), single and few output samples, and tap
+    counts below, at and above one unrolled group of 8."""
     import paper_2011_06787_b300 as sp
     T, nd = 3, 3
     A = oracle.autocorr(_responses(T, 30, 2000, seed=7), Nj).astype(np.complex64)
@@ -49,7 +49,8 @@ def test_xi2_matches_oracle(Nj, n):
     xi_or = oracle.xi2(z, A, Nj, n)
     err = np.abs(xi - xi_or) / np.maximum(np.abs(xi_or), 1.0)
     assert err.max() < XI_TOL, err.max()
-    assert 0.5 < xi_or.mean() < 2.0
+    if n >= 100:
+        assert 0.5 < xi_or.mean() < 2.0
 
 
 def test_xi2_of_a_template_shaped_window_is_near_zero():
