@@ -68,7 +68,8 @@ void spiir_debug_fail_alloc_at(int k);
 int spiir_debug_wait_timeout(uint32_t iterations, void *stream);
 
 /* Sticky device-side status: SPIIR_OK, or SPIIR_ETIMEOUT after a bounded wait inside a
- * kernel gave up.  Synchronises the device.  clear != 0 resets the word. */
+ * kernel gave up.  Synchronises the device.  clear != 0 resets the word.  The word is a
+ * file-scope device variable: neither this call nor any kernel allocates it. */
 int spiir_device_status(int clear);
 
 /* ------------------------------------------------------------------------------------
@@ -148,8 +149,11 @@ int spiir_filter_chunk(spiir_bank_t bank, const float *strain_dev, int64_t strai
  * called.  The first call on a device looks up that array's device address with the device
  * current (cudaGetSymbolAddress), so make the first call before any stream capture.
  * Every call reuses the same array: calls whose GPU work can overlap (different streams
- * without ordering) race and give wrong results; order them on one stream.  The coefficient
- * copies read the host arrays before the call returns; the rest is enqueued on stream.
+ * without ordering) race and give wrong results; order them on one stream.  Everything,
+ * including the copies of the host arrays into the array, is enqueued on stream: the host
+ * arrays must stay valid and unchanged until the stream has passed this call (for example,
+ * until cudaStreamSynchronize(stream) returns).  A bounded device wait that runs out is
+ * reported by spiir_device_status, as for every other kernel of the library.
  * Limits: n_det <= 4, n_templates <= 4096, n_filters <= 131072, n <= 65536, delays <= 8192,
  * and the packed problem must fit in the array; otherwise SPIIR_EUNSUPPORTED with the limit
  * in spiir_last_error().  Invalid values: SPIIR_EINVAL as in spiir_bank_create. */
@@ -238,7 +242,7 @@ int spiir_coherent_scan(spiir_sky_t sky, const float *snr_dev, int64_t snr_pitch
  * R[j] = sum_k conj(u[k]) u[k + j], A[-j] = conj(A[j])); the SNR is taken as normalised
  * (E|z|^2 = 2 in noise), so the statistic is a reduced chi-square of mean 1.  The network
  * value is xi_C^2 = (1 / N_d) sum_I xi_I^2, each detector read at its arrival time for the
- * coherent argmax pixel.  Nj ("n_lags") is typically 175 (Sec. IV); at most 1024.
+ * coherent argmax pixel.  Nj ("n_lags") is typically 175 (Sec. III.D); at most 1024.
  * ---------------------------------------------------------------------------------- */
 
 /* A_dev [T][2 n_lags + 1] complex (entry n_lags + j is lag j) from the responses

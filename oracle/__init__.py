@@ -493,8 +493,8 @@ def select_candidates(z, off: int, n: int, threshold: float = 4.0, per_second: i
 
     Every comparison is made on |z|^2 in FP32, re*re + im*im with each operation rounded, against
     threshold^2 rounded the same way (the values the GPU decides on; equal values are equal on
-    both sides).  Returns a list of (detector, template, sample, |z|) sorted by detector, then
-    template, then second; |z| is the square root, in FP64, of that FP32 |z|^2."""
+    both sides).  Returns a list of (detector, template, sample, |z|^2) sorted by detector, then
+    template, then second; |z|^2 is that FP32 value."""
     z = np.asarray(z)
     T, n_det, _ = z.shape
     thr2 = np.float32(threshold) * np.float32(threshold)
@@ -511,7 +511,7 @@ def select_candidates(z, off: int, n: int, threshold: float = 4.0, per_second: i
             if key not in kept or best[k] > best[kept[key]]:
                 kept[key] = int(k)
         for (t, _), k in sorted(kept.items()):
-            out.append((I, t, k, float(np.sqrt(np.float64(best[k])))))
+            out.append((I, t, k, float(best[k])))
     return out
 
 

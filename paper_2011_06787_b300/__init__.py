@@ -423,11 +423,12 @@ class Selector:
 
     @staticmethod
     def records(cand, n_cand):
-        """Host copy of the records as a list of (detector, template, sample, |z|) (synchronises)."""
+        """Host copy of the records as a list of (detector, template, sample, |z|^2), the last the
+        FP32 value the selection stored (synchronises)."""
         n = min(int(n_cand.item()), cand.shape[0])
         c = cand[:n].cpu().numpy()
-        m2 = c[:, 3].copy().view(np.float32).astype(np.float64)
-        return [(int(a), int(b), int(k), float(np.sqrt(v))) for (a, b, k), v in zip(c[:, :3], m2)]
+        m2 = c[:, 3].copy().view(np.float32)
+        return [(int(a), int(b), int(k), float(v)) for (a, b, k), v in zip(c[:, :3], m2)]
 
 
 def coherent_candidates(sky, snr, offset: int, cand, n_cand, first_shift: int = 0, n_shifts: int = 1,

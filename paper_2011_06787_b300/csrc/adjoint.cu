@@ -548,15 +548,12 @@ extern "C" int spiir_impulse_forward(int T, int F, const float *a1, const float 
         const size_t smem = (size_t)nt * (kAdjR + 1) * sizeof(float2) + (size_t)(nt / 32) * kAdjR * sizeof(float2);
         const dim3 grid((unsigned)nck, (unsigned)T);
         float2 *U = reinterpret_cast<float2 *>(u);
-        static bool attr = false;
-        if (!attr) {  // up to 256 threads x 33 float2 of reduction rows: above the 48 KB default
-            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-            SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_fwd_seg<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-            attr = true;
-        }
+        // up to 256 threads x 33 float2 of reduction rows: above the 48 KB default
+        SPIIR_TRY(set_max_dyn_smem((const void *)k_fwd_seg<2>, 100 * 1024));
+        SPIIR_TRY(set_max_dyn_smem((const void *)k_fwd_seg<4>, 100 * 1024));
+        SPIIR_TRY(set_max_dyn_smem((const void *)k_fwd_seg<6>, 100 * 1024));
+        SPIIR_TRY(set_max_dyn_smem((const void *)k_fwd_seg<8>, 100 * 1024));
+        SPIIR_TRY(set_max_dyn_smem((const void *)k_fwd_seg<10>, 100 * 1024));
         switch (S) {
             case 2: k_fwd_seg<2><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
             case 4: k_fwd_seg<4><<<grid, nt, smem, st>>>(A, B, delay, F, n, C, nck, CK, U); break;
@@ -573,11 +570,7 @@ extern "C" int spiir_impulse_forward(int T, int F, const float *a1, const float 
     if (smem > 227 * 1024)
         return fail(SPIIR_EUNSUPPORTED, "%d filters per template need a checkpoint buffer (the sequential form "
                                         "fits %d)", F, 227 * 1024 / ((kAdjR + 1) * (int)sizeof(float2)) / 32 * 32);
-    static bool attr_seq = false;
-    if (!attr_seq) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_impulse_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr_seq = true;
-    }
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_impulse_fwd, 227 * 1024));
     k_impulse_fwd<<<T, nt, smem, st>>>(A, B, delay, S0, F, n, kAdjR, reinterpret_cast<float2 *>(u), nullptr, 1);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
@@ -606,12 +599,8 @@ extern "C" int spiir_impulse_backward(int T, int F, const float *a1, const float
     auto GA = reinterpret_cast<float2 *>(grad_a1);
     auto GB = reinterpret_cast<float2 *>(grad_b0);
     auto GS = reinterpret_cast<float2 *>(grad_s0);
-    static bool attr = false;
-    if (!attr) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_bwd_local, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_bwd_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr = true;
-    }
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_bwd_local, 227 * 1024));
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_bwd_seg, 227 * 1024));
     const int ntl = 128;  // filter pairs per block of the local pass
     k_bwd_local<<<dim3((unsigned)nck, (unsigned)T, (unsigned)((F + 2 * ntl - 1) / (2 * ntl))), ntl,
                   (size_t)C * sizeof(float4), st>>>(A, F, n, C, nck, G, W);

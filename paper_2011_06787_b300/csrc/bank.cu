@@ -271,12 +271,7 @@ __global__ void __launch_bounds__(NL, 1) k_filter_bank_persistent(const __grid_c
 
 template <int S, int NL, int R>
 static int launch_bank(const BankArgs &a, int n_cta, int n_det, size_t smem, cudaStream_t stream) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_filter_bank<S, NL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kBankMaxSmem));
-        attr_set = true;
-    }
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_filter_bank<S, NL, R>, kBankMaxSmem));
     k_filter_bank<S, NL, R><<<dim3(n_cta, n_det), NL, smem, stream>>>(a);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
@@ -885,34 +880,30 @@ extern "C" int spiir_bank_get_shape(spiir_bank_t b, int *filters_per_lane, int *
 // memory, or in a process that must not grow its footprint after start-up).  This entry
 // point runs the same filter-bank kernel as spiir_filter_chunk on one segment that starts a
 // stream (zero IIR states, zero strain history), with every piece of scratch -- the copied
-// coefficients, their packed layout, the block tables, the IIR states, the strain window
-// and a status word -- carved out of one file-scope device array of fixed size.  The array
-// exists on every GPU that loads the library, for the life of the process.  All calls share
-// it, so calls whose GPU work overlaps (different streams, no ordering) race and corrupt
-// each other's results.
+// coefficients, their packed layout, the block tables, the IIR states and the strain window
+// -- carved out of one file-scope device array of fixed size.  The array exists on every GPU
+// that loads the library, for the life of the process.  All calls share it, so calls whose
+// GPU work overlaps (different streams, no ordering) race and corrupt each other's results.
+// A bounded wait that runs out is recorded in the library's status word (itself a file-scope
+// device variable), which spiir_device_status reports.
 
 namespace spiir {
 
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-static std::mutex g_static_mu;
-static void *g_static_addr[64];
 
-// Device address of the scratch array on the current device.  Looked up once per device,
-// on the first call made with that device current.
+// Device address of the scratch array in the current device's context.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with the device
+// current -- on every call, which is cheap once the module is loaded and stays right after
+// the context has been re-created.
 static int static_scratch_address(unsigned char **out) {
-    int dev = 0;
-    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(SPIIR_EUNSUPPORTED, "device index %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(SPIIR_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-        g_static_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return fail(SPIIR_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
     }
-    *out = static_cast<unsigned char *>(g_static_addr[dev]);
+    *out = static_cast<unsigned char *>(p);
     return SPIIR_OK;
 }
 
@@ -1054,7 +1045,6 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     const size_t o_segs = take(sizeof(int4) * n_templates), o_so = take(sizeof(int) * (n_cta + 1));
     const size_t o_wf = take(sizeof(int) * n_cta * (NL / 32)), o_act = take(sizeof(int) * n_cta);
     const size_t o_x = take(sizeof(float) * xpitch * n_det);
-    const size_t o_status = take(sizeof(int));
     if (cur > kStaticScratchBytes)
         return fail(SPIIR_EUNSUPPORTED, "problem needs %zu bytes of scratch; the static array holds %zu", cur,
                     kStaticScratchBytes);
@@ -1064,6 +1054,8 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     if (smem > (size_t)kBankMaxSmem) return fail(SPIIR_EUNSUPPORTED, "strain window does not fit in shared memory");
     unsigned char *base = nullptr;
     SPIIR_TRY(static_scratch_address(&base));
+    int *status = device_status_word();
+    if (!status) return fail(SPIIR_ECUDA, "device status word unavailable");
     // inputs into the scratch, packed region and strain window cleared
     SPIIR_CUDA_TRY(cudaMemcpyAsync(base + o_off, off, sizeof(int64_t) * (n_templates + 1), cudaMemcpyHostToDevice, st));
     if (F > 0) {
@@ -1073,7 +1065,6 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     }
     SPIIR_CUDA_TRY(cudaMemsetAsync(base + o_pk, 0, pk_bytes, st));
     SPIIR_CUDA_TRY(cudaMemsetAsync(base + o_x, 0, sizeof(float) * xpitch * n_det, st));
-    SPIIR_CUDA_TRY(cudaMemsetAsync(base + o_status, 0, sizeof(int), st));
     SPIIR_CUDA_TRY(cudaMemcpy2DAsync(reinterpret_cast<float *>(base + o_x) + D_pad, xpitch * sizeof(float), strain,
                                      strain_pitch * sizeof(float), n * sizeof(float), n_det, cudaMemcpyDeviceToDevice,
                                      st));
@@ -1112,7 +1103,7 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     a.z = reinterpret_cast<float2 *>(snr);
     a.zpitch = snr_pitch;
     a.n_det = n_det;
-    a.status = reinterpret_cast<int *>(base + o_status);
+    a.status = status;
     a.n_cta_total = n_cta;
     a.n_pairs_total = npair;
     a.x_elems = xpitch * n_det;

@@ -562,37 +562,22 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
 }
 
 // Resident blocks of a kernel for a dynamic shared-memory size (the opt-in limit is raised to
-// max_smem once per kernel and device; the last query is cached).
-struct LaunchCache {
-    int dev = -1, n_sm = 0;
-    size_t smem = 0;
-    int per_sm = 0;
-};
+// max_smem once per kernel and device; both queries are cached per device).
 template <typename K>
-static int resident_blocks(LaunchCache &c, K kern, int threads, size_t smem, int max_smem, int &n_sm, int &per_sm) {
+static int resident_blocks(K kern, int threads, size_t smem, int max_smem, int &n_sm, int &per_sm) {
     int dev = 0;
     SPIIR_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != c.dev) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-        SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev));
-        c.dev = dev;
-        c.smem = (size_t)-1;
-    }
-    if (smem != c.smem) {
-        SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, kern, threads, smem));
-        c.smem = smem;
-    }
-    n_sm = c.n_sm;
-    per_sm = c.per_sm;
+    SPIIR_TRY(set_max_dyn_smem((const void *)kern, max_smem));
+    SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    SPIIR_TRY(resident_blocks_per_sm((const void *)kern, threads, smem, &per_sm));
     return SPIIR_OK;
 }
 
 template <int ND, int S>
 static int launch_chunked(const PointArgs &a, size_t smem, cudaStream_t stream) {
     auto kern = k_points_chunked<ND, S>;
-    static LaunchCache cache;
     int n_sm = 0, per_sm = 0;
-    SPIIR_TRY(resident_blocks(cache, kern, kPtThreads, smem, kPtChunkSmem, n_sm, per_sm));
+    SPIIR_TRY(resident_blocks(kern, kPtThreads, smem, kPtChunkSmem, n_sm, per_sm));
     const int64_t items = (int64_t)a.max_cand * ((a.n_shifts + S - 1) / S);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
     kern<<<grid, kPtThreads, smem, stream>>>(a);
@@ -617,9 +602,8 @@ static int dispatch_chunked(const PointArgs &a, cudaStream_t stream) {
 template <int ND, bool SMEM_TAB>
 static int launch_points(const PointArgs &a, size_t smem, cudaStream_t stream) {
     auto kern = k_points<ND, SMEM_TAB>;
-    static LaunchCache cache;
     int n_sm = 0, per_sm = 0;
-    SPIIR_TRY(resident_blocks(cache, kern, kPtThreads, smem, kPtMaxSmem, n_sm, per_sm));
+    SPIIR_TRY(resident_blocks(kern, kPtThreads, smem, kPtMaxSmem, n_sm, per_sm));
     const int64_t items = (int64_t)a.max_cand * a.n_shifts;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
     kern<<<grid, kPtThreads, smem, stream>>>(a);

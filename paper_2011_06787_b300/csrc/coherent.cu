@@ -379,15 +379,10 @@ __global__ void __launch_bounds__(TPB) k_coherent_grouped(const __grid_constant_
 template <int ND, bool TAB_SMEM, bool MAP, int TPB, int PPT>
 static int launch_grouped(const GroupedArgs &a, size_t smem, cudaStream_t stream) {
     auto kern = k_coherent_grouped<ND, TAB_SMEM, MAP, TPB, PPT>;
-    static int blocks_per_sm = -1;
-    static size_t smem_seen = 0;
-    if (blocks_per_sm < 0 || smem_seen != smem) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        int nb = 0;
-        SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TPB, smem));
-        blocks_per_sm = std::max(1, nb);
-        smem_seen = smem;
-    }
+    SPIIR_TRY(set_max_dyn_smem((const void *)kern, 227 * 1024));
+    int blocks_per_sm = 0;
+    SPIIR_TRY(resident_blocks_per_sm((const void *)kern, TPB, smem, &blocks_per_sm));
+    blocks_per_sm = std::max(1, blocks_per_sm);
     int dev = 0, n_sm = 0;
     SPIIR_CUDA_TRY(cudaGetDevice(&dev));
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -420,15 +415,10 @@ static int dispatch_grouped(const GroupedArgs &a, int tpb, int ppt, bool tab_sme
 template <int ND, bool SMEM_TAB, bool MAP>
 static int launch_coh(const CohArgs &a, size_t smem, cudaStream_t stream) {
     auto kern = k_coherent<ND, SMEM_TAB, MAP>;
-    static int blocks_per_sm = -1;
-    static size_t smem_seen = 0;
-    if (blocks_per_sm < 0 || smem_seen != smem) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        int nb = 0;
-        SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kCohThreads, smem));
-        blocks_per_sm = std::max(1, nb);
-        smem_seen = smem;
-    }
+    SPIIR_TRY(set_max_dyn_smem((const void *)kern, 227 * 1024));
+    int blocks_per_sm = 0;
+    SPIIR_TRY(resident_blocks_per_sm((const void *)kern, kCohThreads, smem, &blocks_per_sm));
+    blocks_per_sm = std::max(1, blocks_per_sm);
     int dev = 0, n_sm = 0;
     SPIIR_CUDA_TRY(cudaGetDevice(&dev));
     SPIIR_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));

@@ -406,14 +406,10 @@ __global__ void __launch_bounds__(tm_threads(MW), 1) k_coherent_tmem_pt(const __
 template <int NSUB, int MW>
 static int launch_tmem_nsub(const TmemArgs &a, const TmemTab *tab, int grid, size_t smem, cudaStream_t stream) {
     constexpr int NT = tm_threads(MW);
-    static bool attr = false;
-    if (!attr) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<false, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem<true, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<false, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_coherent_tmem_pt<true, NSUB, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr = true;
-    }
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_coherent_tmem<false, NSUB, MW>, 227 * 1024));
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_coherent_tmem<true, NSUB, MW>, 227 * 1024));
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_coherent_tmem_pt<false, NSUB, MW>, 227 * 1024));
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_coherent_tmem_pt<true, NSUB, MW>, 227 * 1024));
     if (tab && a.n_pix <= kTmTabPix && a.n_grp <= kTmTabGrp) {
         if (a.skymap)
             k_coherent_tmem_pt<true, NSUB, MW><<<grid, NT, smem, stream>>>(a, *tab);

@@ -2,8 +2,11 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -77,23 +80,49 @@ void host_free_pinned(void *p) {
     if (p) cudaFreeHost(p);
 }
 
-static std::mutex g_status_mu;
-static int *g_status[64];
+// The sticky status word is a file-scope device variable: reading or clearing it allocates
+// nothing.  Its device address is looked up on every call, so that it stays right after the
+// context of the current device has been re-created.
+static __device__ int g_status_word;
 
 int *device_status_word() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lk(g_status_mu);
-    if (!g_status[dev]) {
-        int *p = nullptr;
-        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        cudaMemset(p, 0, sizeof(int));
-        g_status[dev] = p;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return g_status[dev];
+    return static_cast<int *>(p);
+}
+
+static std::mutex g_attr_mu;
+static std::set<std::tuple<int, const void *, int>> g_attr_done;
+
+int set_max_dyn_smem(const void *func, int bytes) {
+    int dev = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const auto key = std::make_tuple(dev, func, bytes);
+    if (g_attr_done.count(key)) return SPIIR_OK;
+    SPIIR_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    g_attr_done.insert(key);
+    return SPIIR_OK;
+}
+
+static std::map<std::tuple<int, const void *, int, size_t>, int> g_occupancy;
+
+int resident_blocks_per_sm(const void *func, int threads, size_t smem, int *out) {
+    int dev = 0;
+    SPIIR_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const auto key = std::make_tuple(dev, func, threads, smem);
+    auto it = g_occupancy.find(key);
+    if (it == g_occupancy.end()) {
+        int nb = 0;
+        SPIIR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, smem));
+        it = g_occupancy.emplace(key, nb).first;
+    }
+    *out = it->second;
+    return SPIIR_OK;
 }
 
 }  // namespace spiir

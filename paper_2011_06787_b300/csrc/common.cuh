@@ -21,8 +21,15 @@ void dev_free(void *p);
 int host_alloc_pinned(void **p, size_t bytes, const char *what);
 void host_free_pinned(void *p);
 
-// Sticky status word of the current device (allocated on first use).
+// Sticky status word of the current device (a file-scope device variable; nothing is
+// allocated).  NULL if its address cannot be found.
 int *device_status_word();
+
+// Raise a kernel's dynamic shared-memory limit to `bytes`, once per (device, kernel, bytes);
+// safe to call from several host threads.
+int set_max_dyn_smem(const void *func, int bytes);
+// Resident blocks per SM of a kernel at a launch shape, cached per (device, kernel, shape).
+int resident_blocks_per_sm(const void *func, int threads, size_t smem, int *out);
 
 // Maximum iterations of any bounded device-side wait before it gives up.
 constexpr uint32_t kWaitLimit = 1u << 26;

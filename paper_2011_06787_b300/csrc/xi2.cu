@@ -463,12 +463,8 @@ extern "C" int spiir_xi2(int T, int n_det, const float *snr, int64_t snr_pitch, 
     const int ntap = 2 * n_lags + 1;
     const int L = xi_plane_stride(n_lags) <= kXiLSmall ? kXiLSmall : kXiLMax;
     const size_t smem = (size_t)ntap * sizeof(float4) + (size_t)8 * L * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_xi2<kXiLSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-        SPIIR_CUDA_TRY(cudaFuncSetAttribute(k_xi2<kXiLMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-        attr = true;
-    }
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_xi2<kXiLSmall>, 100 * 1024));
+    SPIIR_TRY(set_max_dyn_smem((const void *)k_xi2<kXiLMax>, 100 * 1024));
     const dim3 grid((unsigned)((n + kXiKT - 1) / kXiKT), (unsigned)n_det, (unsigned)T);
     auto kern = L == kXiLSmall ? k_xi2<kXiLSmall> : k_xi2<kXiLMax>;
     kern<<<grid, kXiThreads, smem, (cudaStream_t)stream>>>(reinterpret_cast<const float2 *>(snr), snr_pitch,

@@ -114,7 +114,7 @@ def test_selection_of_quiet_data_is_empty_and_repeatable():
     for _ in range(2):  # the workspace is zero again after each call
         cand, cnt = sel.select(zt, 0, 4.0)
         torch.cuda.synchronize()
-        assert sp.Selector.records(cand, cnt) == [(1, 5, 1234, 9.0)]
+        assert sp.Selector.records(cand, cnt) == [(1, 5, 1234, 81.0)]
 
 
 def test_nan_snr_is_never_a_candidate():

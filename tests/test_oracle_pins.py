@@ -660,7 +660,7 @@ def test_candidate_selection_on_constructed_peaks():
     expect = [(0, 0, 900, 6.0), (0, 1, 300, 7.0), (0, 2, 1000, 5.0), (0, 3, 700, 5.5), (0, 3, 2100, 6.0),
               (1, 1, 2047, 4.5), (1, 1, 2048, 4.6)]
     assert [(a, b, c) for a, b, c, _ in got] == [(a, b, c) for a, b, c, _ in expect]
-    np.testing.assert_allclose([v for *_, v in got], [v for *_, v in expect], rtol=1e-6)
+    np.testing.assert_allclose([v for *_, v in got], [v * v for *_, v in expect], rtol=1e-6)
 
 
 def test_candidate_threshold_is_decided_in_fp32():
