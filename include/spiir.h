@@ -88,9 +88,12 @@ int spiir_device_status(int clear);
  *   b0_host [2 F]   feedforward coefficients (re, im), finite.
  *   delay_host [F]  integer delays d_l in samples, 0 <= d_l <= 1<<20.
  * The coefficients are copied; the bank owns its IIR states (all zero) and a strain
- * history of max(d_l) samples per detector (zero).  Errors: SPIIR_EINVAL for bad
- * shapes or values, SPIIR_EUNSUPPORTED when one template has more filters than one
- * thread block can hold (4096 in this build), SPIIR_ENOMEM, SPIIR_ECUDA. */
+ * history of max(d_l) samples per detector (zero).  A bank whose largest delay is at least
+ * 16384 samples is cut into delay bins of 16384 samples (see spiir_bank_set_delay_bin), so
+ * long templates (a 74 s chirp from 30 Hz spans about 151k samples at 2048 Hz) fit.
+ * Errors: SPIIR_EINVAL for bad shapes or values, SPIIR_EUNSUPPORTED when one template has
+ * more filters than one thread block can hold (4096 in this build), SPIIR_ENOMEM,
+ * SPIIR_ECUDA. */
 int spiir_bank_create(int n_det, int n_templates, const int64_t *filter_offsets_host,
                       const float *a1_host, const float *b0_host, const int32_t *delay_host,
                       spiir_bank_t *out);
@@ -125,6 +128,21 @@ int spiir_bank_set_shape(spiir_bank_t bank, int filters_per_lane, int lanes_per_
                          int steps_per_reduce, int tile);
 int spiir_bank_get_shape(spiir_bank_t bank, int *filters_per_lane, int *lanes_per_block,
                          int *steps_per_reduce, int *tile);
+
+/* Delay bins (a layout knob for long templates; results do not depend on it beyond the order
+ * of floating-point summation).  Each thread block stages one strain window per time tile that
+ * covers the delays of its own filters.  With delay_bin = B > 0 the filters of template t whose
+ * delays lie in [jB, (j+1)B) form piece j of t; blocks hold pieces of one bin only, so a
+ * window spans at most B + tile samples.  A template's first piece writes its SNR row, its
+ * later pieces write rows of a bank-owned buffer that one more launch adds into the SNR, in
+ * bin order: z_t = sum_j z_t^(j).  delay_bin = 0 keeps every template whole (one window of the
+ * bank's largest delay).  B is 0 or a multiple of 4 in [1024, 1<<20].  Keeps the streaming
+ * state; synchronises the device.  Default: 0 below a largest delay of 16384, else 16384.
+ * get: the bin width, the number of thread blocks and of pieces (templates + extra pieces).
+ * Errors: SPIIR_EINVAL; SPIIR_EUNSUPPORTED when a window does not fit in shared memory (the
+ * bank keeps its previous layout). */
+int spiir_bank_set_delay_bin(spiir_bank_t bank, int32_t delay_bin);
+int spiir_bank_get_delay_bin(spiir_bank_t bank, int32_t *delay_bin, int *n_blocks, int *n_pieces);
 
 /* Filter one chunk of strain and advance the streaming state.
  *   strain_dev [n_det][strain_pitch] float; samples 0..n-1 of each row are this chunk,

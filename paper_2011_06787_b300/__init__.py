@@ -113,6 +113,16 @@ class Bank:
         check(native.lib().spiir_bank_get_shape(self._h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
 
+    def set_delay_bin(self, delay_bin: int):
+        """Delay-bin width of the block layout (spiir_bank_set_delay_bin); 0 keeps templates whole."""
+        check(native.lib().spiir_bank_set_delay_bin(self._h, int(delay_bin)))
+
+    def get_delay_bin(self):
+        """(delay-bin width, thread blocks, delay pieces) of the current layout."""
+        v = [ctypes.c_int32(), ctypes.c_int(), ctypes.c_int()]
+        check(native.lib().spiir_bank_get_delay_bin(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     def state_bytes(self) -> int:
         n = ctypes.c_size_t()
         check(native.lib().spiir_bank_state_bytes(self._h, ctypes.byref(n)))

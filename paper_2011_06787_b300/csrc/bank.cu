@@ -100,25 +100,29 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
         yre[p] = pack2(y.x, y.y);
         yim[p] = pack2(y.z, y.w);
     }
+    // the block's strain window: x[k0 - dhi, k0 - dhi + span + nt) of each tile (dhi, span
+    // multiples of 4), which holds every delayed sample its filters read
+    const int2 win = a.cta_win[cta];
 #pragma unroll
-    for (int s = 0; s < S; ++s) dof[s] = a.D_pad - a.delay[((int64_t)cta * S + s) * NL + tid];
+    for (int s = 0; s < S; ++s) dof[s] = win.x - a.delay[((int64_t)cta * S + s) * NL + tid];
 
     // segment tables of this block
     const int seg0 = a.seg_off[cta];
     const int nseg = a.seg_off[cta + 1] - seg0;
     const int wfirst = a.wfirst[cta * NW + warp];
-    const float *xsrc = a.xbuf + (int64_t)det * a.xpitch;
+    const float *xsrc = a.xbuf + (int64_t)det * a.xpitch + (a.D_pad - win.x);
 
     for (int64_t k0 = 0; k0 < a.n; k0 += a.c_tile) {
         const int nt = (int)min((int64_t)a.c_tile, a.n - k0);
-        const uint32_t bytes = (uint32_t)(a.D_pad + ((nt + 3) & ~3)) * 4u;
+        const uint32_t bytes = (uint32_t)(win.y + ((nt + 3) & ~3)) * 4u;
 #ifdef SPIIR_CHECKED
         {
             int bad = 0;
-            if ((int64_t)det * a.xpitch + k0 + bytes / 4 > a.x_elems) bad = 4;
+            if (win.x > a.D_pad || win.y > win.x || win.y < 0) bad = 9;
+            if ((int64_t)det * a.xpitch + (a.D_pad - win.x) + k0 + bytes / 4 > a.x_elems) bad = 4;
             if (kBankSmemHead + bytes > a.red_offset) bad = 5;
             for (int s = 0; s < S; ++s)
-                if (dof[s] < 0 || dof[s] > a.D_pad) bad = 6;
+                if (dof[s] < 0 || dof[s] > win.y) bad = 6;
             if (__syncthreads_or(bad)) {
                 if (bad) report_bounds(a.status, bad);
                 return false;
@@ -214,9 +218,12 @@ __device__ __forceinline__ bool bank_block(const BankArgs &a, const int cta, con
                 u64 acc = 0;
                 for (int w = g.y >> 5; w <= (g.z - 1) >> 5; ++w)
                     acc = add2(acc, red2[(w * 32 + (sg - a.wfirst[cta * NW + w])) * bank_red_stride(R) + r]);
-                float2 *zrow = a.z + ((int64_t)g.x * a.n_det + det) * a.zpitch;
+                // a template's first delay piece writes z; its later pieces write zpart rows
+                float2 *zrow = g.w ? a.zpart + ((int64_t)g.x * a.n_det + det) * a.zpart_pitch
+                                   : a.z + ((int64_t)g.x * a.n_det + det) * a.zpitch;
 #ifdef SPIIR_CHECKED
-                if (((int64_t)g.x * a.n_det + det) * a.zpitch + k0 + kb + r >= a.z_elems) {
+                if (g.w ? ((int64_t)g.x * a.n_det + det) * a.zpart_pitch + k0 + kb + r >= a.zpart_elems
+                        : ((int64_t)g.x * a.n_det + det) * a.zpitch + k0 + kb + r >= a.z_elems) {
                     report_bounds(a.status, 7);
                     continue;
                 }
@@ -301,7 +308,7 @@ static int launch_bank_any(const spiir_bank_s *b, const BankArgs &a, size_t smem
 }
 
 size_t bank_red_offset(const spiir_bank_s *b) {
-    return kBankSmemHead + (size_t)(((b->D_pad + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
+    return kBankSmemHead + (size_t)(((b->win_max + b->c_tile + 3) / 4) * 4 * sizeof(float) + 127) / 128 * 128;
 }
 
 size_t bank_smem_bytes(const spiir_bank_s *b) {
@@ -311,29 +318,42 @@ size_t bank_smem_bytes(const spiir_bank_s *b) {
 // ---------------------------------------------------------------------------------------
 // Host: packing
 
-// Place the filters of the templates of block c into (lane, slot) cells.  In the kernel, the
+// A delay piece: the filters of one template whose delays fall in one delay bin.  A bank
+// without bins has one piece per template.  The first piece of a template writes the
+// template's z row; its later pieces write rows of zpart, added into z after the launch.
+struct Piece {
+    int t = 0;                   // template
+    int row = 0;                 // z row (w = 0) or zpart row (w = 1)
+    int w = 0;
+    std::vector<int64_t> filt;   // filter indices, ascending
+    int lanes = 1;
+};
+
+// Place the filters of the pieces of block c into (lane, slot) cells.  In the kernel, the
 // 32 lanes of a warp load x[k - d] for the same slot in one shared-memory instruction; two
 // different delays with the same residue mod 32 hit the same bank and serialise.  Rows
 // (warp, slot) are therefore filled greedily with distinct residues: each cell takes a filter
-// of its own template from the residue class with the most filters left that is still free in
-// the row, most loaded templates first.  When every remaining residue of a template is taken
-// in the row, the cell stays empty (zero coefficients) if the template has spare cells, and
-// otherwise accepts a conflict.  Empty cells reuse a delay already read in the row, so they
-// cost no extra bank access.
-static void assign_cells(spiir_bank_s *b, int c, const std::vector<int> &lane_t, const std::vector<int> &members) {
+// of its own piece from the residue class with the most filters left that is still free in
+// the row, most loaded pieces first.  When every remaining residue of a piece is taken
+// in the row, the cell stays empty (zero coefficients) if the piece has spare cells, and
+// otherwise accepts a conflict.  Empty cells reuse a delay already read in the row (dfill,
+// a delay of the block, when the row has none), so they cost no extra bank access and stay
+// inside the block's window.
+static void assign_cells(spiir_bank_s *b, int c, const std::vector<int> &lane_p, const std::vector<Piece> &pcs,
+                         const std::vector<int> &members, int32_t dfill) {
     const int S = b->S, NL = b->NL, NP = S / 2;
-    std::map<int, std::vector<std::vector<int64_t>>> pools;  // template -> residue -> filters
+    std::map<int, std::vector<std::vector<int64_t>>> pools;  // piece -> residue -> filters
     std::map<int, int64_t> rem_f, rem_c;
-    for (int t : members) {
-        auto &P = pools[t];
+    for (int q : members) {
+        auto &P = pools[q];
         P.assign(32, {});
-        for (int64_t l = b->offsets[t]; l < b->offsets[t + 1]; ++l) P[b->delay[l] & 31].push_back(l);
+        for (int64_t l : pcs[q].filt) P[b->delay[l] & 31].push_back(l);
         // pop from the back: keep a deterministic order within a residue class
         for (auto &v : P) std::reverse(v.begin(), v.end());
-        rem_f[t] = b->offsets[t + 1] - b->offsets[t];
+        rem_f[q] = (int64_t)pcs[q].filt.size();
         int64_t ln = 0;
-        for (int j = 0; j < NL; ++j) ln += (lane_t[j] == t);
-        rem_c[t] = ln * S;
+        for (int j = 0; j < NL; ++j) ln += (lane_p[j] == q);
+        rem_c[q] = ln * S;
     }
     auto place = [&](int ln, int s, int64_t l, int32_t d) {
         const int64_t slot = ((int64_t)c * S + s) * NL + ln;
@@ -354,21 +374,21 @@ static void assign_cells(spiir_bank_s *b, int c, const std::vector<int> &lane_t,
         for (int w = 0; w < NL / 32; ++w) {
             std::vector<int> ls;
             for (int j = 32 * w; j < 32 * w + 32; ++j)
-                if (lane_t[j] >= 0) ls.push_back(j);
+                if (lane_p[j] >= 0) ls.push_back(j);
             if (ls.empty()) continue;
             std::stable_sort(ls.begin(), ls.end(), [&](int x, int y) {
-                const int tx = lane_t[x], ty = lane_t[y];
-                return (double)rem_f[tx] / std::max<int64_t>(1, rem_c[tx]) >
-                       (double)rem_f[ty] / std::max<int64_t>(1, rem_c[ty]);
+                const int qx = lane_p[x], qy = lane_p[y];
+                return (double)rem_f[qx] / std::max<int64_t>(1, rem_c[qx]) >
+                       (double)rem_f[qy] / std::max<int64_t>(1, rem_c[qy]);
             });
             uint32_t used = 0;
             int32_t row_delay = -1;
             std::vector<int> empty;
             for (int ln : ls) {
-                const int t = lane_t[ln];
-                auto &P = pools[t];
-                rem_c[t] -= 1;
-                if (rem_f[t] == 0) {
+                const int q = lane_p[ln];
+                auto &P = pools[q];
+                rem_c[q] -= 1;
+                if (rem_f[q] == 0) {
                     empty.push_back(ln);
                     continue;
                 }
@@ -376,7 +396,7 @@ static void assign_cells(spiir_bank_s *b, int c, const std::vector<int> &lane_t,
                 for (int r = 0; r < 32; ++r)
                     if (!P[r].empty() && !(used >> r & 1u) && (best < 0 || P[r].size() > P[best].size())) best = r;
                 if (best < 0) {
-                    if (rem_f[t] <= rem_c[t]) {
+                    if (rem_f[q] <= rem_c[q]) {
                         empty.push_back(ln);
                         continue;
                     }
@@ -385,54 +405,90 @@ static void assign_cells(spiir_bank_s *b, int c, const std::vector<int> &lane_t,
                 }
                 const int64_t l = P[best].back();
                 P[best].pop_back();
-                rem_f[t] -= 1;
+                rem_f[q] -= 1;
                 used |= 1u << best;
                 if (row_delay < 0) row_delay = b->delay[l];
                 place(ln, s, l, b->delay[l]);
             }
-            for (int ln : empty) place(ln, s, -1, row_delay < 0 ? 0 : row_delay);
+            for (int ln : empty) place(ln, s, -1, row_delay < 0 ? dfill : row_delay);
             // unused lanes of a busy warp run zero filters too: read the same address
             for (int j = 32 * w; j < 32 * w + 32; ++j)
-                if (lane_t[j] < 0) place(j, s, -1, row_delay < 0 ? 0 : row_delay);
+                if (lane_p[j] < 0) place(j, s, -1, row_delay < 0 ? dfill : row_delay);
         }
     }
 }
 
+// Cut the templates into delay pieces (one per template without bins) and pack the pieces of
+// each bin into blocks, best-fit decreasing: no piece straddles two blocks, and a block holds
+// one bin only, so its window spans at most the bin width plus the tile.
 int bank_pack(spiir_bank_s *b) {
     const int T = b->T;
     const int S = b->S;
     const int NL = b->NL;
     const int NW = NL / 32;
-    std::vector<int> lanes(T);
     for (int t = 0; t < T; ++t) {
         const int64_t f = b->offsets[t + 1] - b->offsets[t];
-        lanes[t] = (int)std::max<int64_t>(1, (f + S - 1) / S);
-        if (lanes[t] > NL)
+        if ((f + S - 1) / S > NL)
             return fail(SPIIR_EUNSUPPORTED, "template %d has %lld filters; at most %d per template", t,
                         (long long)f, NL * S);
     }
-    // best-fit decreasing: place the largest templates first into the fullest block that
-    // still has room
-    std::vector<int> order(T);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lanes[x] > lanes[y]; });
-    std::multimap<int, int> by_free;  // free lanes -> block
-    std::vector<std::vector<int>> members;
-    std::vector<int> used;
-    for (int t : order) {
-        auto it = by_free.lower_bound(lanes[t]);
-        int c;
-        if (it == by_free.end()) {
-            c = (int)members.size();
-            members.emplace_back();
-            used.push_back(0);
-        } else {
-            c = it->second;
-            by_free.erase(it);
+    std::vector<Piece> pcs;
+    std::map<int, std::vector<int>> by_bin;   // bin -> pieces
+    b->h_red_t.clear();
+    b->h_red_off.assign(1, 0);
+    int n_part = 0;
+    for (int t = 0; t < T; ++t) {
+        std::map<int, std::vector<int64_t>> bins;
+        for (int64_t l = b->offsets[t]; l < b->offsets[t + 1]; ++l)
+            bins[b->dbin > 0 ? b->delay[l] / b->dbin : 0].push_back(l);
+        if (bins.empty()) bins[0];  // a template without filters still writes its (zero) row
+        bool first = true;
+        for (auto &kv : bins) {
+            Piece p;
+            p.t = t;
+            p.filt = std::move(kv.second);
+            p.lanes = (int)std::max<int64_t>(1, ((int64_t)p.filt.size() + S - 1) / S);
+            if (first) {
+                p.row = t;
+                p.w = 0;
+            } else {
+                p.row = n_part++;
+                p.w = 1;
+            }
+            by_bin[kv.first].push_back((int)pcs.size());
+            pcs.push_back(std::move(p));
+            first = false;
         }
-        members[c].push_back(t);
-        used[c] += lanes[t];
-        by_free.emplace(NL - used[c], c);
+        if (bins.size() > 1) {
+            b->h_red_t.push_back(t);
+            b->h_red_off.push_back(n_part);
+        }
+    }
+    b->n_part = n_part;
+    // best-fit decreasing within each bin: the largest pieces first into the fullest block that
+    // still has room
+    std::vector<std::vector<int>> members;
+    for (auto &kv : by_bin) {
+        std::vector<int> order = kv.second;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pcs[x].lanes > pcs[y].lanes; });
+        std::multimap<int, int> by_free;  // free lanes -> block
+        std::vector<int> used;
+        const size_t c_first = members.size();
+        for (int q : order) {
+            auto it = by_free.lower_bound(pcs[q].lanes);
+            int c;
+            if (it == by_free.end()) {
+                c = (int)members.size();
+                members.emplace_back();
+                used.push_back(0);
+            } else {
+                c = it->second;
+                by_free.erase(it);
+            }
+            members[c].push_back(q);
+            used[c - c_first] += pcs[q].lanes;
+            by_free.emplace(NL - used[c - c_first], c);
+        }
     }
     const int n_cta = (int)members.size();
     b->n_cta = n_cta;
@@ -448,20 +504,34 @@ int bank_pack(spiir_bank_s *b) {
     b->h_seg_off.assign(n_cta + 1, 0);
     b->h_wfirst.assign((size_t)n_cta * NW, -1);
     b->h_active.assign(n_cta, 0);
-    std::vector<int> lane_t(NL);
+    b->h_win.assign(n_cta, make_int2(0, 0));
+    b->win_max = 0;
+    std::vector<int> lane_p(NL);
     for (int c = 0; c < n_cta; ++c) {
-        // within a block, templates in ascending index order
-        std::sort(members[c].begin(), members[c].end());
+        // within a block, pieces in ascending template order
+        std::sort(members[c].begin(), members[c].end(), [&](int x, int y) { return pcs[x].t < pcs[y].t; });
+        // the block's window: its delays rounded out to multiples of 4 (16-byte copies)
+        int32_t dmin = INT32_MAX, dmax = -1;
+        for (int q : members[c])
+            for (int64_t l : pcs[q].filt) {
+                dmin = std::min(dmin, b->delay[l]);
+                dmax = std::max(dmax, b->delay[l]);
+            }
+        if (dmax < 0) dmin = dmax = 0;
+        const int dhi = (dmax + 3) / 4 * 4, dlo = dmin / 4 * 4;
+        b->h_win[c] = make_int2(dhi, dhi - dlo);
+        b->win_max = std::max(b->win_max, dhi - dlo);
+        std::fill(b->h_delay.begin() + (int64_t)c * S * NL, b->h_delay.begin() + (int64_t)(c + 1) * S * NL, dmin);
         int lane0 = 0;
         b->h_seg_off[c] = (int)b->h_segs.size();
-        std::fill(lane_t.begin(), lane_t.end(), -1);
-        for (int t : members[c]) {
-            for (int j = 0; j < lanes[t]; ++j) lane_t[lane0 + j] = t;
-            b->h_segs.push_back(make_int4(t, lane0, lane0 + lanes[t], 0));
-            lane0 += lanes[t];
+        std::fill(lane_p.begin(), lane_p.end(), -1);
+        for (int q : members[c]) {
+            for (int j = 0; j < pcs[q].lanes; ++j) lane_p[lane0 + j] = q;
+            b->h_segs.push_back(make_int4(pcs[q].row, lane0, lane0 + pcs[q].lanes, pcs[q].w));
+            lane0 += pcs[q].lanes;
         }
         b->h_active[c] = lane0;
-        assign_cells(b, c, lane_t, members[c]);
+        assign_cells(b, c, lane_p, pcs, members[c], dmin);
         const int s0 = b->h_seg_off[c];
         const int ns = (int)b->h_segs.size() - s0;
         for (int w = 0; w < NW; ++w) {
@@ -489,12 +559,17 @@ static int upload(void **dst, const void *src, size_t bytes, const char *what) {
 static void bank_free_packed(spiir_bank_s *b) {
     dev_free(b->are); dev_free(b->aim); dev_free(b->bre); dev_free(b->bim);
     dev_free(b->dly); dev_free(b->state); dev_free(b->segs); dev_free(b->seg_off);
-    dev_free(b->wfirst); dev_free(b->active);
+    dev_free(b->wfirst); dev_free(b->active); dev_free(b->win); dev_free(b->red_t); dev_free(b->red_off);
+    dev_free(b->zpart);
     b->are = b->aim = b->bre = b->bim = nullptr;
     b->dly = nullptr;
     b->state = nullptr;
     b->segs = nullptr;
     b->seg_off = b->wfirst = b->active = nullptr;
+    b->win = nullptr;
+    b->red_t = b->red_off = nullptr;
+    b->zpart = nullptr;
+    b->zpart_pitch = 0;
 }
 
 static void bank_free(spiir_bank_s *b) {
@@ -502,9 +577,7 @@ static void bank_free(spiir_bank_s *b) {
     int prev = -1;
     cudaGetDevice(&prev);
     if (b->device >= 0) cudaSetDevice(b->device);
-    dev_free(b->are); dev_free(b->aim); dev_free(b->bre); dev_free(b->bim);
-    dev_free(b->dly); dev_free(b->state); dev_free(b->segs); dev_free(b->seg_off);
-    dev_free(b->wfirst); dev_free(b->active);
+    bank_free_packed(b);
     dev_free(b->xbuf[0]); dev_free(b->xbuf[1]);
     if (prev >= 0) cudaSetDevice(prev);
     delete b;
@@ -520,6 +593,11 @@ static int bank_alloc_device(spiir_bank_s *b) {
     SPIIR_TRY(upload((void **)&b->seg_off, b->h_seg_off.data(), b->h_seg_off.size() * sizeof(int), "segment offsets"));
     SPIIR_TRY(upload((void **)&b->wfirst, b->h_wfirst.data(), b->h_wfirst.size() * sizeof(int), "warp segments"));
     SPIIR_TRY(upload((void **)&b->active, b->h_active.data(), b->h_active.size() * sizeof(int), "active lanes"));
+    SPIIR_TRY(upload((void **)&b->win, b->h_win.data(), b->h_win.size() * sizeof(int2), "block windows"));
+    if (b->n_part > 0) {
+        SPIIR_TRY(upload((void **)&b->red_t, b->h_red_t.data(), b->h_red_t.size() * sizeof(int), "split templates"));
+        SPIIR_TRY(upload((void **)&b->red_off, b->h_red_off.data(), b->h_red_off.size() * sizeof(int), "piece offsets"));
+    }
     b->state_det_stride = (int64_t)b->n_cta * (b->S / 2) * b->NL;
     SPIIR_TRY(dev_alloc((void **)&b->state, sizeof(float4) * b->state_det_stride * b->n_det, "IIR states"));
     SPIIR_CUDA_TRY(cudaMemset(b->state, 0, sizeof(float4) * b->state_det_stride * b->n_det));
@@ -527,7 +605,18 @@ static int bank_alloc_device(spiir_bank_s *b) {
 }
 
 // (Re)allocate the two strain windows for chunks of up to ncap samples, keeping history.
+static int bank_reserve_zpart(spiir_bank_s *b, int64_t ncap) {
+    if (b->n_part == 0 || (b->zpart && b->zpart_pitch >= ncap)) return SPIIR_OK;
+    dev_free(b->zpart);
+    b->zpart = nullptr;
+    b->zpart_pitch = 0;
+    SPIIR_TRY(dev_alloc((void **)&b->zpart, sizeof(float2) * ncap * b->n_det * b->n_part, "delay pieces"));
+    b->zpart_pitch = ncap;
+    return SPIIR_OK;
+}
+
 static int bank_reserve(spiir_bank_s *b, int64_t ncap, cudaStream_t stream) {
+    SPIIR_TRY(bank_reserve_zpart(b, std::max(ncap, b->ncap)));
     if (ncap <= b->ncap && b->xbuf[0]) return SPIIR_OK;
     const int64_t pitch = ((b->D_pad + ncap + 3) / 4) * 4 + 4;
     float *nb[2] = {nullptr, nullptr};
@@ -560,6 +649,7 @@ BankArgs bank_args(spiir_bank_s *b, float2 *z, int64_t zpitch, int64_t n) {
     a.xbuf = b->xbuf[b->cur];
     a.xpitch = b->xpitch;
     a.D_pad = b->D_pad;
+    a.cta_win = b->win;
     a.n = n;
     a.c_tile = b->c_tile;
     a.are = b->are; a.aim = b->aim; a.bre = b->bre; a.bim = b->bim;
@@ -569,6 +659,8 @@ BankArgs bank_args(spiir_bank_s *b, float2 *z, int64_t zpitch, int64_t n) {
     a.segs = b->segs; a.seg_off = b->seg_off; a.wfirst = b->wfirst; a.cta_active = b->active;
     a.z = z;
     a.zpitch = zpitch;
+    a.zpart = b->zpart;
+    a.zpart_pitch = b->zpart_pitch;
     a.n_det = b->n_det;
     a.status = device_status_word();
     a.red_offset = bank_red_offset(b);
@@ -577,7 +669,34 @@ BankArgs bank_args(spiir_bank_s *b, float2 *z, int64_t zpitch, int64_t n) {
     a.x_elems = b->xpitch * b->n_det;
     a.z_elems = INT64_MAX;
     a.n_segs_total = (int64_t)b->h_segs.size();
+    a.zpart_elems = b->zpart_pitch * b->n_det * b->n_part;
     return a;
+}
+
+// z[t] += the later delay pieces of template t, added in bin order (deterministic).
+__global__ void k_piece_sum(const int *red_t, const int *red_off, int n_det, const float2 *zpart, int64_t zpart_pitch,
+                            float2 *z, int64_t zpitch, int64_t n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = blockIdx.y / n_det, det = blockIdx.y % n_det;
+    float2 *zp = z + ((int64_t)red_t[i] * n_det + det) * zpitch + k;
+    float2 acc = *zp;
+    for (int p = red_off[i]; p < red_off[i + 1]; ++p) {
+        const float2 v = zpart[((int64_t)p * n_det + det) * zpart_pitch + k];
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    *zp = acc;
+}
+
+int bank_piece_sum(spiir_bank_s *b, float2 *z, int64_t zpitch, int64_t n, cudaStream_t stream) {
+    const int n_red = (int)b->h_red_t.size();
+    if (n_red == 0 || n < 1) return SPIIR_OK;
+    if (n > b->zpart_pitch) return fail(SPIIR_EINVAL, "internal: %lld samples exceed the piece buffers", (long long)n);
+    const dim3 grid((unsigned)((n + 255) / 256), (unsigned)(n_red * b->n_det));
+    k_piece_sum<<<grid, 256, 0, stream>>>(b->red_t, b->red_off, b->n_det, b->zpart, b->zpart_pitch, z, zpitch, n);
+    SPIIR_CUDA_TRY(cudaGetLastError());
+    return SPIIR_OK;
 }
 
 template <int S, int NL, int R>
@@ -617,32 +736,13 @@ int bank_filter(spiir_bank_s *b, const float *strain, int64_t strain_pitch, int6
     float *x = b->xbuf[b->cur];
     SPIIR_CUDA_TRY(cudaMemcpy2DAsync(x + b->D_pad, b->xpitch * 4, strain, strain_pitch * 4, n * 4, b->n_det,
                                      cudaMemcpyDeviceToDevice, stream));
-    BankArgs a{};
-    a.xbuf = x;
-    a.xpitch = b->xpitch;
-    a.D_pad = b->D_pad;
-    a.n = n;
-    a.c_tile = b->c_tile;
-    a.are = b->are; a.aim = b->aim; a.bre = b->bre; a.bim = b->bim;
-    a.delay = b->dly;
-    a.state = b->state;
-    a.state_det_stride = b->state_det_stride;
-    a.segs = b->segs; a.seg_off = b->seg_off; a.wfirst = b->wfirst; a.cta_active = b->active;
-    a.z = z;
-    a.zpitch = zpitch;
-    a.n_det = b->n_det;
-    a.status = device_status_word();
-    a.red_offset = bank_red_offset(b);
-    a.n_cta_total = b->n_cta;
-    a.n_pairs_total = (int64_t)b->n_cta * (b->S / 2) * b->NL;
-    a.x_elems = b->xpitch * b->n_det;
-    a.z_elems = INT64_MAX;
-    a.n_segs_total = (int64_t)b->h_segs.size();
+    const BankArgs a = bank_args(b, z, zpitch, n);
     const size_t smem = bank_smem_bytes(b);
     if (smem > (size_t)kBankMaxSmem)
         return fail(SPIIR_EUNSUPPORTED, "strain window of %d + %d samples does not fit in shared memory",
-                    b->D_pad, b->c_tile);
+                    b->win_max, b->c_tile);
     SPIIR_TRY(launch_bank_any(b, a, smem, stream));
+    SPIIR_TRY(bank_piece_sum(b, z, zpitch, n, stream));
     // the last D_pad samples become the history of the next call
     const int nxt = 1 - b->cur;
     if (b->D_pad > 0)
@@ -706,12 +806,15 @@ extern "C" int spiir_bank_create(int n_det, int n_templates, const int64_t *off,
     if (fmax > (int64_t)b->S * b->NL) b->NL = 256;
     if (fmax > (int64_t)b->S * b->NL) b->S = 16;
     b->c_tile = kBankTile;
+    // long delays: blocks hold one delay bin each, so that every block's strain window stays
+    // within the bin width plus the tile
+    b->dbin = dmax >= kBankSplitDelay ? kBankDefaultBin : 0;
     int rc = bank_pack(b);
     if (rc == SPIIR_OK) {
         const size_t smem = bank_smem_bytes(b);
         if (smem > (size_t)kBankMaxSmem)
-            rc = fail(SPIIR_EUNSUPPORTED, "maximum delay %d needs a %zu-byte window; limit %d", dmax, smem,
-                      kBankMaxSmem);
+            rc = fail(SPIIR_EUNSUPPORTED, "a block's delay span %d needs a %zu-byte window; limit %d", b->win_max,
+                      smem, kBankMaxSmem);
     }
     if (rc == SPIIR_OK) rc = bank_alloc_device(b);
     if (rc == SPIIR_OK) rc = bank_reserve(b, 2048, 0);
@@ -816,6 +919,38 @@ extern "C" int spiir_filter_chunk(spiir_bank_t b, const float *strain, int64_t s
                        (cudaStream_t)stream);
 }
 
+// Re-pack the bank for a new launch shape or delay-bin width, keeping the streaming state.  On
+// failure the previous shape is restored and the bank stays usable.
+static int bank_repack(spiir_bank_s *b, int S, int NL, int R, int tile, int dbin) {
+    size_t nb = 0;
+    SPIIR_TRY(spiir_bank_state_bytes(b, &nb));
+    std::vector<char> saved(nb);
+    SPIIR_TRY(spiir_bank_get_state(b, saved.data(), nb));
+    const int oS = b->S, oNL = b->NL, oR = b->R, oT = b->c_tile, oB = b->dbin;
+    b->S = S;
+    b->NL = NL;
+    b->R = R;
+    b->c_tile = tile;
+    b->dbin = dbin;
+    bank_free_packed(b);
+    int rc = bank_pack(b);
+    if (rc == SPIIR_OK && bank_smem_bytes(b) > (size_t)kBankMaxSmem)
+        rc = fail(SPIIR_EUNSUPPORTED, "shape needs %zu bytes of shared memory (window span %d + tile %d)",
+                  bank_smem_bytes(b), b->win_max, tile);
+    if (rc == SPIIR_OK) rc = bank_alloc_device(b);
+    if (rc == SPIIR_OK) rc = bank_reserve_zpart(b, b->ncap);
+    if (rc == SPIIR_OK) rc = spiir_bank_set_state(b, saved.data(), nb);
+    if (rc != SPIIR_OK) {
+        const std::string msg = [] { char m[512]; spiir_last_error(m, sizeof m); return std::string(m); }();
+        bank_free_packed(b);
+        b->S = oS; b->NL = oNL; b->R = oR; b->c_tile = oT; b->dbin = oB;
+        if (bank_pack(b) == SPIIR_OK && bank_alloc_device(b) == SPIIR_OK && bank_reserve_zpart(b, b->ncap) == SPIIR_OK)
+            spiir_bank_set_state(b, saved.data(), nb);
+        return fail(rc, "%s", msg.c_str());
+    }
+    return SPIIR_OK;
+}
+
 extern "C" int spiir_bank_set_shape(spiir_bank_t b, int filters_per_lane, int lanes_per_block, int steps_per_reduce,
                                     int tile) {
     clear_error();
@@ -832,34 +967,23 @@ extern "C" int spiir_bank_set_shape(spiir_bank_t b, int filters_per_lane, int la
     if (fmax > (int64_t)filters_per_lane * lanes_per_block)
         return fail(SPIIR_EUNSUPPORTED, "a template has %lld filters, more than %d lanes x %d", (long long)fmax,
                     lanes_per_block, filters_per_lane);
-    size_t nb = 0;
-    SPIIR_TRY(spiir_bank_state_bytes(b, &nb));
-    std::vector<char> saved(nb);
-    SPIIR_TRY(spiir_bank_get_state(b, saved.data(), nb));
-    const int oS = b->S, oNL = b->NL, oR = b->R, oT = b->c_tile;
-    b->S = filters_per_lane;
-    b->NL = lanes_per_block;
-    b->R = steps_per_reduce;
-    b->c_tile = tile;
-    int rc = bank_smem_bytes(b) <= (size_t)kBankMaxSmem ? SPIIR_OK
-                                                         : fail(SPIIR_EUNSUPPORTED, "shape needs too much shared memory");
-    if (rc == SPIIR_OK) {
-        bank_free_packed(b);
-        rc = bank_pack(b);
-        if (rc == SPIIR_OK) rc = bank_alloc_device(b);
-        if (rc == SPIIR_OK) rc = spiir_bank_set_state(b, saved.data(), nb);
-        if (rc != SPIIR_OK) {
-            // restore the previous shape so that the bank stays usable
-            const std::string msg = [] { char m[512]; spiir_last_error(m, sizeof m); return std::string(m); }();
-            bank_free_packed(b);
-            b->S = oS; b->NL = oNL; b->R = oR; b->c_tile = oT;
-            if (bank_pack(b) == SPIIR_OK && bank_alloc_device(b) == SPIIR_OK) spiir_bank_set_state(b, saved.data(), nb);
-            return fail(rc, "%s", msg.c_str());
-        }
-    } else {
-        b->S = oS; b->NL = oNL; b->R = oR; b->c_tile = oT;
-    }
-    return rc;
+    return bank_repack(b, filters_per_lane, lanes_per_block, steps_per_reduce, tile, b->dbin);
+}
+
+extern "C" int spiir_bank_set_delay_bin(spiir_bank_t b, int32_t delay_bin) {
+    clear_error();
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (delay_bin != 0 && (delay_bin < 1024 || delay_bin > kBankMaxDelay || delay_bin % 4 != 0))
+        return fail(SPIIR_EINVAL, "delay_bin %d must be 0 or a multiple of 4 in [1024, %d]", delay_bin, kBankMaxDelay);
+    return bank_repack(b, b->S, b->NL, b->R, b->c_tile, delay_bin);
+}
+
+extern "C" int spiir_bank_get_delay_bin(spiir_bank_t b, int32_t *delay_bin, int *n_blocks, int *n_pieces) {
+    if (!b) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (delay_bin) *delay_bin = b->dbin;
+    if (n_blocks) *n_blocks = b->n_cta;
+    if (n_pieces) *n_pieces = b->T + b->n_part;
+    return SPIIR_OK;
 }
 
 extern "C" int spiir_bank_get_shape(spiir_bank_t b, int *filters_per_lane, int *lanes_per_block,
@@ -909,8 +1033,8 @@ static int static_scratch_address(unsigned char **out) {
 
 // Block layout in template order: template t takes max(1, ceil(F_t / S)) lanes; a block is
 // closed when the next template does not fit.  One thread; T is small.
-__global__ void k_static_layout(const int64_t *off, int T, int S, int NL, int *cta_of_t, int *lane0_of_t,
-                                int4 *segs, int *seg_off, int *wfirst, int *active) {
+__global__ void k_static_layout(const int64_t *off, int T, int S, int NL, int D_pad, int *cta_of_t, int *lane0_of_t,
+                                int4 *segs, int *seg_off, int *wfirst, int *active, int2 *win) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int NW = NL / 32;
     int c = 0, used = 0;
@@ -932,6 +1056,7 @@ __global__ void k_static_layout(const int64_t *off, int T, int S, int NL, int *c
     active[c] = used;
     seg_off[c + 1] = T;
     for (int cc = 0; cc <= c; ++cc) {
+        win[cc] = make_int2(D_pad, D_pad);  // every block stages the whole history
         const int s0 = seg_off[cc], ns = seg_off[cc + 1] - s0;
         for (int w = 0; w < NW; ++w) {
             int first = -1;
@@ -1044,6 +1169,7 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     const size_t o_cta = take(sizeof(int) * n_templates), o_l0 = take(sizeof(int) * n_templates);
     const size_t o_segs = take(sizeof(int4) * n_templates), o_so = take(sizeof(int) * (n_cta + 1));
     const size_t o_wf = take(sizeof(int) * n_cta * (NL / 32)), o_act = take(sizeof(int) * n_cta);
+    const size_t o_win = take(sizeof(int2) * n_cta);
     const size_t o_x = take(sizeof(float) * xpitch * n_det);
     if (cur > kStaticScratchBytes)
         return fail(SPIIR_EUNSUPPORTED, "problem needs %zu bytes of scratch; the static array holds %zu", cur,
@@ -1068,10 +1194,11 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     SPIIR_CUDA_TRY(cudaMemcpy2DAsync(reinterpret_cast<float *>(base + o_x) + D_pad, xpitch * sizeof(float), strain,
                                      strain_pitch * sizeof(float), n * sizeof(float), n_det, cudaMemcpyDeviceToDevice,
                                      st));
-    k_static_layout<<<1, 32, 0, st>>>(reinterpret_cast<const int64_t *>(base + o_off), n_templates, S, NL,
+    k_static_layout<<<1, 32, 0, st>>>(reinterpret_cast<const int64_t *>(base + o_off), n_templates, S, NL, D_pad,
                                       reinterpret_cast<int *>(base + o_cta), reinterpret_cast<int *>(base + o_l0),
                                       reinterpret_cast<int4 *>(base + o_segs), reinterpret_cast<int *>(base + o_so),
-                                      reinterpret_cast<int *>(base + o_wf), reinterpret_cast<int *>(base + o_act));
+                                      reinterpret_cast<int *>(base + o_wf), reinterpret_cast<int *>(base + o_act),
+                                      reinterpret_cast<int2 *>(base + o_win));
     SPIIR_CUDA_TRY(cudaGetLastError());
     if (F > 0) {
         const int nb = (int)((F + 255) / 256);
@@ -1087,6 +1214,7 @@ extern "C" int spiir_filter_static(int n_det, int n_templates, const int64_t *of
     a.xbuf = reinterpret_cast<const float *>(base + o_x);
     a.xpitch = xpitch;
     a.D_pad = D_pad;
+    a.cta_win = reinterpret_cast<const int2 *>(base + o_win);
     a.n = n;
     a.c_tile = tile;
     a.are = reinterpret_cast<const float2 *>(base + o_are);

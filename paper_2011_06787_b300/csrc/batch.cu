@@ -350,6 +350,9 @@ static int batched_chunk(spiir_batch_s *B, const float *strain, float *ms, int32
     SPIIR_CUDA_TRY(cudaMemsetAsync(B->counter, 0, sizeof(int), s));
     if (B->n_items > 0) SPIIR_TRY(bank_launch_persistent(p, B->shape_S, B->shape_NL, B->shape_R, B->blocks_per_sm, smem, s));
     SPIIR_DEBUG_SYNC("persistent filter");
+    // bands with long delays: add the later delay pieces of their split templates
+    for (int b = 0; b < B->n_bands; ++b)
+        if (B->band_bank[b]) SPIIR_TRY(bank_piece_sum(B->band_bank[b], B->zb[b] + 1, zb_pitch(B, b), band_len(B, b), s));
     for (int b = 0; b < B->n_bands; ++b) {
         spiir_bank_s *k = B->band_bank[b];
         if (!k || k->D_pad == 0) continue;

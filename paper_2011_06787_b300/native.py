@@ -47,6 +47,8 @@ SIGNATURES = {
     "spiir_filter_static": (_I, [_I, _I, _P, _P, _P, _P, _P, _I64, _I64, _P, _I64, _P]),
     "spiir_bank_set_shape": (_I, [_P, _I, _I, _I, _I]),
     "spiir_bank_get_shape": (_I, [_P, _P, _P, _P, _P]),
+    "spiir_bank_set_delay_bin": (_I, [_P, ctypes.c_int32]),
+    "spiir_bank_get_delay_bin": (_I, [_P, _P, _P, _P]),
     "spiir_sky_set_scan_shape": (_I, [_P, _I, _I, _I]),
     "spiir_sky_get_scan_shape": (_I, [_P, _P, _P, _P, _P]),
     "spiir_sky_tables": (_I, [_I, _P, _P, _P, _P, _I, _D, _P, _P, _P]),

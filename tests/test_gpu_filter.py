@@ -87,22 +87,73 @@ def test_edge_cases_empty_single_and_large_templates():
 
 
 def test_maximum_delay_carries_across_chunks():
-    """A filter at the largest supported delay (32768 samples, a 16 s strain window) answers an
-    impulse only in a later chunk, as b0 a1^(k - 5 - d); one sample more is rejected."""
+    """A filter at the largest supported delay (2^20 samples, 512 s at 2048 Hz) answers an
+    impulse only many chunks later, as b0 a1^(k - 5 - d), and its template also holds a
+    filter of delay 7: the two sit in different delay bins, so the template is cut into two
+    pieces whose outputs are added after the launch.  One sample more is rejected."""
     import paper_2011_06787_b300 as sp
+    D = 1 << 20
     a = np.array([0.999 * np.exp(0.3j), 0.9 * np.exp(-1.1j)], np.complex64)
     b = np.array([0.5 + 0.2j, 0.25 - 0.1j], np.complex64)
-    d = np.array([32768, 7], np.int32)
+    d = np.array([D, 7], np.int32)
     bank = synth.Bank(np.array([0, 2], np.int64), a, b, d)
-    x = np.zeros((1, 40000), np.float32)
+    n = D + 6000
+    x = np.zeros((1, n), np.float32)
     x[0, 5] = 1.0
-    z, _ = _run_bank(bank, x, chunks=[20000, 20000])
-    k = np.arange(40000)
+    z, bk = _run_bank(bank, x, chunks=[65536])
+    assert bk.get_delay_bin() == (16384, 2, 2)
+    k = np.arange(n)
     ref = sum(np.where(k >= 5 + dl, complex(bl) * complex(al) ** np.maximum(k - 5 - dl, 0), 0) for al, bl, dl in zip(a, b, d))
     assert np.max(np.abs(z[0, 0] - ref)) <= 1e-5 * np.abs(ref).max()
-    assert abs(z[0, 0, 5 + 32768] - (b[0] + complex(b[1]) * complex(a[1]) ** 32768)) < 1e-6
+    assert abs(z[0, 0, 5 + D] - (b[0] + complex(b[1]) * complex(a[1]) ** D)) < 1e-6
     with pytest.raises(sp.SpiirError):
-        sp.Bank(1, np.array([0, 1], np.int64), a[:1], b[:1], np.array([32769], np.int32))
+        sp.Bank(1, np.array([0, 1], np.int64), a[:1], b[:1], np.array([D + 1], np.int32))
+
+
+def test_long_templates_across_delay_bins_match_oracle():
+    """Templates whose delays span 160k samples (a 78 s chirp at 2048 Hz) stream in 1 s chunks:
+    each is cut into pieces of 16384-sample delay bins, every block stages only its bin's
+    window, and the pieces add up to the oracle's SNR.  One template stays within one bin,
+    one has no filter in bin 0, one is empty."""
+    g = synth.rng(0, "misc", 12)
+    counts = [300, 40, 0, 170, 1]
+    bank = synth.random_bank(g, counts, d_max=160000)
+    bank.delay[300:340] = g.integers(20000, 30000, 40)          # template 1: bins 1 only
+    bank.delay[340:510] = g.integers(17000, 160000, 170)        # template 3: no filter in bin 0
+    x = synth.white_noise(0, 2, 165000, sub=12)
+    z, bk = _run_bank(bank, x, chunks=[2048])
+    dbin, blocks, pieces = bk.get_delay_bin()
+    assert dbin == 16384 and pieces > len(counts)
+    z_or, _, _ = oracle.filter_bank(x, bank.offsets, bank.a1, bank.b0, bank.delay)
+    assert np.all(z[2] == 0)
+    assert_snr_close(z[[0, 1, 3, 4]], z_or[[0, 1, 3, 4]])
+
+
+@pytest.mark.parametrize("delay_bin", [0, 1024, 4096, 16384])
+def test_delay_bin_width_does_not_change_results(delay_bin):
+    """The same bank laid out with whole templates or with pieces of 1024 to 16384-sample bins,
+    changed in the middle of the stream (the state carries over), matches the oracle."""
+    torch = _torch()
+    import paper_2011_06787_b300 as sp
+    g = synth.rng(0, "misc", 13)
+    bank = synth.random_bank(g, [3, 200, 500, 57, 1, 440], d_max=12000)
+    x = synth.white_noise(0, 3, 14000, sub=13)
+    b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+    assert b.get_delay_bin()[0] == 0
+    z1 = torch.zeros((6, 3, 9000), dtype=torch.complex64, device="cuda")
+    b.filter_chunk(torch.from_numpy(np.ascontiguousarray(x[:, :9000])).cuda(), z1)
+    b.set_delay_bin(delay_bin)
+    assert b.get_delay_bin()[0] == delay_bin
+    z2 = torch.zeros((6, 3, 5000), dtype=torch.complex64, device="cuda")
+    b.filter_chunk(torch.from_numpy(np.ascontiguousarray(x[:, 9000:])).cuda(), z2)
+    torch.cuda.synchronize()
+    sp.device_status()
+    z = np.concatenate([z1.cpu().numpy(), z2.cpu().numpy()], axis=2)
+    z_or, _, _ = oracle.filter_bank(x, bank.offsets, bank.a1, bank.b0, bank.delay)
+    assert_snr_close(z, z_or)
+    with pytest.raises(sp.SpiirError):
+        b.set_delay_bin(1000)   # not a multiple of 4 in [1024, 2^20]
+    assert b.get_delay_bin()[0] == delay_bin
 
 
 def test_impulse_response_closed_form_on_gpu():
