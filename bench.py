@@ -350,6 +350,10 @@ def run_gpu(args):
     if "candidates" in args.sections:
         cands = candidates_rate(args, torch, sp, det, sigma, timed_loop, bank)
 
+    scale = None
+    if "scale" in args.sections:
+        scale = scale_rate(args, torch, sp, timed_loop)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -382,6 +386,7 @@ def run_gpu(args):
             "xi2": xi2,
             "candidates": cands,
             "frontend": front,
+            "scale": scale,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
                                                    "h2d_bytes_per_step": n_det * n * 4,
@@ -447,6 +452,87 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
     out["kernel_launches_per_chunk"] = {"plain": 1 + sum(1 for b in banks for k in range(3) if np.any(b[4] == k)) +
                                         2 * len(banks), "batched": 4}
     return out
+
+
+def scale_rate(args, torch, sp, timed_loop):
+    """Scale workload: 3 detectors, 1 s chunks of unit white noise, 4096 chirp templates x 600
+    filters over whole chirps from 30 Hz (delays up to 151,713 samples), coherent scan over nside
+    32 (12288 pixels).  Three forms per chunk: the single-rate pipeline (filter bank at 2048 Hz
+    with 16384-sample delay bins, then the scan), and the same filters recast over 2048 / 512 /
+    128 Hz bands through the batch, per-band plain launches against the graph-replayed
+    persistent launch.  The single-rate filter bank and scan are also timed alone on the same
+    chunks (the legs of the pipeline step)."""
+    from paper_2011_06787_b300 import autotune
+    c = synth.SCALE
+    dev = torch.cuda.current_device()
+    det = synth.detectors(c["index"], 3)
+    sigma = synth.noise_weights(c["index"], 3, *c["sigma"])
+    bank, _, _ = synth.scale_bank()
+    mr = synth.scale_bank_multirate(bank)
+    sky = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, c["nside"], 2048.0))
+    T, n, P, H = bank.n_templates, c["chunk"], sky.n_pix, sky.halo
+    steps = max(3, min(args.steps, 6))
+    xs = [torch.from_numpy(synth.white_noise(c["index"], 3, n, sub=500 + i)).to(dev) for i in range(3 + steps)]
+    ms = torch.empty((T, n), device=dev)
+    am = torch.empty((T, n), dtype=torch.int32, device=dev)
+    nl = torch.empty((T, n), device=dev)
+    b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+    zbuf = torch.zeros((T, 3, n + 2 * H), dtype=torch.complex64, device=dev)
+    for i in range(3):
+        b.filter_chunk(xs[i], zbuf[:, :, 2 * H:])
+    if args.scan_shape:
+        sky.set_scan_shape(*[int(v) for v in args.scan_shape.split(",")])
+    elif not args.no_tune:
+        autotune.tune_scan(sky, zbuf, n, ms, am, nl, reps=2)
+    b.reset()
+    pipe = sp.Pipeline(b, sky, max_chunk=n)
+    for i in range(3):
+        pipe.run(xs[i], ms, am, nl)
+    single = float(np.mean(timed_loop(lambda i: pipe.run(xs[3 + i], ms, am, nl), steps)))
+    k1 = float(np.mean(timed_loop(lambda i: b.filter_chunk(xs[3 + i], zbuf[:, :, 2 * H:]), steps)))
+    k2 = float(np.mean(timed_loop(lambda i: sky.scan(zbuf, n, ms, am, nl), steps)))
+    dbin, blocks, pieces = b.get_delay_bin()
+    del pipe, b, zbuf
+    torch.cuda.empty_cache()
+    batch = sp.Batch(3, [mr], c["factors"], sky, n)
+    out_b = {}
+    x = torch.empty((3, n), device=dev)
+    for mode, name in ((0, "multirate_plain"), (2, "multirate_batched_graph")):
+        batch.reset()
+        for i in range(3):
+            x.copy_(xs[i])
+            batch.run(x, ms, am, nl, mode=mode)
+
+        def step(i, mode=mode):
+            x.copy_(xs[3 + i])
+            batch.run(x, ms, am, nl, mode=mode)
+        out_b[name] = float(np.mean(timed_loop(step, steps)))
+    sp.device_status()
+    del batch
+    torch.cuda.empty_cache()
+    updates = int(bank.n_filters) * 3 * n
+    mr_updates = int(np.sum(3 * (n // np.asarray(c["factors"])[mr[4]])))
+    peak = 148 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    k1_tf = K1_FLOPS_PER_UPDATE * updates / (k1 * 1e-3) / 1e12
+    k2_tf = k2_flops_per_pixel_sample(3) * T * n * P / (k2 * 1e-3) / 1e12
+    return {"workload": f"3 det, 1 s chunks; {T} chirp templates x {c['n_filters']} filters from 30 Hz "
+                        f"(delays up to {int(bank.delay.max())} samples); nside {c['nside']} ({P} pixels)",
+            "steps": steps, "scan_shape": list(sky.get_scan_shape()[:3]),
+            "single_rate": {"ms_per_chunk": single, "updates_per_s": updates / (single * 1e-3),
+                            "pixel_samples_per_s": T * n * P / (single * 1e-3),
+                            "delay_bin": dbin, "blocks": blocks, "pieces": pieces,
+                            "kernel_ms": {"k_filter_bank + k_piece_sum": k1, "coherent scan": k2}},
+            "multirate_plain": {"ms_per_chunk": out_b["multirate_plain"],
+                                "updates_per_s": mr_updates / (out_b["multirate_plain"] * 1e-3)},
+            "multirate_batched_graph": {"ms_per_chunk": out_b["multirate_batched_graph"],
+                                        "updates_per_s": mr_updates / (out_b["multirate_batched_graph"] * 1e-3)},
+            "multirate_updates_per_chunk": mr_updates,
+            "speedup_graph_vs_plain": out_b["multirate_plain"] / out_b["multirate_batched_graph"],
+            "roofline": {"filter_bank": {"bound": "alu", "achieved": k1_tf, "peak": peak, "unit": "TFLOP/s",
+                                         "frac": k1_tf / peak, "flops_per_launch": K1_FLOPS_PER_UPDATE * updates},
+                         "coherent_scan": {"bound": "alu", "achieved": k2_tf, "peak": peak, "unit": "TFLOP/s",
+                                           "frac": k2_tf / peak,
+                                           "flops_per_launch": k2_flops_per_pixel_sample(3) * T * n * P}}}
 
 
 def bank_autocorr(torch, sp, bank, Nj, dev, nr=6000):
@@ -736,9 +822,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
-    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2,candidates,frontend",
+    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2,candidates,frontend,scale",
                     help="comma list of measurements: main (always timed), batched, adjoint, skymap, xi2, candidates, "
-                         "frontend")
+                         "frontend, scale")
     ap.add_argument("--adjoint-templates", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--scan-shape", default="", help="fixed coherent-scan shape threads,pairs,table (no autotuning)")

@@ -287,24 +287,57 @@ def chirp_workload(n_templates: int = CHIRP["n_templates"], n_filters: int = CHI
 # Scale workload: 4096 chirp templates x 600 filters, 60 s, 20 injections, nside 32
 
 SCALE = dict(index=4, n_det=3, rate=2048, chunk=2048, n_chunks=60, n_templates=4096, n_filters=600,
-             mc=(1.0, 3.0), f_lo=30.0, max_template_s=15.0, nside=32, sigma=(0.5, 2.0),
-             n_inj=20, snr=(8.0, 20.0), tc_s=(20.0, 58.0))
+             mc=(1.0, 3.0), f_lo=30.0, f_hi=1024.0, nside=32, sigma=(0.5, 2.0),
+             n_inj=20, snr=(8.0, 20.0), tc_s=(20.0, 58.0), factors=(1, 4, 16))
 
 
-def template_f_lo(mc_msun: float, max_s: float = SCALE["max_template_s"], f_lo: float = SCALE["f_lo"]) -> float:
-    """Start frequency of a template: f_lo, raised so that the Newtonian chirp lasts at most
-    max_s seconds (the time to coalescence tau(f) = 5/256 (pi f)^(-8/3) M^(-5/3))."""
+def chirp_fit(mc_msun: float, n_filters: int, rate: float = 2048.0, f_lo: float = 30.0, f_hi: float = 1024.0):
+    """First-order IIR fit of conj(h), h = newtonian_chirp(mc) (time-reversed, sample j at
+    tau_j = tau(f_hi) + j / rate), built from the chirp's closed form so that long templates cost
+    O(n_filters): the segment construction of segment_fit with the integral of |phi''|^(1/2)
+    taken analytically.  With phi(tau) = -2 (tau / 5M)^(5/8), phi'' is proportional to
+    tau^(-11/8), so the integral of |phi''|^(1/2) grows as tau^(5/16) and segment i starts at
+    the first sample with tau^(5/16) - tau_hi^(5/16) >= (i / N) (tau_lo^(5/16) - tau_hi^(5/16)).
+    On each segment omega is the mean phase slope of conj(h), gamma = -1 / length and b0 the
+    value of conj(h) at the segment start.  Returns (a1, b0, delay, n, sum_j |h_j|^2) with
+    complex128 coefficients and int32 delays."""
     M = mc_msun * G_MSUN_S
-    f = (max_s * 256.0 / 5.0 * M ** (5.0 / 3.0)) ** (-3.0 / 8.0) / math.pi
-    return max(f_lo, f)
+    tau_of_f = lambda f: (5.0 / 256.0) * (math.pi * f) ** (-8.0 / 3.0) * M ** (-5.0 / 3.0)
+    t_hi, t_lo = tau_of_f(f_hi), tau_of_f(f_lo)
+    n = int(math.floor((t_lo - t_hi) * rate)) + 1
+    tau_end = t_hi + (n - 1) / rate
+    u = np.linspace(0.0, 1.0, n_filters + 1) * (tau_end ** 0.3125 - t_hi ** 0.3125) + t_hi ** 0.3125
+    edges = np.ceil((u ** 3.2 - t_hi) * rate - 1e-9).astype(np.int64)
+    edges = np.clip(edges, 0, n)
+    edges[0], edges[-1] = 0, n
+    k = np.arange(edges.size)
+    edges = np.maximum.accumulate(edges - k) + k      # strictly increasing
+    edges = np.minimum(edges, n)
+    lo = np.minimum(edges[:-1], n - 1)
+    hi = np.maximum(np.minimum(edges[1:], n), lo + 1)
+    L = np.maximum(hi - lo, 1)
+    phase = lambda j: -2.0 * ((t_hi + j / rate) / (5.0 * M)) ** 0.625        # phase of h at sample j
+    amp = lambda j: ((t_hi + j / rate) / t_hi) ** (-0.25)                     # (f / f_hi)^(2/3)
+    jb = np.where(L > 1, hi - 1, np.minimum(lo + 1, n - 1))
+    omega = -(phase(jb.astype(np.float64)) - phase(lo.astype(np.float64))) / np.maximum(jb - lo, 1)
+    a1 = np.exp(-1.0 / L + 1j * omega)
+    b0 = amp(lo.astype(np.float64)) * np.exp(-1j * phase(lo.astype(np.float64)))
+    # sum_j amp_j^2 = sum_j (tau_j / t_hi)^(-1/2) by Euler-Maclaurin (the integrand is smooth)
+    g = lambda j: ((t_hi + j / rate) / t_hi) ** (-0.5)
+    dg = lambda j: -0.5 * ((t_hi + j / rate) / t_hi) ** (-1.5) / (rate * t_hi)
+    e = float(n - 1)
+    integral = 2.0 * rate * t_hi * (((t_hi + e / rate) / t_hi) ** 0.5 - 1.0)
+    power = integral + 0.5 * (g(0.0) + g(e)) + (dg(e) - dg(0.0)) / 12.0
+    return a1, b0, lo.astype(np.int32), n, power
 
 
 def scale_bank(n_templates: int = SCALE["n_templates"], n_filters: int = SCALE["n_filters"]):
     """Template bank on a uniform chirp-mass grid over [1, 3] Msun.  Template t is the
-    first-order IIR fit (segment_fit) of conj(h_t), h_t the time-reversed Newtonian chirp from
-    template_f_lo(Mc_t) to 1024 Hz, so that the bank's output is the correlation with the
-    chirp; b0 is scaled by sqrt(2 / sum |h_t|^2), which makes E|z|^2 = 2 in unit white noise
-    (up to the fit's mismatch).  Returns (Bank, mc [T], template lengths [T])."""
+    first-order IIR fit (chirp_fit) of conj(h_t), h_t the whole time-reversed Newtonian chirp
+    from 30 Hz to 1024 Hz (12 s at 3 Msun to 74 s, about 151k samples, at 1 Msun), so that the
+    bank's output is the correlation with the chirp; b0 is scaled by sqrt(2 / sum |h_t|^2), which
+    makes E|z|^2 = 2 in unit white noise (up to the fit's mismatch).  Returns (Bank, mc [T],
+    template lengths [T])."""
     c = SCALE
     mcs = np.linspace(c["mc"][0], c["mc"][1], n_templates)
     A = np.empty((n_templates, n_filters), dtype=np.complex64)
@@ -312,14 +345,43 @@ def scale_bank(n_templates: int = SCALE["n_templates"], n_filters: int = SCALE["
     D = np.empty((n_templates, n_filters), dtype=np.int32)
     lens = np.empty(n_templates, dtype=np.int64)
     for t, mc in enumerate(mcs):
-        h = newtonian_chirp(float(mc), f_lo=template_f_lo(float(mc)))
-        a1, b0, d = segment_fit(np.conj(h), n_filters)
+        a1, b0, d, n, power = chirp_fit(float(mc), n_filters, c["rate"], c["f_lo"], c["f_hi"])
         A[t] = a1.astype(np.complex64)
-        B[t] = (b0 * math.sqrt(2.0 / float(np.sum(np.abs(h) ** 2)))).astype(np.complex64)
+        B[t] = (b0 * math.sqrt(2.0 / power)).astype(np.complex64)
         D[t] = d
-        lens[t] = h.size
+        lens[t] = n
     off = np.arange(n_templates + 1, dtype=np.int64) * n_filters
     return Bank(off, A.ravel(), B.ravel(), D.ravel()), mcs, lens
+
+
+def scale_bank_multirate(bank: Bank, factors=SCALE["factors"], rate: float = 2048.0, fir_delay: float = 15.5):
+    """The scale bank recast over the multirate bands of the batched path (decimation by M_b
+    with the 32-tap low-pass, band SNR upsampled linearly with one band sample of lag).  A
+    full-rate filter (a, b, d) of frequency f = |arg a| rate / 2 pi goes to the slowest band
+    with f <= 0.3 rate / M_b (0.6 of the band's Nyquist frequency) whose rate still gives the
+    filter's decay length 1 / |log|a|| at least 2 band samples and whose total lag
+    fir_delay + M_b fits in d; there it becomes (a^M, M b a^(l - d), d_b) with
+    d_b = floor((d - fir_delay - M) / M) and l = M d_b + M + fir_delay the full-rate lag of the
+    band path, so that its response approximates b a^(k - d).  Returns (offsets, a1, b0, delay,
+    band) for spiir_batch_create and oracle.multirate_bank."""
+    a = bank.a1.astype(np.complex128)
+    b = bank.b0.astype(np.complex128)
+    d = bank.delay.astype(np.int64)
+    f = np.abs(np.angle(a)) * rate / (2.0 * math.pi)
+    decay = 1.0 / np.maximum(-np.log(np.abs(a)), 1e-12)
+    band = np.zeros(a.size, dtype=np.int32)
+    for bi, M in enumerate(factors):
+        if M == 1:
+            continue
+        ok = (f <= 0.3 * rate / M) & (decay >= 2.0 * M) & (d >= fir_delay + M)
+        band[ok] = bi      # later (slower) bands override earlier ones
+    Mv = np.asarray(factors, dtype=np.int64)[band]
+    db = np.where(Mv == 1, d, np.floor((d - fir_delay - Mv) / Mv)).astype(np.int64)
+    lag = np.where(Mv == 1, d, Mv * db + Mv + fir_delay)
+    loga = np.log(a)
+    a_b = np.exp(Mv * loga)
+    b_b = np.where(Mv == 1, b, Mv * b * np.exp((lag - d) * loga))
+    return (bank.offsets.copy(), a_b.astype(np.complex64), b_b.astype(np.complex64), db.astype(np.int32), band)
 
 
 def scale_injections(n: int = SCALE["n_inj"]):
