@@ -36,10 +36,21 @@ WORKLOAD = "online-sized: 3 det, 1024 templates x U{200..900} filters, d<=4096, 
 METRIC = "IIR filter·sample updates/s; coherent sky-pixel·samples/s; batched vs plain"
 UNIT = "filter·sample updates/s"
 K1_FLOPS_PER_UPDATE = 12          # Sec. II.B.2
+K1_LANE_OPS_PER_UPDATE = 8        # 4 FMA + 2 MUL + 2 ADD on the FP32 lanes
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 # candidate-driven scan, 3 detectors: U_s^T w (3 detectors x 4 FMA) and |.|^2 (3 FMA + 1 MUL)
 K_POINT_FLOPS = 2 * 12 + 2 * 3 + 1
+
+
+def k1_roofline(updates, ms, n_sm=148):
+    """Filter-bank roofline: its 12 flops per update issue as 8 FP32 lane operations, so the
+    ceiling for this mix is the lane rate x 12 / 8 (57.7 TFLOP/s at 148 SMs and 2032 MHz)."""
+    achieved = K1_FLOPS_PER_UPDATE * updates / (ms * 1e-3) / 1e12
+    peak = n_sm * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 * K1_FLOPS_PER_UPDATE / K1_LANE_OPS_PER_UPDATE / 1e12
+    return {"kernel": "k_filter_bank", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_launch": K1_FLOPS_PER_UPDATE * updates,
+            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {SM_MAX_MHZ:.0f} MHz x 12 flops / 8 lane ops"}
 
 
 def k2_flops_per_pixel_sample(n_det):
@@ -350,6 +361,10 @@ def run_gpu(args):
     if "candidates" in args.sections:
         cands = candidates_rate(args, torch, sp, det, sigma, timed_loop, bank)
 
+    search = None
+    if "search" in args.sections:
+        search = search_rate(args, torch, sp, det, sigma, timed_loop)
+
     scale = None
     if "scale" in args.sections:
         scale = scale_rate(args, torch, sp, timed_loop)
@@ -386,6 +401,7 @@ def run_gpu(args):
             "xi2": xi2,
             "candidates": cands,
             "frontend": front,
+            "search": search,
             "scale": scale,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT,
@@ -513,7 +529,6 @@ def scale_rate(args, torch, sp, timed_loop):
     updates = int(bank.n_filters) * 3 * n
     mr_updates = int(np.sum(3 * (n // np.asarray(c["factors"])[mr[4]])))
     peak = 148 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    k1_tf = K1_FLOPS_PER_UPDATE * updates / (k1 * 1e-3) / 1e12
     k2_tf = k2_flops_per_pixel_sample(3) * T * n * P / (k2 * 1e-3) / 1e12
     return {"workload": f"3 det, 1 s chunks; {T} chirp templates x {c['n_filters']} filters from 30 Hz "
                         f"(delays up to {int(bank.delay.max())} samples); nside {c['nside']} ({P} pixels)",
@@ -528,11 +543,58 @@ def scale_rate(args, torch, sp, timed_loop):
                                         "updates_per_s": mr_updates / (out_b["multirate_batched_graph"] * 1e-3)},
             "multirate_updates_per_chunk": mr_updates,
             "speedup_graph_vs_plain": out_b["multirate_plain"] / out_b["multirate_batched_graph"],
-            "roofline": {"filter_bank": {"bound": "alu", "achieved": k1_tf, "peak": peak, "unit": "TFLOP/s",
-                                         "frac": k1_tf / peak, "flops_per_launch": K1_FLOPS_PER_UPDATE * updates},
+            "roofline": {"filter_bank": k1_roofline(updates, k1),
                          "coherent_scan": {"bound": "alu", "achieved": k2_tf, "peak": peak, "unit": "TFLOP/s",
                                            "frac": k2_tf / peak,
                                            "flops_per_launch": k2_flops_per_pixel_sample(3) * T * n * P}}}
+
+
+def search_rate(args, torch, sp, det, sigma, timed_loop):
+    """Candidate-driven streaming search (Sec. II.C.1 - II.C.3) on the online workload: per 1 s
+    chunk, the filter bank (1024 templates, b0 scaled to E|z|^2 close to 2) into the SNR ring,
+    selection (threshold 4, one candidate per template per second), zero-lag scan on nside 16,
+    100 time shifts of 205 samples on nside 8, xi_C^2 (Nj = 175) at every candidate and shift;
+    one spiir_search_run call per chunk of unit white noise.  The ring is filled past its
+    20.5 s history before timing."""
+    Nj, n, n_sh, step = 175, 2048, 100, 205
+    dev = torch.cuda.current_device()
+    bank = synth.normalised(synth.online_bank())
+    sky16 = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 16, 2048.0))
+    sky8 = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 8, 2048.0))
+    A, _ = bank_autocorr(torch, sp, bank, Nj, dev)
+    b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+    srch = sp.Search(b, sky16, sky8, A, Nj, n, 4.0, 2048, n_sh, step, max_cand=16384)
+    L, Hb, La, _ = srch.info()
+    fill = (L + n - 1) // n
+    steps = max(3, min(args.steps, 16))
+    xs = [torch.from_numpy(synth.white_noise(1, 3, n, sub=3000 + i)).to(dev) for i in range(fill + steps)]
+    for i in range(fill):
+        srch.run(xs[i])
+    cnts = []
+
+    def step_fn(i):
+        srch.run(xs[fill + i])
+    t = timed_loop(step_fn, steps)
+    # candidate counts of the same chunks (not timed)
+    srch.reset()
+    for i in range(fill + steps):
+        srch.run(xs[i])
+        if i >= fill:
+            cnts.append(int(srch.n_cand.item()))
+    zb = torch.zeros((bank.n_templates, 3, n), dtype=torch.complex64, device=dev)
+    k1 = float(np.mean(timed_loop(lambda i: b.filter_chunk(xs[i % len(xs)], zb), steps)))
+    sp.device_status()
+    ms = float(np.mean(t))
+    updates = int(bank.n_filters) * 3 * n
+    del srch, b, zb, A
+    torch.cuda.empty_cache()
+    return {"workload": f"online bank (1024 templates, E|z|^2 ~ 2), 3 det, {n}-sample chunks; threshold 4; "
+                        f"zero lag nside 16, {n_sh} shifts x {step} samples on nside 8; xi^2 Nj = {Nj}; "
+                        f"ring {L} samples ({Hb} history, lag {La})",
+            "steps": steps, "ms_per_second_of_data": ms, "candidates_per_chunk": float(np.mean(cnts)),
+            "updates_per_s": updates / (ms * 1e-3), "filter_bank_ms": k1,
+            "candidate_stages_ms": ms - k1,
+            "roofline": k1_roofline(updates, k1)}
 
 
 def bank_autocorr(torch, sp, bank, Nj, dev, nr=6000):
@@ -822,9 +884,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain multirate measurement")
-    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2,candidates,frontend,scale",
+    ap.add_argument("--sections", default="main,batched,adjoint,skymap,xi2,candidates,search,frontend,scale",
                     help="comma list of measurements: main (always timed), batched, adjoint, skymap, xi2, candidates, "
-                         "frontend, scale")
+                         "search, frontend, scale")
     ap.add_argument("--adjoint-templates", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--scan-shape", default="", help="fixed coherent-scan shape threads,pairs,table (no autotuning)")

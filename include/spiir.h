@@ -43,6 +43,7 @@ typedef struct spiir_sky_s *spiir_sky_t;
 typedef struct spiir_pipeline_s *spiir_pipeline_t;
 typedef struct spiir_batch_s *spiir_batch_t;
 typedef struct spiir_frontend_s *spiir_frontend_t;
+typedef struct spiir_search_s *spiir_search_t;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int spiir_version(void);
@@ -405,6 +406,59 @@ int spiir_xi2_candidates(spiir_sky_t sky, int n_templates, const float *snr_dev,
                          const int32_t *n_cand_dev, int max_cand, int first_shift, int n_shifts,
                          int shift_step, const int32_t *argmax_dev, float *xi2_dev,
                          float *xi2_det_dev, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Candidate-driven streaming search (Sec. II.C.1 - II.C.3): the paper's coherent stage as it
+ * runs per chunk.  One call filters a chunk of strain into a ring of SNR history (Sec. II.B.1)
+ * and, on the span of the stream that the ring now fully surrounds, selects the
+ * single-detector candidates (spiir_select_candidates), evaluates the coherent statistic and
+ * null stream at every candidate at zero lag on the foreground sky and under the time shifts
+ * 1 .. n_shifts on the background sky (spiir_coherent_candidates), and xi_C^2 at each of those
+ * coherent argmax pixels (spiir_xi2_candidates).  The candidate count stays on the device;
+ * nothing is synchronised.
+ * Span: a call analyses the chunk-long span [S0, S0 + chunk) of stream samples with
+ * S0 = (samples filtered after the call) - chunk - La, La = 2 H + n_lags (H the larger sky
+ * halo): the search lags the strain by La samples, the most the zero-lag stages read past a
+ * candidate.  The background and xi^2 read back up to
+ * Hb = n_shifts (n_det - 1) shift_step + 2 H + n_lags samples before a candidate, so the ring
+ * keeps L = Hb + chunk + La samples per (template, detector) (2 L entries: each sample is
+ * stored twice so that any L consecutive samples are contiguous).  Samples before the stream
+ * start are zero.  Seconds (one candidate per template per second) are blocks of per_second
+ * samples counted from S0.
+ * ---------------------------------------------------------------------------------- */
+
+/* bank, sky_fg (zero lag; nside 16 in the paper), sky_bg (time shifts; nside 8) must share
+ * n_det >= 2 and outlive the search, and the bank is driven only through it.  A_dev
+ * [T][2 n_lags + 1] complex: each template's autocorrelation as for spiir_xi2 (copied).
+ * chunk: strain samples per call.  threshold: |z| above which a sample is a candidate (4 in
+ * the paper).  n_shifts (100 in the paper, 0 for none) time shifts of shift_step samples per
+ * companion (205 = 0.1 s at 2048 Hz).  max_cand: rows of the candidate outputs.
+ * Errors: SPIIR_EINVAL, SPIIR_ENOMEM, SPIIR_ECUDA. */
+int spiir_search_create(spiir_bank_t bank, spiir_sky_t sky_fg, spiir_sky_t sky_bg, const float *A_dev,
+                        int n_lags, int64_t chunk, float threshold, int per_second, int n_shifts,
+                        int shift_step, int max_cand, spiir_search_t *out);
+void spiir_search_destroy(spiir_search_t search);
+/* Ring length L, history Hb and lag La (samples), and S0 of the next call's span. */
+int spiir_search_info(spiir_search_t search, int64_t *ring_len, int64_t *history, int64_t *lag,
+                      int64_t *next_span_start);
+/* Zero the bank's state and the ring (a new stream).  Enqueued on stream. */
+int spiir_search_reset(spiir_search_t search, void *stream);
+/* One chunk.  strain_dev [n_det][strain_pitch] f32, chunk samples continuing the stream.
+ * Outputs (device, caller-owned; rows past the count are not written):
+ *   cand_dev [max_cand][4] int32 (16-byte aligned): (detector, template, sample k of the span,
+ *     bits of the FP32 |z|^2) as spiir_select_candidates; stream sample = S0 + k.
+ *   n_cand_dev [1] int32: candidates found (above max_cand on overflow).
+ *   fg_*_dev [max_cand]: zero-lag maximum of rho_C^2 over the foreground sky, its pixel, the
+ *     null stream there and xi_C^2 there.
+ *   bg_*_dev [max_cand][n_shifts]: the same for shifts 1 .. n_shifts on the background sky
+ *     (may be NULL when n_shifts = 0).
+ *   span_start: NULL or a host int64 that receives S0.
+ * Calls on one search must be ordered on one stream.  Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
+int spiir_search_run(spiir_search_t search, const float *strain_dev, int64_t strain_pitch,
+                     int32_t *cand_dev, int32_t *n_cand_dev, float *fg_max_dev,
+                     int32_t *fg_argmax_dev, float *fg_null_dev, float *fg_xi2_dev,
+                     float *bg_max_dev, int32_t *bg_argmax_dev, float *bg_null_dev,
+                     float *bg_xi2_dev, int64_t *span_start, void *stream);
 
 /* ------------------------------------------------------------------------------------
  * Impulse response and its adjoint, for refining IIR coefficients against target

@@ -287,6 +287,67 @@ class Pipeline:
         return True
 
 
+class Search:
+    """Candidate-driven streaming search (spiir_search_*): per chunk, filter bank into an SNR
+    ring, candidate selection, zero-lag scan on sky_fg, time-shift background on sky_bg and
+    xi_C^2 at the candidates (Sec. II.C.1 - II.C.3).  A [T][2 n_lags + 1] complex64 CUDA tensor
+    of the templates' autocorrelations.  Output tensors are allocated once and overwritten by
+    every run(); rows past the count keep older values."""
+
+    def __init__(self, bank: Bank, sky_fg: Sky, sky_bg: Sky, A, n_lags: int, chunk: int, threshold: float = 4.0,
+                 per_second: int = 2048, n_shifts: int = 100, shift_step: int = 205, max_cand: int = 16384):
+        import torch
+        _require_cuda(A, torch.complex64, "A")
+        h = ctypes.c_void_p()
+        check(native.lib().spiir_search_create(bank.handle, sky_fg.handle, sky_bg.handle, _dev_ptr(A), int(n_lags),
+                                               int(chunk), float(threshold), int(per_second), int(n_shifts),
+                                               int(shift_step), int(max_cand), ctypes.byref(h)))
+        self._h = h
+        self.bank, self.sky_fg, self.sky_bg = bank, sky_fg, sky_bg
+        self.chunk, self.n_shifts, self.max_cand = int(chunk), int(n_shifts), int(max_cand)
+        dev = A.device
+        m, s = max(1, max_cand), max(1, n_shifts)
+        self.cand = torch.zeros((m, 4), dtype=torch.int32, device=dev)
+        self.n_cand = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.fg = (torch.full((m,), float("nan"), device=dev), torch.full((m,), -1, dtype=torch.int32, device=dev),
+                   torch.full((m,), float("nan"), device=dev), torch.full((m,), float("nan"), device=dev))
+        self.bg = (torch.full((m, s), float("nan"), device=dev), torch.full((m, s), -1, dtype=torch.int32, device=dev),
+                   torch.full((m, s), float("nan"), device=dev), torch.full((m, s), float("nan"), device=dev))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            native.lib().spiir_search_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        """(ring length L, history Hb, lag La, S0 of the next span) in samples."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        check(native.lib().spiir_search_info(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def reset(self, stream=None):
+        check(native.lib().spiir_search_reset(self._h, _stream_ptr(stream)))
+
+    def run(self, strain, stream=None):
+        """strain [n_det][>= chunk] float32 CUDA tensor.  Returns S0, the stream sample of the
+        span's sample 0; the results are in self.cand, self.n_cand, self.fg = (max, argmax,
+        null, xi2) [max_cand] and self.bg = the same [max_cand][n_shifts]."""
+        import torch
+        _require_cuda(strain, torch.float32, "strain")
+        s0 = ctypes.c_int64()
+        bg = [_dev_ptr(t) for t in self.bg] if self.n_shifts > 0 else [None] * 4
+        check(native.lib().spiir_search_run(self._h, _dev_ptr(strain), strain.stride(0), _dev_ptr(self.cand),
+                                            _dev_ptr(self.n_cand), *[_dev_ptr(t) for t in self.fg], *bg,
+                                            ctypes.byref(s0), _stream_ptr(stream)))
+        return s0.value
+
+
 class Batch:
     """Batched multirate banks (spiir_batch_*).  banks: list of (offsets, a1, b0, delay, band)
     host arrays, one per bank; band_factor: decimation factor of each band."""

@@ -14,7 +14,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libspiir.so")
 
-SOURCES = ["common.cu", "bank.cu", "coherent.cu", "coherent_tmem.cu", "xi2.cu", "candidates.cu", "frontend.cu", "pipeline.cu", "adjoint.cu", "batch.cu", "sky_tables.cpp"]
+SOURCES = ["common.cu", "bank.cu", "coherent.cu", "coherent_tmem.cu", "xi2.cu", "candidates.cu", "frontend.cu", "pipeline.cu", "search.cu", "adjoint.cu", "batch.cu", "sky_tables.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

@@ -170,6 +170,19 @@ def online_bank(n_templates: int = ONLINE["n_templates"]) -> Bank:
     return full.subset(range(n_templates))
 
 
+def normalised(bank: Bank, power: float = 2.0) -> Bank:
+    """The bank with each template's b0 scaled so that the filters' output powers in unit white
+    noise add up to `power`: sum_l |b0_l|^2 / (1 - |a1_l|^2) = power (cross terms between
+    filters, which average out over random phases and delays, are left out).  With power 2 the
+    SNR of a template has E|z|^2 close to 2, the normalisation the candidate threshold assumes."""
+    a2 = np.abs(bank.a1.astype(np.complex128)) ** 2
+    b2 = np.abs(bank.b0.astype(np.complex128)) ** 2
+    per = np.add.reduceat(b2 / (1.0 - a2), bank.offsets[:-1]) if bank.n_filters else np.zeros(0)
+    per = np.where(np.diff(bank.offsets) > 0, per, 1.0)
+    scale = np.repeat(np.sqrt(power / per), np.diff(bank.offsets))
+    return Bank(bank.offsets.copy(), bank.a1.copy(), (bank.b0 * scale).astype(np.complex64), bank.delay.copy())
+
+
 def online_bank_global(world: int = 1, per_rank: int = ONLINE["n_templates"]) -> Bank:
     """Bank of world x per_rank online-sized templates for a run sharded by template over
     world GPUs (each rank filters a contiguous slice).  world = 1 gives online_bank(per_rank)."""
