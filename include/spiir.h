@@ -322,6 +322,9 @@ int spiir_frontend_create(int n_det, int M, int n_dec_taps, const float *dec_tap
                           int n_white_taps, const float *white_taps_host, int64_t max_in,
                           spiir_frontend_t *out);
 void spiir_frontend_destroy(spiir_frontend_t fe);
+/* Shape query: detectors, decimation factor and the largest input segment.  Any output
+ * pointer may be NULL. */
+int spiir_frontend_info(spiir_frontend_t fe, int *n_det, int *M, int64_t *max_in);
 /* Zero the histories (a new stream).  Enqueued on stream. */
 int spiir_frontend_reset(spiir_frontend_t fe, void *stream);
 /* One segment: strain_dev [n_det][strain_pitch] f32 at the input rate, n_in samples (a positive
@@ -472,7 +475,8 @@ int spiir_search_run(spiir_search_t search, const float *strain_dev, int64_t str
  *   u_dev [T][n] complex.  ckpt_dev: NULL, or [ceil(n / ckpt_every)][T][F] complex that
  *   receives y_l[j ckpt_every - 1] for every j (the state before sample j ckpt_every);
  *   ckpt_every a multiple of 32 in [32, 8192].  Delays may exceed n.  Enqueued on stream.
- * With checkpoints the segment starting states are found by FP64 jumps,
+ * With checkpoints the segment starting states are found by jumps in double-float (pairs of
+ * FP32 numbers, about 44 significant bits; no FP64 runs on the device),
  *   y[(j+1)C - 1] = a^C y[jC - 1] + b a^((j+1)C - 1 - d) [jC <= d < (j+1)C],
  * and the segments run in parallel in FP32; without, one pass per template over all n, which
  * holds at most 864 filters per template (SPIIR_EUNSUPPORTED above). */
@@ -488,9 +492,9 @@ int spiir_impulse_forward(int n_templates, int filters_per_template, const float
  *   grad_a1 = sum_k lambda_l[k] conj(y_l[k-1]), grad_b0 = lambda_l[d_l] (0 if d_l >= n),
  *   grad_s0 = conj(a1_l) lambda_l[0], where lambda_l[n] = 0 and
  *   lambda_l[k] = grad_u_t[k] + conj(a1_l) lambda_l[k+1].
- * Parallel over checkpoint segments: each segment's own part of lambda, an FP64 scan over the
+ * Parallel over checkpoint segments: each segment's own part of lambda, a double-float scan over the
  * segments for their boundary values, then states recomputed from the checkpoints and the
- * gradients formed segment by segment (added over segments in FP64, in order).  Shared memory
+ * gradients formed segment by segment (added over segments in double-float, in order).  Shared memory
  * grows with ckpt_every: SPIIR_EUNSUPPORTED when it does not fit.  Enqueued on stream. */
 int spiir_impulse_backward(int n_templates, int filters_per_template, const float *a1_dev,
                            const float *b0_dev, const int32_t *delay_dev, int64_t n,
@@ -521,6 +525,18 @@ int spiir_pipeline_reset(spiir_pipeline_t pipe, void *stream);
 int spiir_pipeline_run(spiir_pipeline_t pipe, const float *strain_dev, int64_t strain_pitch,
                        int64_t n, float *max_stat_dev, int32_t *argmax_dev,
                        float *null_stat_dev, float *skymap_dev, void *stream);
+
+/* The whole path from raw strain (Sec. II.A - II.C): strain_dev [n_det][strain_pitch] at the
+ * front end's input rate, n_in samples (a positive multiple of its M with n_in / M <= max_chunk),
+ * goes through spiir_frontend_run (down-sampling and whitening, its own lags) into a buffer the
+ * pipeline owns, then through the step of spiir_pipeline_run with n = n_in / M.  Outputs as for
+ * spiir_pipeline_run.  fe must have the bank's n_det; it keeps its own stream of histories, so
+ * drive it only through this call while it is attached to a stream of chunks.  Four or more
+ * launches on stream.  Errors: SPIIR_EINVAL, SPIIR_ENOMEM (first call), SPIIR_ECUDA. */
+int spiir_pipeline_run_frontend(spiir_pipeline_t pipe, spiir_frontend_t fe, const float *strain_dev,
+                                int64_t strain_pitch, int64_t n_in, float *max_stat_dev,
+                                int32_t *argmax_dev, float *null_stat_dev, float *skymap_dev,
+                                void *stream);
 
 /* Same with host buffers: copies the strain [n_det][n] to the device, runs, copies
  * max_stat, argmax and null_stat [n_templates][n] back and synchronises stream.  Host

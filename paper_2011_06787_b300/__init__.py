@@ -252,6 +252,17 @@ class Pipeline:
                                               _dev_ptr(skymap) if skymap is not None else None,
                                               _stream_ptr(stream)))
 
+    def run_frontend(self, fe, strain, max_stat, argmax, null_stat, skymap=None, stream=None):
+        """Raw strain at the front end's input rate, [n_det][n_in] float32 CUDA tensor: front end
+        (down-sampling, whitening) then this pipeline's step, n = n_in / M (spiir_pipeline_run_frontend)."""
+        import torch
+        _require_cuda(strain, torch.float32, "strain")
+        check(native.lib().spiir_pipeline_run_frontend(self._h, fe.handle, _dev_ptr(strain), strain.stride(0),
+                                                       strain.shape[1], _dev_ptr(max_stat), _dev_ptr(argmax),
+                                                       _dev_ptr(null_stat),
+                                                       _dev_ptr(skymap) if skymap is not None else None,
+                                                       _stream_ptr(stream)))
+
     def run_host(self, strain: np.ndarray, max_stat: np.ndarray, argmax: np.ndarray, null_stat: np.ndarray,
                  stream=None):
         """Host buffers (ideally page-locked): strain [n_det][n] float32 C-contiguous; outputs [T][n]."""

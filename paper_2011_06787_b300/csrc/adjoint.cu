@@ -14,7 +14,8 @@
 //
 // Device mapping (K3).  Both directions are parallel over checkpoint segments of C samples
 // (C a multiple of 32):
-//   forward   1. one thread per filter jumps from segment to segment in FP64,
+//   forward   1. one thread per filter jumps from segment to segment in double-float (pairs
+//                of FP32 numbers, about 44 significant bits),
 //                y[(j+1)C - 1] = a^C y[jC - 1] + b a^((j+1)C - 1 - d) [jC <= d < (j+1)C],
 //                and writes every segment's starting state (the checkpoints);
 //             2. one block per (segment, template) runs the C steps in FP32 from its checkpoint,
@@ -22,15 +23,15 @@
 //                filters per sample with a transposed shared-memory reduction every 32 steps.
 //   backward  1. per (segment, template, filter group): lambda over the segment in reverse from
 //                a zero boundary (the segment's own contribution);
-//             2. one thread per filter scans the segments in reverse in FP64: the boundary of
+//             2. one thread per filter scans the segments in reverse in double-float: the boundary of
 //                segment j is lambda at its end, lambda[jC] = local_j + conj(a)^len_j lambda_end;
 //                grad_s0 = conj(a) lambda[0];
 //             3. per (segment, template, filter group): states are recomputed from the
 //                checkpoint (every 32nd kept in shared memory, each 32-step block recomputed
 //                into registers), lambda runs in reverse from the boundary, and the segment's
 //                share of grad_a1 (blocked sums) and grad_b0 (at k = d) are formed;
-//             4. one thread per filter adds the segments' shares of grad_a1 in FP64, in order.
-// The FP64 jumps make every segment start exact to FP32 rounding, so FP32 error does not
+//             4. one thread per filter adds the segments' shares of grad_a1 in double-float, in order.
+// The double-float jumps make every segment start exact to FP32 rounding, so FP32 error does not
 // accumulate over the whole response.  Without a checkpoint buffer the forward runs one
 // block per template sequentially over all n samples.
 #include <algorithm>
@@ -94,41 +95,74 @@ __global__ void k_impulse_fwd(const float2 *__restrict__ a1, const float2 *__res
     }
 }
 
-// complex FP64 arithmetic for the segment jumps
-struct c64 {
-    double x, y;
+// Double-float arithmetic for the segment jumps: a value is the unevaluated sum hi + lo of two
+// FP32 numbers (about 44 significant bits), built from the error-free transformations two-sum
+// (Knuth) and two-product by FMA (Dekker's product with a fused multiply-add), as in the
+// double-double library of Hida, Li and Bailey.  It runs on the FP32 pipe: no FP64 runs on the
+// device.
+struct df {
+    float hi, lo;
 };
-__device__ __forceinline__ c64 cmul64(c64 a, c64 b) { return {fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)}; }
-__device__ __forceinline__ c64 cpow64(c64 a, int64_t m) {
-    c64 r{1.0, 0.0};
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    const df t = two_sum(x.lo, y.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ float df_round(df x) { return x.hi + x.lo; }
+
+struct cdf {
+    df x, y;
+};
+__device__ __forceinline__ cdf cdf_of(float2 v) { return {{v.x, 0.f}, {v.y, 0.f}}; }
+__device__ __forceinline__ cdf cmul_df(cdf a, cdf b) {
+    return {df_add(df_mul(a.x, b.x), df_neg(df_mul(a.y, b.y))), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
+}
+__device__ __forceinline__ cdf cadd_df(cdf a, cdf b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
+__device__ __forceinline__ cdf cpow_df(cdf a, int64_t m) {
+    cdf r{{1.f, 0.f}, {0.f, 0.f}};
     while (m > 0) {
-        if (m & 1) r = cmul64(r, a);
-        a = cmul64(a, a);
+        if (m & 1) r = cmul_df(r, a);
+        a = cmul_df(a, a);
         m >>= 1;
     }
     return r;
 }
-__device__ __forceinline__ float2 f2(c64 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ float2 f2(cdf a) { return make_float2(df_round(a.x), df_round(a.y)); }
 
-// Forward 1: segment starting states (checkpoints) by FP64 jumps.
+// Forward 1: segment starting states (checkpoints) by double-float jumps.
 __global__ void k_fwd_jump(const float2 *__restrict__ a1, const float2 *__restrict__ b0,
                            const int *__restrict__ dly, const float2 *__restrict__ s0, int64_t TF, int64_t n, int C,
                            int nck, float2 *__restrict__ ck) {
     const int64_t fi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (fi >= TF) return;
-    const c64 a{a1[fi].x, a1[fi].y}, b{b0[fi].x, b0[fi].y};
+    const cdf a = cdf_of(a1[fi]), b = cdf_of(b0[fi]);
     const int64_t d = dly[fi];
-    const c64 aC = cpow64(a, C);
-    c64 y{s0[fi].x, s0[fi].y};
+    const cdf aC = cpow_df(a, C);
+    cdf y = cdf_of(s0[fi]);
     ck[fi] = f2(y);
     for (int j = 0; j + 1 < nck; ++j) {
         const int64_t k0 = (int64_t)j * C;
-        y = cmul64(aC, y);
-        if (d >= k0 && d < k0 + C) {
-            const c64 t = cmul64(b, cpow64(a, k0 + C - 1 - d));
-            y.x += t.x;
-            y.y += t.y;
-        }
+        y = cmul_df(aC, y);
+        if (d >= k0 && d < k0 + C) y = cadd_df(y, cmul_df(b, cpow_df(a, k0 + C - 1 - d)));
         ck[(int64_t)(j + 1) * TF + fi] = f2(y);
     }
 }
@@ -281,33 +315,32 @@ __global__ void k_bwd_local(const float2 *__restrict__ a1, int F, int64_t n, int
     if (ok1) work[j * TF + fi + 1] = make_float2(r.y, i.y);
 }
 
-// Backward 2: FP64 reverse scan over the segments of one filter.  work[j][fi] holds the local
+// Backward 2: double-float reverse scan over the segments of one filter.  work[j][fi] holds the local
 // lambda at the start of segment j on entry and lambda at its end (the boundary) on exit;
 // work[nck][fi] and work[nck + 1][fi] receive a^16 and a^64 for the segment pass.
 __global__ void k_bwd_scan(const float2 *__restrict__ a1, int64_t TF, int64_t n, int C, int nck,
                            float2 *__restrict__ work, float2 *__restrict__ gb, float2 *__restrict__ gs) {
     const int64_t fi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (fi >= TF) return;
-    const c64 ac{a1[fi].x, -a1[fi].y};  // conj(a)
-    const c64 pC = cpow64(ac, C), pL = cpow64(ac, n - (int64_t)(nck - 1) * C);
-    c64 lam{0.0, 0.0};  // lambda at the end of the current segment (lambda[n] = 0)
-    const c64 a{a1[fi].x, a1[fi].y};
-    work[(int64_t)nck * TF + fi] = f2(cpow64(a, kL2));
-    work[(int64_t)(nck + 1) * TF + fi] = f2(cpow64(a, kL1));
+    const cdf ac = cdf_of(make_float2(a1[fi].x, -a1[fi].y));  // conj(a)
+    const cdf pC = cpow_df(ac, C), pL = cpow_df(ac, n - (int64_t)(nck - 1) * C);
+    cdf lam{{0.f, 0.f}, {0.f, 0.f}};  // lambda at the end of the current segment (lambda[n] = 0)
+    const cdf a = cdf_of(a1[fi]);
+    work[(int64_t)nck * TF + fi] = f2(cpow_df(a, kL2));
+    work[(int64_t)(nck + 1) * TF + fi] = f2(cpow_df(a, kL1));
     for (int j = nck - 1; j >= 0; --j) {
         float2 *w = work + (int64_t)j * TF + fi;
         const float2 loc = *w;
         *w = f2(lam);
-        const c64 q = cmul64(j == nck - 1 ? pL : pC, lam);
-        lam = {loc.x + q.x, loc.y + q.y};
+        lam = cadd_df(cdf_of(loc), cmul_df(j == nck - 1 ? pL : pC, lam));
     }
-    gs[fi] = f2(cmul64(ac, lam));  // conj(a) lambda[0]
+    gs[fi] = f2(cmul_df(ac, lam));  // conj(a) lambda[0]
     gb[fi] = make_float2(0.f, 0.f);  // set by the segment holding d, if d < n
 }
 
 // Backward 3: per (segment, template, filter group), one filter pair per thread.  work[j][fi]:
 // the boundary lambda on entry, the segment's share of grad_a1 on exit; work[nck][fi] and
-// work[nck + 1][fi] hold a^16 and a^64 (FP64, rounded).  States at every 64th step come from
+// work[nck + 1][fi] hold a^16 and a^64 (double-float, rounded).  States at every 64th step come from
 // jumps by a^64 (shared memory), at every 16th from jumps by a^16 (registers), and each 16-step
 // block is recomputed step by step into registers before lambda runs back over it.
 struct Pair {  // two filters as packed FP32 pairs: real parts, imaginary parts
@@ -398,15 +431,15 @@ __global__ void __launch_bounds__(256) k_bwd_seg(const float2 *__restrict__ a1, 
     const u64 r16 = pack2(a16[0].x, a16[1].x), i16 = pack2(a16[0].y, a16[1].y), ni16 = neg2(i16);
     const u64 r64 = pack2(a64[0].x, a64[1].x), i64 = pack2(a64[0].y, a64[1].y), ni64 = neg2(i64);
     // impulse terms added by the jumps over the 64- and 16-step blocks that hold the impulse:
-    // b a^(end - d), end the block's last step (FP64)
+    // b a^(end - d), end the block's last step (double-float)
     float2 t64[2], t16[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         t64[h] = t16[h] = make_float2(0.f, 0.f);
         if (ed[h] >= 0) {
-            const c64 a{av[h].x, av[h].y}, b{bv[h].x, bv[h].y};
-            t64[h] = f2(cmul64(b, cpow64(a, kL1 - 1 - ed[h] % kL1)));
-            t16[h] = f2(cmul64(b, cpow64(a, kL2 - 1 - ed[h] % kL2)));
+            const cdf a = cdf_of(av[h]), b = cdf_of(bv[h]);
+            t64[h] = f2(cmul_df(b, cpow_df(a, kL1 - 1 - ed[h] % kL1)));
+            t16[h] = f2(cmul_df(b, cpow_df(a, kL2 - 1 - ed[h] % kL2)));
         }
     }
     // 64-step marks
@@ -487,17 +520,17 @@ __global__ void __launch_bounds__(256) k_bwd_seg(const float2 *__restrict__ a1, 
     }
 }
 
-// Backward 4: grad_a1 = the segments' shares added in FP64, in segment order.
+// Backward 4: grad_a1 = the segments' shares added in double-float, in segment order.
 __global__ void k_bwd_sum(int64_t TF, int nck, const float2 *__restrict__ work, float2 *__restrict__ ga) {
     const int64_t fi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (fi >= TF) return;
-    double x = 0.0, y = 0.0;
+    df x{0.f, 0.f}, y{0.f, 0.f};
     for (int j = 0; j < nck; ++j) {
         const float2 v = work[(int64_t)j * TF + fi];
-        x += v.x;
-        y += v.y;
+        x = df_add(x, {v.x, 0.f});
+        y = df_add(y, {v.y, 0.f});
     }
-    ga[fi] = make_float2((float)x, (float)y);
+    ga[fi] = make_float2(df_round(x), df_round(y));
 }
 
 // threads per block of the backward segment kernel (one filter pair each): groups of at most

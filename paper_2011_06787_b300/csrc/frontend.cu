@@ -291,6 +291,14 @@ extern "C" int spiir_frontend_create(int n_det, int M, int n_dec_taps, const flo
 
 extern "C" void spiir_frontend_destroy(spiir_frontend_t f) { fe_free(f); }
 
+extern "C" int spiir_frontend_info(spiir_frontend_t f, int *n_det, int *M, int64_t *max_in) {
+    if (!f) return fail(SPIIR_EINVAL, "front end is NULL");
+    if (n_det) *n_det = f->n_det;
+    if (M) *M = f->M;
+    if (max_in) *max_in = f->max_in;
+    return SPIIR_OK;
+}
+
 extern "C" int spiir_frontend_reset(spiir_frontend_t f, void *stream) {
     clear_error();
     if (!f) return fail(SPIIR_EINVAL, "front end is NULL");

@@ -23,6 +23,7 @@ struct spiir_pipeline_s {
     float *strain_dev = nullptr;
     float *ms_dev = nullptr, *nl_dev = nullptr;
     int32_t *am_dev = nullptr;
+    float *fe_out = nullptr;  // [n_det][max_chunk]: front-end output of spiir_pipeline_run_frontend
     // asynchronous host-buffer steps: two staging sets alternate; the outputs of a step go to
     // the host on the copy stream while the next step runs (set 0 is the staging above)
     bool async_ready = false;
@@ -55,6 +56,7 @@ static void pipe_free(spiir_pipeline_s *p) {
     dev_free(p->ms_dev);
     dev_free(p->nl_dev);
     dev_free(p->am_dev);
+    dev_free(p->fe_out);
     delete p;
 }
 
@@ -164,6 +166,27 @@ extern "C" int spiir_pipeline_run(spiir_pipeline_t p, const float *strain, int64
     if (n < 1 || n > p->max_chunk) return fail(SPIIR_EINVAL, "n = %lld outside [1, %lld]", (long long)n, (long long)p->max_chunk);
     if (spitch < n) return fail(SPIIR_EINVAL, "strain_pitch < n");
     return pipe_run(p, strain, spitch, n, ms, am, nl, map, (cudaStream_t)stream);
+}
+
+extern "C" int spiir_pipeline_run_frontend(spiir_pipeline_t p, spiir_frontend_t fe, const float *strain_dev,
+                                           int64_t strain_pitch, int64_t n_in, float *ms, int32_t *am, float *nl,
+                                           float *map, void *stream) {
+    clear_error();
+    if (!p || !fe) return fail(SPIIR_EINVAL, "pipeline or front end is NULL");
+    if (!strain_dev || !ms || !am || !nl) return fail(SPIIR_EINVAL, "NULL buffer");
+    int nd = 0, M = 1;
+    int64_t max_in = 0;
+    SPIIR_TRY(spiir_frontend_info(fe, &nd, &M, &max_in));
+    if (nd != p->bank->n_det) return fail(SPIIR_EINVAL, "front end has %d detectors, the bank %d", nd, p->bank->n_det);
+    if (n_in < M || n_in % M != 0 || n_in / M > p->max_chunk)
+        return fail(SPIIR_EINVAL, "n_in = %lld must be a positive multiple of %d with n_in / %d <= %lld",
+                    (long long)n_in, M, M, (long long)p->max_chunk);
+    if (!p->fe_out)
+        SPIIR_TRY(dev_alloc((void **)&p->fe_out, sizeof(float) * (size_t)nd * p->max_chunk, "front-end output"));
+    cudaStream_t s = (cudaStream_t)stream;
+    NvtxRange r("spiir.frontend_chunk");
+    SPIIR_TRY(spiir_frontend_run(fe, strain_dev, strain_pitch, n_in, p->fe_out, p->max_chunk, stream));
+    return pipe_run(p, p->fe_out, p->max_chunk, n_in / M, ms, am, nl, map, s);
 }
 
 extern "C" int spiir_pipeline_run_host(spiir_pipeline_t p, const float *strain_host, int64_t n, float *ms_host,

@@ -64,6 +64,8 @@ SIGNATURES = {
     "spiir_frontend_create": (_I, [_I, _I, _I, _P, _I, _P, _I64, ctypes.POINTER(_P)]),
     "spiir_frontend_destroy": (None, [_P]),
     "spiir_frontend_reset": (_I, [_P, _P]),
+    "spiir_frontend_info": (_I, [_P, _P, _P, _P]),
+    "spiir_pipeline_run_frontend": (_I, [_P, _P, _P, _I64, _I64, _P, _P, _P, _P, _P]),
     "spiir_frontend_run": (_I, [_P, _P, _I64, _I64, _P, _I64, _P]),
     "spiir_xi2_candidates": (_I, [_P, _I, _P, _I64, _I64, _P, _I, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "spiir_select_workspace_bytes": (_I, [_I, _I, _I64, _I, ctypes.POINTER(_SZ)]),

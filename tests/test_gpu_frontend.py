@@ -94,3 +94,47 @@ def test_frontend_rejects_bad_segments():
         fe.run(torch.zeros((2, 100), device="cuda"))      # not a multiple of 8
     with pytest.raises(sp.SpiirError):
         fe.run(torch.zeros((2, 2048), device="cuda"))     # above max_in
+
+
+def test_raw_strain_to_statistic_in_one_call():
+    """spiir_pipeline_run_frontend: 16384 Hz strain of three detectors through the front end,
+    the filter bank and the coherent scan per 1 s segment, against the oracle's front end,
+    filter bank and scan composed over the same stream."""
+    import torch
+    import paper_2011_06787_b300 as sp
+    from helpers import assert_coherent_close
+    n_det, M, Ld, Lw, seg, n_seg = 3, 8, 192, 1025, 16384, 3
+    x = _colored(11, n_det, seg * n_seg, (0.9, 0.5, -0.3))
+    h = oracle.lowpass_taps(Ld, M, 0.9).astype(np.float32)
+    w = np.stack([oracle.whitening_kernel(_psd_ar1(2048.0, 4096, p, 1.0), 2048.0, Lw) for p in (0.8, 0.4, -0.2)]
+                 ).astype(np.float32)
+    fe = sp.Frontend(n_det, h, M, w, seg)
+    det = synth.detectors(11, n_det)
+    sigma = synth.noise_weights(11, n_det, 0.5, 2.0)
+    bank = synth.random_bank(synth.rng(11, "misc", 1), [30, 200, 77, 410], d_max=1500)
+    sky = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 4, 2048.0))
+    pipe = sp.Pipeline(sp.Bank(n_det, bank.offsets, bank.a1, bank.b0, bank.delay), sky, max_chunk=seg // M)
+    T, n, H = bank.n_templates, seg // M, sky.halo
+    outs = []
+    for s in range(n_seg):
+        ms = torch.empty((T, n), device="cuda")
+        am = torch.empty((T, n), dtype=torch.int32, device="cuda")
+        nl = torch.empty((T, n), device="cuda")
+        pipe.run_frontend(fe, torch.from_numpy(np.ascontiguousarray(x[:, s * seg:(s + 1) * seg])).cuda(), ms, am, nl)
+        outs.append([v.cpu().numpy() for v in (ms, am, nl)])
+    torch.cuda.synchronize()
+    sp.device_status()
+    y_or, _, _ = oracle.frontend(x, h, M, w)
+    z_or, _, _ = oracle.filter_bank(y_or, bank.offsets, bank.a1, bank.b0, bank.delay)
+    _, G, d_or = oracle.sky_geometry(det, sigma, 4, 2048.0)
+    # output j of segment s is 2048 Hz sample s n + j - H
+    zp = np.concatenate([np.zeros((T, n_det, 2 * H)), z_or], axis=2)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(zp, G, d_or, H, n * n_seg, skymap=True)
+    ms = np.concatenate([o[0] for o in outs], axis=1)
+    am = np.concatenate([o[1] for o in outs], axis=1)
+    nl = np.concatenate([o[2] for o in outs], axis=1)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    bad = torch.zeros((n_det, 100), device="cuda")                                  # not a multiple of 8
+    with pytest.raises(sp.SpiirError):
+        pipe.run_frontend(fe, bad, torch.empty((T, n), device="cuda"), torch.empty((T, n), dtype=torch.int32,
+                          device="cuda"), torch.empty((T, n), device="cuda"))
