@@ -256,9 +256,11 @@ __global__ void __launch_bounds__(NL, (S == 8 && NL == 128) ? 5 : 1) k_filter_ba
 
 // Persistent form: a grid of resident blocks takes (bank, block, detector) work items from a
 // shared counter (atomic fetch-and-add, no waiting) in the order of the item list, so that
-// banks of uneven size and different rates share one launch.
+// banks of uneven size and different rates share one launch.  The default shape asks for four
+// resident blocks (at most 128 registers), which the multirate banks' shared memory allows.
 template <int S, int NL, int R>
-__global__ void __launch_bounds__(NL, 1) k_filter_bank_persistent(const __grid_constant__ PersistArgs p) {
+__global__ void __launch_bounds__(NL, (S == 8 && NL == 128) ? 4 : 1)
+    k_filter_bank_persistent(const __grid_constant__ PersistArgs p) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int item_s;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);

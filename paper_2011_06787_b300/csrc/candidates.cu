@@ -6,8 +6,8 @@
 // candidate of its template, and each (detector, template, second) keeps the largest one (the
 // earliest among equals).  All decisions are taken on |z|^2 = re*re + im*im in FP32 with each
 // operation rounded (no contraction), so that they are reproducible bit for bit.
-//   k_select:  one block per (32 samples, detector); warp w reads templates w, w + 8, ... with
-//              coalesced 8-byte loads (lane = sample), the 8 warps combine in shared memory and
+//   k_select:  one block per (32 samples, detector); warp w reads templates w, w + 32, ... with
+//              coalesced 8-byte loads (lane = sample), the 32 warps combine in shared memory and
 //              a sample over the threshold posts the key (|z|^2 bits, ~k) to its slot
 //              (detector, template, second) with a 64-bit atomicMax: the largest value wins,
 //              then the smallest sample.
@@ -39,7 +39,7 @@
 
 namespace spiir {
 
-constexpr int kSelWarps = 8;
+constexpr int kSelWarps = 32;
 constexpr int kSelThreads = 32 * kSelWarps;
 constexpr int kSelUnroll = 16;
 constexpr int kCompThreads = 1024;
@@ -310,7 +310,9 @@ __global__ void __launch_bounds__(kPtThreads) k_points(const __grid_constant__ P
 // a warp reduces its S (value, pixel) pairs in log2(32) butterfly steps that halve the pairs
 // a lane holds at each of the first log2(S) steps (S + log2(32 / S) shuffles per value instead
 // of 5 S), then the warps combine through shared memory.
-constexpr int kPtWP = 192;
+constexpr int kPtWP = 192;        // window entries per (shift, companion): wide skies
+constexpr int kPtWPNarrow = 96;   // the same when the relative delays span at most 96 samples
+constexpr int kPtChunkThreads = 128;
 
 __device__ __forceinline__ void take_pair(float &kv, int &kp, float rv, int rp) {
     if (rv > kv || (rv == kv && rp < kp)) {
@@ -397,10 +399,10 @@ __device__ __forceinline__ PtItem<ND> decode_item(const PointArgs &a, int64_t it
 
 // Start the copies of an item's windows into buf ([S][NC][kPtWP]): one warp per
 // (shift column, companion) window, lanes striding it, 8-byte asynchronous copies.
-template <int ND, int S>
+template <int ND, int S, int WP>
 __device__ __forceinline__ void stage_item(const PointArgs &a, const PtItem<ND> &it, float2 *buf, int wid, int lane) {
     constexpr int NC = ND - 1;
-    constexpr int kWarps = kPtThreads / 32;
+    constexpr int kWarps = kPtChunkThreads / 32;
     for (int wi = wid; wi < S * NC; wi += kWarps) {
         const int i = wi / NC, q = wi % NC;
         if (!((it.okmask >> i) & 1u)) continue;
@@ -413,17 +415,17 @@ __device__ __forceinline__ void stage_item(const PointArgs &a, const PtItem<ND> 
         }
         const int64_t s = (int64_t)a.first_shift + it.s_first + i;
         const float2 *row = a.snr + ((int64_t)it.t * ND + J) * a.pitch + it.e - s * (q + 1) * a.step + dq;
-        float2 *dst = buf + (i * NC + q) * kPtWP;
+        float2 *dst = buf + (i * NC + q) * WP;
         for (int j = lane; j < len; j += 32) cp_async8(dst + j, row + j);
     }
 }
 
-template <int ND, int S>
-__global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_constant__ PointArgs a) {
+template <int ND, int S, int WP>
+__global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __grid_constant__ PointArgs a) {
     using Entry = TabEntry<ND>;
     constexpr int NC = ND - 1;                    // companions of the reference detector
-    constexpr int kShiftWords = NC * kPtWP;       // float2 entries per shift
-    constexpr int kWarps = kPtThreads / 32;
+    constexpr int kShiftWords = NC * WP;          // float2 entries per shift
+    constexpr int kWarps = kPtChunkThreads / 32;
     constexpr int kLog = (S == 1) ? 0 : (S == 2) ? 1 : (S == 4) ? 2 : (S == 8) ? 3 : (S == 16) ? 4 : 5;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_v[kWarps][S];
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
     int64_t item = blockIdx.x;
     if (item >= n_items) return;
     PtItem<ND> cur = decode_item<ND, S>(a, item, n_chunks, lane);
-    stage_item<ND, S>(a, cur, wbuf, wid, lane);
+    stage_item<ND, S, WP>(a, cur, wbuf, wid, lane);
     cp_async_commit();
     for (int k = 0; item < n_items; ++k, item += gridDim.x) {
         float2 *win = wbuf + (k & 1) * S * kShiftWords;
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
         PtItem<ND> nit = cur;
         if (nxt < n_items) {
             nit = decode_item<ND, S>(a, nxt, n_chunks, lane);
-            stage_item<ND, S>(a, nit, wbuf + ((k + 1) & 1) * S * kShiftWords, wid, lane);
+            stage_item<ND, S, WP>(a, nit, wbuf + ((k + 1) & 1) * S * kShiftWords, wid, lane);
         }
         cp_async_commit();
         cp_async_wait<1>();
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
         // chunk (100 shifts in chunks of 16 end with 4) evaluates only the shifts it has
         auto scan = [&](auto na) {
             constexpr int NA = decltype(na)::value;
-            for (int p = tid; p < a.n_pix; p += kPtThreads) {
+            for (int p = tid; p < a.n_pix; p += kPtChunkThreads) {
                 // the entry's fields of detectors r and Jq[q] at run-time offsets (a select over
                 // a register copy of the entry would be turned back into a local-memory array)
                 const Entry *ep = tab + p;
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
                     const float u0 = ep->u[cur.Jq[q]][0], u1 = ep->u[cur.Jq[q]][1];
                     U0[q] = pack2(u0, u0);
                     U1[q] = pack2(u1, u1);
-                    wq[q] = reinterpret_cast<const float *>(win + q * kPtWP + (ep->off[cur.Jq[q]] - offr - cur.dmn[q]));
+                    wq[q] = reinterpret_cast<const float *>(win + q * WP + (ep->off[cur.Jq[q]] - offr - cur.dmn[q]));
                 }
 #pragma unroll
                 for (int i = 0; i < NA; ++i) {
@@ -542,7 +544,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) k_points_chunked(const __grid_c
                             // companion slot of detector J and its window start (J != r)
                             const int q = (J < r) ? J : J - 1;
                             const int dm = (J < r) ? cur.dmn[J < NC ? J : 0] : cur.dmn[J > 0 ? J - 1 : 0];
-                            const float2 w = (J == r) ? wr : win[i * kShiftWords + q * kPtWP + en.off[J] - offr - dm];
+                            const float2 w = (J == r) ? wr : win[i * kShiftWords + q * WP + en.off[J] - offr - dm];
                             const float u = un[J * (ND - 2) + j];
                             cr = fmaf(u, w.x, cr);
                             ci = fmaf(u, w.y, ci);
@@ -573,30 +575,36 @@ static int resident_blocks(K kern, int threads, size_t smem, int max_smem, int &
     return SPIIR_OK;
 }
 
-template <int ND, int S>
+template <int ND, int S, int WP>
 static int launch_chunked(const PointArgs &a, size_t smem, cudaStream_t stream) {
-    auto kern = k_points_chunked<ND, S>;
+    auto kern = k_points_chunked<ND, S, WP>;
     int n_sm = 0, per_sm = 0;
-    SPIIR_TRY(resident_blocks(kern, kPtThreads, smem, kPtChunkSmem, n_sm, per_sm));
+    SPIIR_TRY(resident_blocks(kern, kPtChunkThreads, smem, kPtChunkSmem, n_sm, per_sm));
     const int64_t items = (int64_t)a.max_cand * ((a.n_shifts + S - 1) / S);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
-    kern<<<grid, kPtThreads, smem, stream>>>(a);
+    kern<<<grid, kPtChunkThreads, smem, stream>>>(a);
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }
 
 // shifts per chunk: 1 for the zero-lag scan, else as many as keep the double-buffered windows
-// within two blocks per SM
+// within the shared memory of four blocks per SM (narrow windows) or two (wide ones)
 static int chunk_shifts(int nd, int n_shifts) { return n_shifts == 1 ? 1 : (nd <= 3 ? 16 : 8); }
+
+template <int ND, int WP>
+static int dispatch_chunked_wp(const PointArgs &a, cudaStream_t stream) {
+    const size_t win1 = sizeof(float2) * (ND - 1) * WP;  // one shift's windows
+    switch (chunk_shifts(ND, a.n_shifts)) {
+        case 1: return launch_chunked<ND, 1, WP>(a, 2 * win1, stream);
+        case 8: return launch_chunked<ND, 8, WP>(a, 2 * 8 * win1, stream);
+        default: return launch_chunked<ND, 16, WP>(a, 2 * 16 * win1, stream);
+    }
+}
 
 template <int ND>
 static int dispatch_chunked(const PointArgs &a, cudaStream_t stream) {
-    const size_t win1 = sizeof(float2) * (ND - 1) * kPtWP;  // one shift's windows
-    switch (chunk_shifts(ND, a.n_shifts)) {
-        case 1: return launch_chunked<ND, 1>(a, 2 * win1, stream);
-        case 8: return launch_chunked<ND, 8>(a, 2 * 8 * win1, stream);
-        default: return launch_chunked<ND, 16>(a, 2 * 16 * win1, stream);
-    }
+    return a.Wmax <= kPtWPNarrow ? dispatch_chunked_wp<ND, kPtWPNarrow>(a, stream)
+                                 : dispatch_chunked_wp<ND, kPtWP>(a, stream);
 }
 
 template <int ND, bool SMEM_TAB>
