@@ -164,6 +164,7 @@ struct PointArgs {
     int dmin[4][4], dmax[4][4];  // range of Delta_J - Delta_r over the sky, [r][J]
     int Wmax;                    // largest window, entries per detector in shared memory
     size_t tab_bytes;            // table staged in shared memory (0: read from global)
+    const void *ptab;            // PtEnt<ND>[ND][n_pix]: per-reference entries of the chunked scan
     float *max_stat;             // [max_cand][n_shifts]
     int32_t *argmax;
     float *null_stat;
@@ -355,6 +356,18 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Per-reference-detector entry of the chunked scan: for reference detector r and pixel p, the
+// signal columns U_s[p][r] and U_s[p][J_q] of its companions J_q (q = 0 .. N_d - 2, detector
+// order without r) and each companion's window index Delta_Jq(p) - Delta_r(p) - min over the sky
+// of the same difference.  Two or three 16-byte loads per pixel replace the gather of the
+// general entry's fields at run-time detector indices.
+template <int ND>
+struct __align__(16) PtEnt {
+    float ur[2];
+    float uq[ND - 1][2];
+    int idx[ND - 1];
+};
+
 // One (candidate, chunk) work item as every thread of the block sees it.
 template <int ND>
 struct PtItem {
@@ -432,7 +445,8 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
     __shared__ int s_p[kWarps][S];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const Entry *__restrict__ tab = reinterpret_cast<const Entry *>(a.table);  // read through L1
-    float2 *wbuf = reinterpret_cast<float2 *>(smem);                             // [2][S][NC][kPtWP]
+    const PtEnt<ND> *__restrict__ ptab = reinterpret_cast<const PtEnt<ND> *>(a.ptab);
+    float2 *wbuf = reinterpret_cast<float2 *>(smem);                             // [2][S][NC][WP]
     const int nc = min(*a.n_cand, a.max_cand);
     const int n_chunks = (a.n_shifts + S - 1) / S;
     const int64_t n_items = (int64_t)max(nc, 0) * n_chunks;
@@ -469,21 +483,17 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
         // chunk (100 shifts in chunks of 16 end with 4) evaluates only the shifts it has
         auto scan = [&](auto na) {
             constexpr int NA = decltype(na)::value;
+            const PtEnt<ND> *__restrict__ pr = ptab + (int64_t)r * a.n_pix;
             for (int p = tid; p < a.n_pix; p += kPtChunkThreads) {
-                // the entry's fields of detectors r and Jq[q] at run-time offsets (a select over
-                // a register copy of the entry would be turned back into a local-memory array)
-                const Entry *ep = tab + p;
-                const int offr = ep->off[r];
-                const float ur0 = ep->u[r][0], ur1 = ep->u[r][1];
-                const u64 yb0 = mul2(pack2(ur0, ur0), wr2), yb1 = mul2(pack2(ur1, ur1), wr2);
+                const PtEnt<ND> pe = pr[p];
+                const u64 yb0 = mul2(pack2(pe.ur[0], pe.ur[0]), wr2), yb1 = mul2(pack2(pe.ur[1], pe.ur[1]), wr2);
                 u64 U0[NC], U1[NC];
                 const float *wq[NC];
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
-                    const float u0 = ep->u[cur.Jq[q]][0], u1 = ep->u[cur.Jq[q]][1];
-                    U0[q] = pack2(u0, u0);
-                    U1[q] = pack2(u1, u1);
-                    wq[q] = reinterpret_cast<const float *>(win + q * WP + (ep->off[cur.Jq[q]] - offr - cur.dmn[q]));
+                    U0[q] = pack2(pe.uq[q][0], pe.uq[q][0]);
+                    U1[q] = pack2(pe.uq[q][1], pe.uq[q][1]);
+                    wq[q] = reinterpret_cast<const float *>(win + q * WP + pe.idx[q]);
                 }
 #pragma unroll
                 for (int i = 0; i < NA; ++i) {
@@ -624,6 +634,35 @@ static int dispatch_points(const PointArgs &a, size_t smem, cudaStream_t stream)
     return a.tab_bytes ? launch_points<ND, true>(a, smem, stream) : launch_points<ND, false>(a, smem, stream);
 }
 
+// The per-reference point entries of a sky (built once, after the relative delay ranges).
+template <int ND>
+static int build_point_table(spiir_sky_s *sky) {
+    const int P = sky->n_pix;
+    std::vector<PtEnt<ND>> h((size_t)ND * P);
+    for (int r = 0; r < ND; ++r)
+        for (int p = 0; p < P; ++p) {
+            PtEnt<ND> &e = h[(size_t)r * P + p];
+            const int32_t *dl = &sky->h_delays[(size_t)p * ND];
+            const float *us = &sky->h_usig[(size_t)p * ND * 2];
+            e.ur[0] = us[2 * r];
+            e.ur[1] = us[2 * r + 1];
+            for (int q = 0; q < ND - 1; ++q) {
+                const int J = q < r ? q : q + 1;
+                e.uq[q][0] = us[2 * J];
+                e.uq[q][1] = us[2 * J + 1];
+                e.idx[q] = dl[J] - dl[r] - sky->rel_min[r * ND + J];
+            }
+        }
+    void *d = nullptr;
+    SPIIR_TRY(dev_alloc(&d, h.size() * sizeof(PtEnt<ND>), "candidate point table"));
+    if (cudaMemcpy(d, h.data(), h.size() * sizeof(PtEnt<ND>), cudaMemcpyHostToDevice) != cudaSuccess) {
+        dev_free(d);
+        return fail(SPIIR_ECUDA, "copy of the candidate point table failed");
+    }
+    sky->pt_tab = d;
+    return SPIIR_OK;
+}
+
 }  // namespace spiir
 
 using namespace spiir;
@@ -729,6 +768,15 @@ extern "C" int spiir_coherent_candidates(spiir_sky_t sky, int T, const float *sn
             a.dmax[r][J] = sky->rel_max[r * ND + J];
             Wmax = std::max(Wmax, a.dmax[r][J] - a.dmin[r][J] + 1);
         }
+    if (!sky->pt_tab) {
+        switch (ND) {
+            case 2: SPIIR_TRY(build_point_table<2>(sky)); break;
+            case 3: SPIIR_TRY(build_point_table<3>(sky)); break;
+            case 4: SPIIR_TRY(build_point_table<4>(sky)); break;
+            default: break;
+        }
+    }
+    a.ptab = sky->pt_tab;
     a.Wmax = Wmax;
     a.max_stat = max_stat;
     a.argmax = argmax;

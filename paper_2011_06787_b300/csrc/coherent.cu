@@ -551,6 +551,7 @@ static void sky_free(spiir_sky_s *s) {
     dev_free(s->g_grp);
     dev_free(s->t_ent);
     dev_free(s->d_delays);
+    dev_free(s->pt_tab);
     delete s->t_tab;
     delete s;
 }

@@ -128,6 +128,7 @@ struct spiir_sky_s {
     std::vector<int32_t> h_delays;
     int16_t *d_delays = nullptr;  // [P][n_det] on the device (signal-consistency gather)
     std::vector<int> rel_min, rel_max;  // [r][J]: range of Delta_J - Delta_r over the sky (on first use)
+    void *pt_tab = nullptr;             // [n_det][P] per-reference point entries of the candidate scan (on first use)
     std::vector<float> h_usig, h_unull;
 };
 
