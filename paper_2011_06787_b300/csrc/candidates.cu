@@ -358,14 +358,19 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Per-reference-detector entry of the chunked scan: for reference detector r and pixel p, the
 // signal columns U_s[p][r] and U_s[p][J_q] of its companions J_q (q = 0 .. N_d - 2, detector
-// order without r) and each companion's window index Delta_Jq(p) - Delta_r(p) - min over the sky
-// of the same difference.  Two or three 16-byte loads per pixel replace the gather of the
-// general entry's fields at run-time detector indices.
+// order without r), each companion's window index Delta_Jq(p) - Delta_r(p) - min over the sky of
+// the same difference (10 bits each, packed), and p.  Two or three 16-byte loads per pixel
+// replace the gather of the general entry's fields at run-time detector indices.
+// Order: the sky in chunks of kPtChunkThreads consecutive pixels, each chunk sorted by the
+// companions' window indices, so that the lanes of a warp read nearby window entries (fewer
+// shared-memory bank conflicts) while every thread still visits its pixels in increasing p (one
+// per chunk), which keeps the lowest pixel among equal statistics with a plain comparison.
 template <int ND>
 struct __align__(16) PtEnt {
     float ur[2];
     float uq[ND - 1][2];
-    int idx[ND - 1];
+    uint32_t idx;   // idx_q = (idx >> 10 q) & 1023
+    int p;          // pixel index
 };
 
 // One (candidate, chunk) work item as every thread of the block sees it.
@@ -493,7 +498,7 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
                 for (int q = 0; q < NC; ++q) {
                     U0[q] = pack2(pe.uq[q][0], pe.uq[q][0]);
                     U1[q] = pack2(pe.uq[q][1], pe.uq[q][1]);
-                    wq[q] = reinterpret_cast<const float *>(win + q * WP + pe.idx[q]);
+                    wq[q] = reinterpret_cast<const float *>(win + q * WP + ((pe.idx >> (10 * q)) & 1023u));
                 }
 #pragma unroll
                 for (int i = 0; i < NA; ++i) {
@@ -508,7 +513,7 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
                     const float v = m.x + m.y;
                     if (v > best[i]) {
                         best[i] = v;
-                        arg[i] = p;
+                        arg[i] = pe.p;
                     }
                 }
             }
@@ -639,20 +644,36 @@ template <int ND>
 static int build_point_table(spiir_sky_s *sky) {
     const int P = sky->n_pix;
     std::vector<PtEnt<ND>> h((size_t)ND * P);
-    for (int r = 0; r < ND; ++r)
+    for (int r = 0; r < ND; ++r) {
+        std::vector<std::pair<uint64_t, int>> key(P);
         for (int p = 0; p < P; ++p) {
-            PtEnt<ND> &e = h[(size_t)r * P + p];
+            const int32_t *dl = &sky->h_delays[(size_t)p * ND];
+            uint64_t k = 0;
+            for (int q = 0; q < ND - 1; ++q) {
+                const int J = q < r ? q : q + 1;
+                k = (k << 10) | (uint64_t)(dl[J] - dl[r] - sky->rel_min[r * ND + J]);
+            }
+            key[p] = {k, p};
+        }
+        for (int c0 = 0; c0 < P; c0 += kPtChunkThreads)
+            std::sort(key.begin() + c0, key.begin() + std::min(P, c0 + kPtChunkThreads));
+        for (int i = 0; i < P; ++i) {
+            const int p = key[i].second;
+            PtEnt<ND> &e = h[(size_t)r * P + i];
             const int32_t *dl = &sky->h_delays[(size_t)p * ND];
             const float *us = &sky->h_usig[(size_t)p * ND * 2];
             e.ur[0] = us[2 * r];
             e.ur[1] = us[2 * r + 1];
+            e.idx = 0;
             for (int q = 0; q < ND - 1; ++q) {
                 const int J = q < r ? q : q + 1;
                 e.uq[q][0] = us[2 * J];
                 e.uq[q][1] = us[2 * J + 1];
-                e.idx[q] = dl[J] - dl[r] - sky->rel_min[r * ND + J];
+                e.idx |= (uint32_t)(dl[J] - dl[r] - sky->rel_min[r * ND + J]) << (10 * q);
             }
+            e.p = p;
         }
+    }
     void *d = nullptr;
     SPIIR_TRY(dev_alloc(&d, h.size() * sizeof(PtEnt<ND>), "candidate point table"));
     if (cudaMemcpy(d, h.data(), h.size() * sizeof(PtEnt<ND>), cudaMemcpyHostToDevice) != cudaSuccess) {
