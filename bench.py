@@ -510,7 +510,7 @@ def scale_rate(args, torch, sp, timed_loop):
     """Scale workload: 3 detectors, 1 s chunks of unit white noise, 4096 chirp templates x 600
     filters over whole chirps from 30 Hz (delays up to 151,713 samples), coherent scan over nside
     32 (12288 pixels).  Three forms per chunk: the single-rate pipeline (filter bank at 2048 Hz
-    with 16384-sample delay bins, then the scan), and the same filters recast over 2048 / 512 /
+    with 8192-sample delay bins, then the scan), and the same filters recast over 2048 / 512 /
     128 Hz bands through the batch, per-band plain launches against the graph-replayed
     persistent launch.  The single-rate filter bank and scan are also timed alone on the same
     chunks (the legs of the pipeline step)."""

@@ -90,8 +90,9 @@ int spiir_device_status(int clear);
  *   delay_host [F]  integer delays d_l in samples, 0 <= d_l <= 1<<20.
  * The coefficients are copied; the bank owns its IIR states (all zero) and a strain
  * history of max(d_l) samples per detector (zero).  A bank whose largest delay is at least
- * 16384 samples is cut into delay bins of 16384 samples (see spiir_bank_set_delay_bin), so
- * long templates (a 74 s chirp from 30 Hz spans about 151k samples at 2048 Hz) fit.
+ * 16384 samples is cut into delay bins of 8192 samples with 256-lane blocks (see
+ * spiir_bank_set_delay_bin), so long templates (a 74 s chirp from 30 Hz spans about 151k
+ * samples at 2048 Hz) fit.
  * Errors: SPIIR_EINVAL for bad shapes or values, SPIIR_EUNSUPPORTED when one template has
  * more filters than one thread block can hold (4096 in this build), SPIIR_ENOMEM,
  * SPIIR_ECUDA. */
@@ -138,7 +139,7 @@ int spiir_bank_get_shape(spiir_bank_t bank, int *filters_per_lane, int *lanes_pe
  * later pieces write rows of a bank-owned buffer that one more launch adds into the SNR, in
  * bin order: z_t = sum_j z_t^(j).  delay_bin = 0 keeps every template whole (one window of the
  * bank's largest delay).  B is 0 or a multiple of 4 in [1024, 1<<20].  Keeps the streaming
- * state; synchronises the device.  Default: 0 below a largest delay of 16384, else 16384.
+ * state; synchronises the device.  Default: 0 below a largest delay of 16384, else 8192.
  * get: the bin width, the number of thread blocks and of pieces (templates + extra pieces).
  * Errors: SPIIR_EINVAL; SPIIR_EUNSUPPORTED when a window does not fit in shared memory (the
  * bank keeps its previous layout). */

@@ -811,6 +811,7 @@ extern "C" int spiir_bank_create(int n_det, int n_templates, const int64_t *off,
     // long delays: blocks hold one delay bin each, so that every block's strain window stays
     // within the bin width plus the tile
     b->dbin = dmax >= kBankSplitDelay ? kBankDefaultBin : 0;
+    if (b->dbin > 0 && b->S == 8) b->NL = 256;
     int rc = bank_pack(b);
     if (rc == SPIIR_OK) {
         const size_t smem = bank_smem_bytes(b);

@@ -101,7 +101,7 @@ def test_maximum_delay_carries_across_chunks():
     x = np.zeros((1, n), np.float32)
     x[0, 5] = 1.0
     z, bk = _run_bank(bank, x, chunks=[65536])
-    assert bk.get_delay_bin() == (16384, 2, 2)
+    assert bk.get_delay_bin() == (8192, 2, 2)
     k = np.arange(n)
     ref = sum(np.where(k >= 5 + dl, complex(bl) * complex(al) ** np.maximum(k - 5 - dl, 0), 0) for al, bl, dl in zip(a, b, d))
     assert np.max(np.abs(z[0, 0] - ref)) <= 1e-5 * np.abs(ref).max()
@@ -112,7 +112,7 @@ def test_maximum_delay_carries_across_chunks():
 
 def test_long_templates_across_delay_bins_match_oracle():
     """Templates whose delays span 160k samples (a 78 s chirp at 2048 Hz) stream in 1 s chunks:
-    each is cut into pieces of 16384-sample delay bins, every block stages only its bin's
+    each is cut into pieces of 8192-sample delay bins, every block stages only its bin's
     window, and the pieces add up to the oracle's SNR.  One template stays within one bin,
     one has no filter in bin 0, one is empty."""
     g = synth.rng(0, "misc", 12)
@@ -123,7 +123,7 @@ def test_long_templates_across_delay_bins_match_oracle():
     x = synth.white_noise(0, 2, 165000, sub=12)
     z, bk = _run_bank(bank, x, chunks=[2048])
     dbin, blocks, pieces = bk.get_delay_bin()
-    assert dbin == 16384 and pieces > len(counts)
+    assert dbin == 8192 and pieces > len(counts)
     z_or, _, _ = oracle.filter_bank(x, bank.offsets, bank.a1, bank.b0, bank.delay)
     assert np.all(z[2] == 0)
     assert_snr_close(z[[0, 1, 3, 4]], z_or[[0, 1, 3, 4]])

@@ -5,7 +5,7 @@ chirp templates x 600 IIR filters over the whole chirp from 30 Hz (up to 74 s, d
 stream.
 
 Two forms of the bank run the stream:
-  * the plain single-rate pipeline (filter bank at 2048 Hz, delays cut into 16384-sample bins);
+  * the plain single-rate pipeline (filter bank at 2048 Hz, delays cut into 8192-sample bins);
   * the batched multirate path: the same filters recast over bands of 2048 / 512 / 128 Hz
     (synth.scale_bank_multirate), one persistent filter launch per chunk replayed from a CUDA
     graph, compared with the per-band plain launches of the same multirate bank.
@@ -147,7 +147,7 @@ def test_scale_single_rate_injections_recovered_within_one_pixel_of_the_oracle(w
     bank = w["bank"]
     assert int(bank.delay.max()) > 151000    # whole chirps from 30 Hz: no truncation
     b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
-    assert b.get_delay_bin()[0] == 16384
+    assert b.get_delay_bin()[0] == 8192
     pipe = sp.Pipeline(b, w["sky"], max_chunk=w["n"])
     ms, am, nl = _outputs(bank.n_templates, w["n"])
 
