@@ -445,14 +445,6 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         m.n_templates = T;
         m.n = n;
         m.H = sky->halo;
-        m.n_pix = sky->n_pix;
-        m.ent = sky->t_ent;
-        m.orig = sky->g_orig;
-        m.grp = sky->g_grp;
-        m.n_grp = sky->n_grp;
-        m.q0 = sky->g_q0;
-        m.g0 = sky->g_g0;
-        for (int i = 0; i < 5; ++i) m.slice[i] = sky->t_slice[i];
         m.mw = sky->scan_tmem_mw;
         m.C = tmem_columns(sky->halo, m.mw);
         m.max_stat = max_stat;
@@ -460,9 +452,23 @@ int coherent_scan(spiir_sky_s *sky, const float2 *snr, int64_t pitch, int T, int
         m.null_stat = null_stat;
         m.skymap = skymap;
         m.map_vec = (n % 4 == 0 && ((uintptr_t)skymap % 16) == 0) ? 1 : 0;
+        m.sky_pix = sky->n_pix;
         // short chunks: several templates share a work item (their rows split the 128 lanes)
         m.nsub = tmem_templates_per_item(n, m.mw);
-        return launch_coherent_tmem(m, sky->scan_tmem_param ? sky->t_tab : nullptr, stream);
+        for (size_t k = 0; k < sky->t_parts.size(); ++k) {
+            const TmPart &pt = sky->t_parts[k];
+            m.n_pix = pt.n_pix;
+            m.ent = sky->t_ent + pt.first;
+            m.orig = sky->g_orig + pt.first;
+            m.grp = sky->t_grp + pt.gfirst;
+            m.n_grp = pt.n_grp;
+            m.q0 = pt.q0;
+            m.g0 = pt.g0;
+            for (int i = 0; i < 5; ++i) m.slice[i] = pt.slice[i];
+            m.merge = k > 0 ? 1 : 0;
+            SPIIR_TRY(launch_coherent_tmem(m, sky->scan_tmem_param ? pt.tab : nullptr, stream));
+        }
+        return SPIIR_OK;
     }
     if (sky->grouped) {
         GroupedArgs g{};
@@ -552,7 +558,8 @@ static void sky_free(spiir_sky_s *s) {
     dev_free(s->t_ent);
     dev_free(s->d_delays);
     dev_free(s->pt_tab);
-    delete s->t_tab;
+    dev_free(s->t_grp);
+    for (auto &pt : s->t_parts) delete pt.tab;
     delete s;
 }
 
@@ -623,40 +630,81 @@ static int build_grouped(spiir_sky_s *s, const int32_t *delays, const float *u_s
     SPIIR_CUDA_TRY(cudaMemcpy(s->g_orig, orig.data(), sizeof(uint16_t) * P, cudaMemcpyHostToDevice));
     SPIIR_CUDA_TRY(cudaMemcpy(s->g_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice));
     s->n_grp = (int)grp.size();
-    // tensor-memory scan: raw offsets delta_I = H + Delta_I, and four slices of consecutive
-    // groups holding nearly equal numbers of pixels
-    if (nd == 3 && tmem_fits(P, s->n_grp, H, 8)) {
+    // tensor-memory scan: raw offsets delta_I = H + Delta_I; the groups cut into parts of at most
+    // kTmTabPix pixels and kTmTabGrp groups, each part into four slices of consecutive groups
+    // holding nearly equal numbers of pixels
+    if (nd == 3 && 2 * tmem_columns(H, 8) <= 256) {
         std::vector<float4> te(ent);
         for (int q = 0; q < P; ++q) {
             const int p = order[q];
             const unsigned packed = (unsigned)(H + delays[(int64_t)p * nd + 1]) | ((unsigned)(H + delays[(int64_t)p * nd + 2]) << 16);
             memcpy(&te[q].w, &packed, 4);
         }
-        SPIIR_TRY(dev_alloc((void **)&s->t_ent, sizeof(float4) * P, "tensor-memory sky table"));
-        SPIIR_CUDA_TRY(cudaMemcpy(s->t_ent, te.data(), sizeof(float4) * P, cudaMemcpyHostToDevice));
-        s->t_slice[0] = 0;
-        for (int k = 1; k < 4; ++k) {
-            // the group boundary closest to a quarter of the pixels
-            const int64_t target = (int64_t)P * k / 4;
-            int best = s->t_slice[k - 1];
-            int64_t best_d = INT64_MAX;
-            for (int c = s->t_slice[k - 1]; c <= s->n_grp; ++c) {
-                const int64_t start = c < s->n_grp ? grp[c].y : P;
-                const int64_t d = start > target ? start - target : target - start;
-                if (d < best_d) {
-                    best_d = d;
-                    best = c;
-                }
+        std::vector<TmPart> parts;
+        for (int g = 0; g < s->n_grp;) {
+            TmPart pt;
+            pt.gfirst = g;
+            pt.first = grp[g].y;
+            while (g < s->n_grp && pt.n_grp < kTmTabGrp && grp[g].z - pt.first <= kTmTabPix) {
+                ++pt.n_grp;
+                ++g;
             }
-            s->t_slice[k] = best;
+            if (pt.n_grp == 0) {  // one group above kTmTabPix pixels: no parameter tables
+                parts.clear();
+                break;
+            }
+            pt.n_pix = grp[g - 1].z - pt.first;
+            parts.push_back(pt);
         }
-        s->t_slice[4] = s->n_grp;
-        s->tmem_ok = true;
-        if (P <= kTmTabPix && s->n_grp <= kTmTabGrp) {
-            s->t_tab = new (std::nothrow) TmemTab();
-            if (!s->t_tab) return fail(SPIIR_ENOMEM, "host copy of the tensor-memory tables");
-            for (int q = 0; q < P; ++q) memcpy(&s->t_tab->d12[q], &te[q].w, 4);
-            for (int g = 0; g < s->n_grp; ++g) s->t_tab->grp[g] = grp[g];
+        std::vector<int4> rg(grp);
+        bool ok = !parts.empty();
+        for (auto &pt : parts) {
+            for (int g = pt.gfirst; g < pt.gfirst + pt.n_grp; ++g) {
+                rg[g].y -= pt.first;
+                rg[g].z -= pt.first;
+            }
+            // slices: the group boundary closest to each quarter of the part's pixels
+            pt.slice[0] = 0;
+            for (int k = 1; k < 4; ++k) {
+                const int64_t target = (int64_t)pt.n_pix * k / 4;
+                int best = pt.slice[k - 1];
+                int64_t best_d = INT64_MAX;
+                for (int c = pt.slice[k - 1]; c <= pt.n_grp; ++c) {
+                    const int64_t start = c < pt.n_grp ? rg[pt.gfirst + c].y : pt.n_pix;
+                    const int64_t d = start > target ? start - target : target - start;
+                    if (d < best_d) {
+                        best_d = d;
+                        best = c;
+                    }
+                }
+                pt.slice[k] = best;
+            }
+            pt.slice[4] = pt.n_grp;
+            // the part's lowest pixel index and its group
+            int qmin = 0;
+            for (int q = 1; q < pt.n_pix; ++q)
+                if (orig[pt.first + q] < orig[pt.first + qmin]) qmin = q;
+            pt.q0 = qmin;
+            for (int c = 0; c < pt.n_grp; ++c)
+                if (rg[pt.gfirst + c].y <= qmin && qmin < rg[pt.gfirst + c].z) pt.g0 = c;
+            pt.tab = new (std::nothrow) TmemTab();
+            if (!pt.tab) {
+                ok = false;
+                break;
+            }
+            for (int q = 0; q < pt.n_pix; ++q) memcpy(&pt.tab->d12[q], &te[pt.first + q].w, 4);
+            for (int c = 0; c < pt.n_grp; ++c) pt.tab->grp[c] = rg[pt.gfirst + c];
+            ok = ok && tmem_fits(pt.n_pix, pt.n_grp, H, 8);
+        }
+        if (ok) {
+            SPIIR_TRY(dev_alloc((void **)&s->t_ent, sizeof(float4) * P, "tensor-memory sky table"));
+            SPIIR_CUDA_TRY(cudaMemcpy(s->t_ent, te.data(), sizeof(float4) * P, cudaMemcpyHostToDevice));
+            SPIIR_TRY(dev_alloc((void **)&s->t_grp, sizeof(int4) * rg.size(), "tensor-memory pixel groups"));
+            SPIIR_CUDA_TRY(cudaMemcpy(s->t_grp, rg.data(), sizeof(int4) * rg.size(), cudaMemcpyHostToDevice));
+            s->t_parts = parts;
+            s->tmem_ok = true;
+        } else {
+            for (auto &pt : parts) delete pt.tab;
         }
     }
     s->g_W = W;
@@ -754,7 +802,9 @@ extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs, i
         // tensor-memory scan, 8 samples per thread row with 512 threads or 16 with 256; the
         // shared-memory kernel keeps its shape for sky-map requests
         const int mw = threads == 512 ? 8 : 16;
-        if (!s->tmem_ok || !tmem_fits(s->n_pix, s->n_grp, s->halo, mw))
+        bool fits = s->tmem_ok;
+        for (const auto &pt : s->t_parts) fits = fits && tmem_fits(pt.n_pix, pt.n_grp, s->halo, mw);
+        if (!fits)
             return fail(SPIIR_EUNSUPPORTED, "tensor-memory scan needs 3 detectors, an orthonormal basis, "
                                             "|Delta| <= %d and a table that fits in shared memory", mw == 8 ? 60 : 56);
         if (table_in_shared != 0 && table_in_shared != 1)
@@ -779,8 +829,10 @@ extern "C" int spiir_sky_set_scan_shape(spiir_sky_t s, int threads, int pairs, i
     dev_free(s->g_orig);
     dev_free(s->g_grp);
     dev_free(s->t_ent);
-    delete s->t_tab;
-    s->t_tab = nullptr;
+    dev_free(s->t_grp);
+    for (auto &pt : s->t_parts) delete pt.tab;
+    s->t_parts.clear();
+    s->t_grp = nullptr;
     s->g_ent = nullptr;
     s->g_orig = nullptr;
     s->g_grp = nullptr;

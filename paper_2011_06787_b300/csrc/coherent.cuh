@@ -57,6 +57,8 @@ struct TmemArgs {
     int map_vec;            // 1: n % 4 == 0 and skymap 16-byte aligned (vector stores)
     int nsub;               // templates per work item (1, 2 or 4): 128 / nsub rows each
     int mw;                 // consecutive samples per thread row: 8 (512 threads) or 16 (256)
+    int sky_pix;            // pixels of the whole sky (sky-map row stride)
+    int merge;              // 1: a part after the first, keep the better of the stored and the new result
 };
 
 // Per-pixel delay offsets (delta_1 | delta_2 << 16) and the pixel groups of the tensor-memory
@@ -71,6 +73,18 @@ struct TmemTab {
 
 int tmem_columns(int H, int mw);
 bool tmem_fits(int n_pix, int n_grp, int H, int mw);
+
+// A part of the sky for the tensor-memory scan: consecutive pixel groups (of the delay-sorted
+// order) holding at most kTmTabPix pixels and kTmTabGrp groups, so that its tables travel as a
+// kernel parameter.  Larger skies are scanned part by part, each part keeping the better of its
+// own and the stored (maximum, lowest pixel).
+struct TmPart {
+    int first = 0, n_pix = 0;      // sorted pixels [first, first + n_pix)
+    int gfirst = 0, n_grp = 0;     // its groups (positions re-based to the part)
+    int q0 = 0, g0 = 0;            // part-local sorted position and group of its lowest-index pixel
+    int slice[5] = {0, 0, 0, 0, 0};
+    TmemTab *tab = nullptr;        // host copy of its parameter tables
+};
 int tmem_templates_per_item(int64_t n, int mw);
 int launch_coherent_tmem(const TmemArgs &a, const TmemTab *tab, cudaStream_t stream);
 
@@ -122,8 +136,8 @@ struct spiir_sky_s {
     // tensor-memory scan tables (same pixel order and groups as the grouped scan)
     bool tmem_ok = false;
     float4 *t_ent = nullptr;
-    spiir::TmemTab *t_tab = nullptr;  // host copy of the parameter tables (NULL when the sky is too large)
-    int t_slice[5] = {0, 0, 0, 0, 0};
+    std::vector<spiir::TmPart> t_parts;  // the sky in parts of the tensor-memory scan
+    int4 *t_grp = nullptr;               // [G] groups with pixel positions re-based to their part
     // inputs kept to rebuild the grouped tables when the launch shape changes
     std::vector<int32_t> h_delays;
     int16_t *d_delays = nullptr;  // [P][n_det] on the device (signal-consistency gather)

@@ -27,8 +27,11 @@
 // groups are cut into four slices of nearly equal pixel count.  Per sample the four slice
 // maxima are merged in shared memory; the sample's winning group is then rescanned in scalar
 // arithmetic to find the lowest pixel index attaining the maximum, as in the shared-memory
-// kernel.  A maximum that several groups attain exactly (unless pixel 0, the all-zero window,
-// settles it) is left to a second pass in which a whole warp rescans the sky for that sample.
+// kernel.  A maximum that several groups attain exactly (unless the lowest pixel, pixel 0 with
+// the all-zero window, settles it) is left to a second pass in which a whole warp rescans the
+// sky for that sample.  A sky above 4096 pixels or 512 groups runs as consecutive parts that fit
+// those limits, one launch each: every part after the first replaces a stored result only by a
+// larger maximum, or an equal one at a lower pixel index.
 // In sky-map mode every row also writes its 8 statistics of each pixel to
 // map[t][p][k] (two 16-byte streaming stores), which overlaps the map's HBM writes with the
 // arithmetic.
@@ -249,7 +252,7 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                     // the row's MW samples of this pixel: one contiguous segment per warp, written
                     // with the streaming (evict-first) hint
                     const int64_t kr = k0 + MW * (row % RPT);
-                    float *mrow = a.skymap + ((int64_t)trow * P + orig[p]) * a.n + kr;
+                    float *mrow = a.skymap + ((int64_t)trow * a.sky_pix + orig[p]) * a.n + kr;
                     if (a.map_vec && kr + MW <= a.n) {
 #pragma unroll
                         for (int m = 0; m < MW; m += 4)
@@ -313,6 +316,12 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
         auto store = [&](int tj, int jk, float B, int arg, float nul) {
             if (arg == 0x7fffffff) arg = 0;  // only when every statistic is NaN
             const int64_t o = (int64_t)tj * a.n + k0 + jk;
+            if (a.merge) {
+                // a later part of the sky: replace the stored result only by a larger maximum,
+                // or an equal one at a lower pixel
+                const float old = a.max_stat[o];
+                if (!(B > old || (B == old && arg < a.argmax[o]))) return;
+            }
             a.max_stat[o] = B;
             a.argmax[o] = arg;
             a.null_stat[o] = nul;
@@ -341,7 +350,7 @@ __device__ __forceinline__ void tmem_scan(const TmemArgs &a, const TmemTab *pt) 
                 float v, tt;
                 stat(a.q0, H + grp[a.g0].w, xj, v, tt);
                 if (v == B) {
-                    store(tj, jk, B, 0, tt);
+                    store(tj, jk, B, orig[a.q0], tt);  // the lowest pixel index of the (part of the) sky
                 } else {
                     tie_slots[atomicAdd(n_tie, 1)] = j;
                 }

@@ -502,3 +502,59 @@ def test_tensor_memory_sky_map_scalar_tail_and_odd_lengths(n):
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
     mp = np.transpose(mp, (0, 2, 1))
     assert np.all(np.abs(mp - sm_or) <= 1e-4 * sm_or.max(axis=-1, keepdims=True))
+
+
+@pytest.mark.parametrize("threads,param", [(512, 1), (256, 1), (512, 0)])
+def test_tensor_memory_scan_of_a_sky_in_parts(threads, param):
+    """nside 32 (12288 pixels) exceeds one parameter table (4096 pixels): the tensor-memory
+    scan runs the sky as consecutive parts, each later part keeping the better of its own and the
+    stored (maximum, lowest pixel).  Against the oracle and the shared-memory scan, in argmax and
+    sky-map mode."""
+    sky, G, d_or = _sky(4, 3, 32, (0.5, 2.0))
+    H, T, n = sky.halo, 2, 1300
+    z = synth.complex_gaussian_snr(4, (T, 3, n + 2 * H), sub=32)
+    ms_s, am_s, nl_s, _ = _scan(sky, z, n)
+    sky.set_scan_shape(threads, 4, param)
+    assert sky.get_scan_shape() == (threads, 4, param, 1)
+    ms, am, nl, _ = _scan(sky, z, n)
+    assert np.all(np.abs(ms - ms_s) <= 1e-5 * ms_s.max()) and np.mean(am == am_s) > 0.999
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G, d_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    ms2, am2, nl2, mp = _scan(sky, z, n, skymap=True)
+    assert np.array_equal(ms2, ms) and np.array_equal(am2, am) and np.array_equal(nl2, nl)
+    mp = np.transpose(mp, (0, 2, 1))
+    assert np.all(np.abs(mp - sm_or) <= 1e-4 * np.maximum(sm_or.max(axis=-1, keepdims=True), 1e-30))
+
+
+def test_tensor_memory_parts_resolve_exact_ties_and_zero_windows_to_the_lowest_pixel():
+    """Three copies of the nside-16 sky (9216 pixels, three parts) whose detector-0 delays are
+    0, 1 and 2 samples later, with detector 0 silent: each pixel ties exactly with its copies,
+    which sit in other groups and parts, and the original (lowest) index must win; an all-zero
+    window ties every pixel and gives pixel 0."""
+    import paper_2011_06787_b300 as sp
+    det = synth.detectors(1, 3)
+    sigma = synth.noise_weights(1, 3, 0.5, 2.0)
+    d, us, un = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 16, 2048.0)
+    _, G, d_or = oracle.sky_geometry(det, sigma, 16, 2048.0)
+    m, copies = d.shape[0], 3
+    idx = np.concatenate([np.arange(m)] * copies)
+    shift = np.repeat(np.arange(copies), m).astype(np.int32)
+    d2, d2_or = d[idx].copy(), d_or[idx].copy()
+    d2[:, 0] += shift
+    d2_or[:, 0] += shift
+    sky = sp.Sky(d2, us[idx], un[idx])
+    sky.set_scan_shape(512, 4, 1)
+    H, n, T = sky.halo, 1100, 2
+    z = synth.complex_gaussian_snr(1, (T, 3, n + 2 * H), sub=72).astype(np.complex64)
+    z[:, 0, :] = 0
+    z[1, :, :400] = 0                      # template 1 starts with an all-zero window
+    ms, am, nl, _ = _scan(sky, z, n)
+    ms_or, am_or, nl_or, sm_or = oracle.coherent(z, G[idx], d2_or, H, n, skymap=True)
+    assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+    assert np.all(am < m)
+    zero = np.all(sm_or == 0, axis=-1)
+    assert zero.any() and np.all(am[zero] == 0) and np.all(ms[zero] == 0)
+    top = np.sort(sm_or[:, :, :m], axis=-1)
+    clear = top[..., -1] - top[..., -2] > 1e-4 * top[..., -1]
+    assert clear.mean() > 0.5
+    np.testing.assert_array_equal(am[clear], am_or[clear])
