@@ -499,6 +499,18 @@ def batched_vs_plain(args, sp, torch, dev, stream, flush, timed_loop, det, sigma
         t = timed_loop(step, args.steps)
         tot = float(np.sum(t))
         out[name] = {"ms_per_chunk": tot / args.steps, "updates_per_s": updates * args.steps / (tot * 1e-3)}
+    # the persistent filter launch alone: CUDA events around it in eager batched chunks
+    batch.reset()
+    batch.filter_time()
+    fts = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        x.copy_(xs[i])
+        batch.run(x, ms, am, nl, mode=1)
+        if i >= args.warmup:
+            fts.append(batch.filter_time())
+    ft = float(np.mean(fts))
+    out["persistent_filter_launch"] = {"ms": ft, "roofline": k1_roofline(updates, ft)}
     sp.device_status()
     out["speedup_graph_vs_plain"] = out["plain"]["ms_per_chunk"] / out["batched_graph"]["ms_per_chunk"]
     out["kernel_launches_per_chunk"] = {"plain": 1 + sum(1 for b in banks for k in range(3) if np.any(b[4] == k)) +

@@ -610,6 +610,12 @@ int spiir_batch_set_shape(spiir_batch_t batch, int filters_per_lane, int lanes_p
  * spiir_batch_reset (SPIIR_EINVAL otherwise).  Enqueued on stream. */
 int spiir_batch_run(spiir_batch_t batch, int mode, const float *strain_dev, float *max_stat_dev,
                     int32_t *argmax_dev, float *null_stat_dev, void *stream);
+/* Device time of the persistent filter launch alone (a measurement hook; no counterpart in
+ * the paper).  The first call creates two CUDA events and returns *ms = -1; from then on every
+ * eager batched chunk (mode 1) records them around its persistent launch, and a call
+ * synchronises on the second event and returns the last such launch's time in ms (-1 before
+ * one has run).  Graph-replayed chunks are not timed.  Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
+int spiir_batch_filter_time(spiir_batch_t batch, float *ms);
 
 #ifdef __cplusplus
 }

@@ -416,6 +416,13 @@ class Batch:
         check(native.lib().spiir_batch_set_shape(self._h, int(filters_per_lane), int(lanes_per_block),
                                                  int(steps_per_reduce), int(blocks_per_sm)))
 
+    def filter_time(self) -> float:
+        """Device time (ms) of the last eager batched chunk's persistent filter launch; the
+        first call arms the events and returns -1 (spiir_batch_filter_time)."""
+        v = ctypes.c_float()
+        check(native.lib().spiir_batch_filter_time(self._h, ctypes.byref(v)))
+        return float(v.value)
+
     def run(self, strain, max_stat, argmax, null_stat, mode=GRAPH, stream=None):
         import torch
         _require_cuda(strain, torch.float32, "strain")

@@ -150,6 +150,9 @@ struct spiir_batch_s {
     const float *g_strain = nullptr;
     float *g_ms = nullptr, *g_nl = nullptr;
     int32_t *g_am = nullptr;
+    // CUDA events around the persistent filter launch of eager batched chunks (mode 1)
+    cudaEvent_t f_ev[2] = {nullptr, nullptr};
+    bool f_timed = false;
 };
 
 namespace spiir {
@@ -161,6 +164,8 @@ static void batch_free(spiir_batch_s *B) {
     if (!B) return;
     if (B->gexec) cudaGraphExecDestroy(B->gexec);
     if (B->cap) cudaStreamDestroy(B->cap);
+    for (int i = 0; i < 2; ++i)
+        if (B->f_ev[i]) cudaEventDestroy(B->f_ev[i]);
     for (int b = 0; b < kMaxBands; ++b) {
         if (B->band_bank[b]) spiir_bank_destroy(B->band_bank[b]);
         dev_free(B->zb[b]);
@@ -348,7 +353,15 @@ static int batched_chunk(spiir_batch_s *B, const float *strain, float *ms, int32
     p.n_items = B->n_items;
     p.counter = B->counter;
     SPIIR_CUDA_TRY(cudaMemsetAsync(B->counter, 0, sizeof(int), s));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SPIIR_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    const bool timed = cs == cudaStreamCaptureStatusNone && B->f_ev[0] && B->f_ev[1];
+    if (timed) SPIIR_CUDA_TRY(cudaEventRecord(B->f_ev[0], s));
     if (B->n_items > 0) SPIIR_TRY(bank_launch_persistent(p, B->shape_S, B->shape_NL, B->shape_R, B->blocks_per_sm, smem, s));
+    if (timed) {
+        SPIIR_CUDA_TRY(cudaEventRecord(B->f_ev[1], s));
+        B->f_timed = true;
+    }
     SPIIR_DEBUG_SYNC("persistent filter");
     // bands with long delays: add the later delay pieces of their split templates
     for (int b = 0; b < B->n_bands; ++b)
@@ -585,6 +598,23 @@ extern "C" int spiir_batch_set_shape(spiir_batch_t B, int filters_per_lane, int 
         cudaGraphExecDestroy(B->gexec);
         B->gexec = nullptr;
     }
+    return SPIIR_OK;
+}
+
+extern "C" int spiir_batch_filter_time(spiir_batch_t B, float *ms) {
+    clear_error();
+    if (!B || !ms) return fail(SPIIR_EINVAL, "NULL argument");
+    if (!B->f_ev[0]) {
+        for (int i = 0; i < 2; ++i) SPIIR_CUDA_TRY(cudaEventCreate(&B->f_ev[i]));
+        *ms = -1.f;
+        return SPIIR_OK;
+    }
+    if (!B->f_timed) {
+        *ms = -1.f;
+        return SPIIR_OK;
+    }
+    SPIIR_CUDA_TRY(cudaEventSynchronize(B->f_ev[1]));
+    SPIIR_CUDA_TRY(cudaEventElapsedTime(ms, B->f_ev[0], B->f_ev[1]));
     return SPIIR_OK;
 }
 

@@ -112,3 +112,24 @@ def test_persistent_launch_with_full_blocks_and_short_reduction_blocks():
     ms, am, nl = _run(sp, sky, banks, 2, 2, shape=(8, 128, 16, 0))
     ms_or, am_or, nl_or, sm_or = _oracle(banks, G, d_or, sky.halo, 2)
     assert_coherent_close(ms, am, nl, ms_or, am_or, nl_or, sm_or)
+
+
+def test_persistent_filter_launch_time_hook():
+    """spiir_batch_filter_time: -1 until armed and until an eager batched chunk ran; then the
+    device time of that chunk's persistent filter launch, which graph replays leave unchanged."""
+    import torch
+    sp, sky, G, d_or, banks = _setup()
+    b = sp.Batch(3, banks, FACTORS, sky, 512)
+    T = b.n_templates
+    ms = torch.empty((T, 512), device="cuda")
+    am = torch.empty((T, 512), dtype=torch.int32, device="cuda")
+    nl = torch.empty((T, 512), device="cuda")
+    x = torch.from_numpy(synth.multirate_chunk(0, 3, 512)).cuda()
+    assert b.filter_time() == -1.0          # arms the events
+    b.run(x, ms, am, nl, mode=sp.Batch.GRAPH)
+    assert b.filter_time() == -1.0          # graph replays are not timed
+    b.run(x, ms, am, nl, mode=sp.Batch.BATCHED)
+    t1 = b.filter_time()
+    assert 0.0 < t1 < 1000.0
+    b.run(x, ms, am, nl, mode=sp.Batch.GRAPH)
+    assert b.filter_time() == t1
