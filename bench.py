@@ -532,6 +532,8 @@ def scale_rate(args, torch, sp, timed_loop):
     det = synth.detectors(c["index"], 3)
     sigma = synth.noise_weights(c["index"], 3, *c["sigma"])
     bank, _, _ = synth.scale_bank()
+    if args.scale_templates < bank.n_templates:   # a slice of the bank (profiling captures)
+        bank = bank.subset(range(args.scale_templates))
     mr = synth.scale_bank_multirate(bank)
     sky = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, c["nside"], 2048.0))
     T, n, P, H = bank.n_templates, c["chunk"], sky.n_pix, sky.halo
@@ -998,6 +1000,8 @@ def main():
     ap.add_argument("--bank-shape", default="", help="fixed filter-bank shape S,NL,R,tile (no autotuning)")
     ap.add_argument("--batch-shape", default="", help="fixed persistent-launch shape S,NL,R,blocks_per_sm (no autotuning)")
     ap.add_argument("--templates", type=int, default=1024, help="templates per GPU (1024 = the workload)")
+    ap.add_argument("--scale-templates", type=int, default=4096,
+                    help="templates of the scale section (4096 = the workload; fewer for profiling captures)")
     ap.add_argument("--flush-mib", type=int, default=512, help="L2 flush buffer written before each timed step")
     args = ap.parse_args()
     if args.warmup < 3:
