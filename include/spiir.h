@@ -230,9 +230,10 @@ int spiir_sky_info(spiir_sky_t sky, int *n_det, int *n_pix, int *halo);
  * with each other bit for bit; with a sky map each thread writes its samples of a pixel as
  * one contiguous segment.
  * For this shape the third value selects where the pixel groups and per-pixel delay offsets
- * are read: 1 (default) from the kernel's parameter space when the sky has at most 4096
- * pixels and 512 groups (warp-uniform reads, so the tensor-memory addresses stay in uniform
- * registers), else from shared memory; 0 always from shared memory.
+ * are read: 1 (default) from the kernel's parameter space (warp-uniform reads, so the
+ * tensor-memory addresses stay in uniform registers), 0 from shared memory.  A sky above 6400
+ * pixels or 256 pixel groups is scanned as the fewest consecutive parts of nearly equal pixel
+ * counts within those limits (two at nside 32), one launch each, with the same results.
  * Errors: SPIIR_EUNSUPPORTED when the tensor-memory scan does not apply (the previous shape is
  * kept), SPIIR_EINVAL for other shapes. */
 int spiir_sky_set_scan_shape(spiir_sky_t sky, int threads, int pairs, int table_in_shared);

@@ -640,21 +640,40 @@ static int build_grouped(spiir_sky_s *s, const int32_t *delays, const float *u_s
             const unsigned packed = (unsigned)(H + delays[(int64_t)p * nd + 1]) | ((unsigned)(H + delays[(int64_t)p * nd + 2]) << 16);
             memcpy(&te[q].w, &packed, 4);
         }
+        // the fewest parts of nearly equal pixel counts: cut at the group boundaries closest to
+        // k P / n_parts, and take one part more while a part exceeds the table limits
         std::vector<TmPart> parts;
-        for (int g = 0; g < s->n_grp;) {
-            TmPart pt;
-            pt.gfirst = g;
-            pt.first = grp[g].y;
-            while (g < s->n_grp && pt.n_grp < kTmTabGrp && grp[g].z - pt.first <= kTmTabPix) {
-                ++pt.n_grp;
-                ++g;
+        for (int np = (P + kTmTabPix - 1) / kTmTabPix; np <= s->n_grp && parts.empty(); ++np) {
+            std::vector<int> cut{0};
+            for (int k = 1; k < np; ++k) {
+                const int64_t target = (int64_t)P * k / np;
+                int best = cut.back() + 1;
+                int64_t best_d = INT64_MAX;
+                for (int c = cut.back() + 1; c < s->n_grp; ++c) {
+                    const int64_t d = std::llabs((int64_t)grp[c].y - target);
+                    if (d < best_d) {
+                        best_d = d;
+                        best = c;
+                    }
+                }
+                cut.push_back(std::min(best, s->n_grp));
             }
-            if (pt.n_grp == 0) {  // one group above kTmTabPix pixels: no parameter tables
-                parts.clear();
-                break;
+            cut.push_back(s->n_grp);
+            bool fits = true;
+            for (int k = 0; k < np && fits; ++k) {
+                TmPart pt;
+                pt.gfirst = cut[k];
+                pt.n_grp = cut[k + 1] - cut[k];
+                if (pt.n_grp <= 0) {
+                    fits = false;
+                    break;
+                }
+                pt.first = grp[pt.gfirst].y;
+                pt.n_pix = grp[cut[k + 1] - 1].z - pt.first;
+                fits = pt.n_pix <= kTmTabPix && pt.n_grp <= kTmTabGrp;
+                parts.push_back(pt);
             }
-            pt.n_pix = grp[g - 1].z - pt.first;
-            parts.push_back(pt);
+            if (!fits) parts.clear();
         }
         std::vector<int4> rg(grp);
         bool ok = !parts.empty();

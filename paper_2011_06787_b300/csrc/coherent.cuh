@@ -64,8 +64,8 @@ struct TmemArgs {
 // Per-pixel delay offsets (delta_1 | delta_2 << 16) and the pixel groups of the tensor-memory
 // scan, passed as a kernel parameter when the sky is small enough: read with warp-uniform
 // indices from the parameter bank, they yield tensor-memory addresses in uniform registers.
-constexpr int kTmTabPix = 4096;
-constexpr int kTmTabGrp = 512;
+constexpr int kTmTabPix = 6400;   // with the groups, 29.7 KB: within the 32 KB of kernel parameters
+constexpr int kTmTabGrp = 256;
 struct TmemTab {
     uint32_t d12[kTmTabPix];
     int4 grp[kTmTabGrp];
@@ -76,8 +76,9 @@ bool tmem_fits(int n_pix, int n_grp, int H, int mw);
 
 // A part of the sky for the tensor-memory scan: consecutive pixel groups (of the delay-sorted
 // order) holding at most kTmTabPix pixels and kTmTabGrp groups, so that its tables travel as a
-// kernel parameter.  Larger skies are scanned part by part, each part keeping the better of its
-// own and the stored (maximum, lowest pixel).
+// kernel parameter.  Larger skies are cut into the fewest parts of nearly equal pixel counts and
+// scanned part by part, each part keeping the better of its own and the stored (maximum, lowest
+// pixel).
 struct TmPart {
     int first = 0, n_pix = 0;      // sorted pixels [first, first + n_pix)
     int gfirst = 0, n_grp = 0;     // its groups (positions re-based to the part)

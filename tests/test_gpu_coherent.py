@@ -506,7 +506,7 @@ def test_tensor_memory_sky_map_scalar_tail_and_odd_lengths(n):
 
 @pytest.mark.parametrize("threads,param", [(512, 1), (256, 1), (512, 0)])
 def test_tensor_memory_scan_of_a_sky_in_parts(threads, param):
-    """nside 32 (12288 pixels) exceeds one parameter table (4096 pixels): the tensor-memory
+    """nside 32 (12288 pixels) exceeds one parameter table (6400 pixels): the tensor-memory
     scan runs the sky as consecutive parts, each later part keeping the better of its own and the
     stored (maximum, lowest pixel).  Against the oracle and the shared-memory scan, in argmax and
     sky-map mode."""
@@ -527,7 +527,7 @@ def test_tensor_memory_scan_of_a_sky_in_parts(threads, param):
 
 
 def test_tensor_memory_parts_resolve_exact_ties_and_zero_windows_to_the_lowest_pixel():
-    """Three copies of the nside-16 sky (9216 pixels, three parts) whose detector-0 delays are
+    """Three copies of the nside-16 sky (9216 pixels, two parts) whose detector-0 delays are
     0, 1 and 2 samples later, with detector 0 silent: each pixel ties exactly with its copies,
     which sit in other groups and parts, and the original (lowest) index must win; an all-zero
     window ties every pixel and gives pixel 0."""
