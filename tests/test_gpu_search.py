@@ -39,14 +39,15 @@ def _chirp_bank(mcs, n_filters, f_lo):
 def _strain(cfg, det, sigma, N, inj):
     """Unit white noise plus chirps: (mc, f_lo, geocentric coalescence sample, direction, psi,
     network SNR) per injection; detector I sees the chirp at its integer arrival offset."""
-    x = synth.white_noise(cfg, 3, N, sub=77).astype(np.float64)
+    nd = sigma.size
+    x = synth.white_noise(cfg, nd, N, sub=77).astype(np.float64)
     for mc, f_lo, tc, nh, psi, snr in inj:
         hf = synth.newtonian_chirp(mc, f_lo=f_lo)[::-1]
         Fp, Fc = oracle.antenna_patterns(det.arm_x, det.arm_y, nh[None], psi)
         dl = oracle.arrival_delays(det.pos_m, nh[None], 2048.0)[0]
         s = sigma[:, None] * (Fp[0][:, None] * hf.real[None, :] + Fc[0][:, None] * hf.imag[None, :])
         amp = snr / math.sqrt(float(np.sum(s ** 2)))
-        for I in range(3):
+        for I in range(nd):
             start = tc + int(dl[I]) - (hf.size - 1)
             x[I, start: start + hf.size] += amp * s[I]
     return x.astype(np.float32)
@@ -103,20 +104,24 @@ def _xi2_oracle(zp, A, Nj, t, r, e, p, d_or, shift):
     return float(np.mean(vals))
 
 
-@pytest.mark.parametrize("case", ["short", "paper"])
-def test_search_on_injected_chirps_matches_the_oracle(case):
+@pytest.mark.parametrize("case,nd", [("short", 3), ("paper", 3), ("short", 2), ("short", 4)])
+def test_search_on_injected_chirps_matches_the_oracle(case, nd):
+    """Three detectors with short and with the paper's shifts; two (null stream zero) and four
+    detectors (three companions per candidate) with short shifts."""
     import torch
     import paper_2011_06787_b300 as sp
     cfg = 5
     if case == "short":
         T, F, f_lo, n_sh, step, Nj, nside_fg, nside_bg, n_chunks = 12, 120, 80.0, 20, 205, 60, 8, 4, 9
+        if nd == 4:
+            n_sh, n_chunks = 12, 10
         check_shifts = range(n_sh)
     else:
         T, F, f_lo, n_sh, step, Nj, nside_fg, nside_bg, n_chunks = 8, 100, 90.0, 100, 205, 175, 16, 8, 24
         check_shifts = range(0, n_sh, 9)
     chunk, thr, per_second = 2048, 4.0, 2048
-    det = synth.detectors(cfg, 3)
-    sigma = synth.noise_weights(cfg, 3, 0.5, 2.0)
+    det = synth.detectors(cfg, nd)
+    sigma = synth.noise_weights(cfg, nd, 0.5, 2.0)
     mcs = np.linspace(1.1, 2.2, T)
     bank = _chirp_bank(mcs, F, f_lo)
     N = n_chunks * chunk
@@ -135,19 +140,19 @@ def test_search_on_injected_chirps_matches_the_oracle(case):
     skb = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, nside_bg, 2048.0))
     _, Gf, df = oracle.sky_geometry(det, sigma, nside_fg, 2048.0)
     _, Gb, db = oracle.sky_geometry(det, sigma, nside_bg, 2048.0)
-    b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+    b = sp.Bank(nd, bank.offsets, bank.a1, bank.b0, bank.delay)
     At = torch.from_numpy(A).cuda()
     srch = sp.Search(b, skf, skb, At, Nj, chunk, thr, per_second, n_sh, step, max_cand=4096)
     L, Hb, La, _ = srch.info()
     H = max(skf.halo, skb.halo)
-    assert La == 2 * H + Nj and Hb == n_sh * 2 * step + 2 * H + Nj and L == Hb + chunk + La
+    assert La == 2 * H + Nj and Hb == n_sh * (nd - 1) * step + 2 * H + Nj and L == Hb + chunk + La
     assert N > L    # the ring wraps around
 
     # oracle: the whole stream through the FP64 bank, zero before the stream start
     oracle.set_threads(16)
     z_or, _, _ = oracle.filter_bank(x, bank.offsets, bank.a1, bank.b0, bank.delay)
     pad = Hb + La
-    zp = np.concatenate([np.zeros((T, 3, pad)), z_or], axis=2)
+    zp = np.concatenate([np.zeros((T, nd, pad)), z_or], axis=2)
 
     n_matched = n_diff = 0
     found = set()
@@ -181,16 +186,18 @@ def test_search_on_injected_chirps_matches_the_oracle(case):
                     if abs(S0 + k - tc) <= 64:
                         found.add(tc_i)
             pt = np.array([t, I, e0 + k], np.int64)
-            zero = np.zeros(3, np.int64)
+            zero = np.zeros(nd, np.int64)
             p = _check_point(fg[0][i], fg[1][i], fg[2][i], zp, Gf, df, pt, zero)
             want_xi = _xi2_oracle(zp, A, Nj, t, I, e0 + k, p, df, zero)
             assert abs(fg[3][i] - want_xi) <= 1e-4 * max(1.0, want_xi), (c, key, fg[3][i], want_xi)
             for si in check_shifts:
-                sh = oracle.background_shifts(I, 3, si + 1, step)
+                sh = oracle.background_shifts(I, nd, si + 1, step)
                 p = _check_point(bg[0][i, si], bg[1][i, si], bg[2][i, si], zp, Gb, db, pt, sh)
                 want_xi = _xi2_oracle(zp, A, Nj, t, I, e0 + k, p, db, sh)
                 assert abs(bg[3][i, si] - want_xi) <= 1e-4 * max(1.0, want_xi), (c, key, si)
     sp.device_status()
+    if nd == 2:
+        assert np.all(srch.fg[2].cpu().numpy()[:cnt] == 0)    # no null stream with two detectors
     assert n_matched > 30 and n_diff <= max(3, n_matched // 50), (n_matched, n_diff)
     assert found == {0, 1}      # both injections give candidates near their coalescence
 
