@@ -361,10 +361,11 @@ __device__ __forceinline__ void cp_async_wait() {
 // order without r), each companion's window index Delta_Jq(p) - Delta_r(p) - min over the sky of
 // the same difference (10 bits each, packed), and p.  Two or three 16-byte loads per pixel
 // replace the gather of the general entry's fields at run-time detector indices.
-// Order: the sky in chunks of kPtChunkThreads consecutive pixels, each chunk sorted by the
-// companions' window indices, so that the lanes of a warp read nearby window entries (fewer
-// shared-memory bank conflicts) while every thread still visits its pixels in increasing p (one
-// per chunk), which keeps the lowest pixel among equal statistics with a plain comparison.
+// Order: the sky in chunks of kPtChunkThreads consecutive pixels, each chunk arranged by
+// order_chunk so that the 16 lanes of a half-warp read window entries in distinct bank pairs as
+// far as the sky allows (fewer shared-memory bank conflicts), while every thread still visits
+// its pixels in increasing p (one per chunk), which keeps the lowest pixel among equal
+// statistics with a plain comparison.
 template <int ND>
 struct __align__(16) PtEnt {
     float ur[2];
@@ -415,26 +416,26 @@ __device__ __forceinline__ PtItem<ND> decode_item(const PointArgs &a, int64_t it
     return it;
 }
 
-// Start the copies of an item's windows into buf ([S][NC][kPtWP]): one warp per
-// (shift column, companion) window, lanes striding it, 8-byte asynchronous copies.
+// Start the copies of an item's windows into buf ([S][NC][WP]): warp w copies shift columns
+// w, w + 4, ... of each companion, lanes striding a window with 8-byte asynchronous copies.  A
+// companion's windows all have the same length and lie (q + 1) step samples apart per column, so
+// the source offset is stepped rather than recomputed.
 template <int ND, int S, int WP>
 __device__ __forceinline__ void stage_item(const PointArgs &a, const PtItem<ND> &it, float2 *buf, int wid, int lane) {
     constexpr int NC = ND - 1;
     constexpr int kWarps = kPtChunkThreads / 32;
-    for (int wi = wid; wi < S * NC; wi += kWarps) {
-        const int i = wi / NC, q = wi % NC;
-        if (!((it.okmask >> i) & 1u)) continue;
-        int J = 0, dq = 0, len = 0;
 #pragma unroll
-        for (int qq = 0; qq < NC; ++qq) {
-            J = (qq == q) ? it.Jq[qq] : J;
-            dq = (qq == q) ? it.dmn[qq] : dq;
-            len = (qq == q) ? it.dmx[qq] - it.dmn[qq] + 1 : len;
+    for (int q = 0; q < NC; ++q) {
+        const int len = it.dmx[q] - it.dmn[q] + 1;
+        const int64_t s0 = (int64_t)a.first_shift + it.s_first + wid;
+        int64_t o = ((int64_t)it.t * ND + it.Jq[q]) * a.pitch + it.e - s0 * (q + 1) * a.step + it.dmn[q];
+        const int64_t o_step = (int64_t)kWarps * (q + 1) * a.step;
+        float2 *dst = buf + (wid * NC + q) * WP;
+        for (int i = wid; i < S; i += kWarps, o -= o_step, dst += kWarps * NC * WP) {
+            if (!((it.okmask >> i) & 1u)) continue;
+            const float2 *row = a.snr + o;
+            for (int j = lane; j < len; j += 32) cp_async8(dst + j, row + j);
         }
-        const int64_t s = (int64_t)a.first_shift + it.s_first + i;
-        const float2 *row = a.snr + ((int64_t)it.t * ND + J) * a.pitch + it.e - s * (q + 1) * a.step + dq;
-        float2 *dst = buf + (i * NC + q) * WP;
-        for (int j = lane; j < len; j += 32) cp_async8(dst + j, row + j);
     }
 }
 
@@ -640,23 +641,75 @@ static int dispatch_points(const PointArgs &a, size_t smem, cudaStream_t stream)
 }
 
 // The per-reference point entries of a sky (built once, after the relative delay ranges).
+// Shared-memory wavefronts of one half-warp's 8-byte window reads, summed over the companions:
+// for each companion, the largest number of distinct window entries that share a bank pair
+// (entry mod 16; every window starts on a multiple of 16 entries).
+static int half_warp_cost(const uint32_t *idx, int n, int NC) {
+    int c = 0;
+    for (int q = 0; q < NC; ++q) {
+        int per_bank[16] = {0};
+        for (int i = 0; i < n; ++i) {
+            const uint32_t e = (idx[i] >> (10 * q)) & 1023u;
+            bool seen = false;
+            for (int j = 0; j < i && !seen; ++j) seen = ((idx[j] >> (10 * q)) & 1023u) == e;
+            if (!seen) ++per_bank[e & 15];
+        }
+        c += *std::max_element(per_bank, per_bank + 16);
+    }
+    return c;
+}
+
+// Order of one chunk's pixels (key = packed window indices, value = pixel): sorted by key, then
+// pixels exchanged between the half-warps' groups of 16 while that lowers the summed
+// half_warp_cost (a fixed pseudo-random sequence of trial swaps, so the table is reproducible).
+static void order_chunk(std::pair<uint64_t, int> *key, const uint32_t *idx_of_pixel, int n, int NC) {
+    std::sort(key, key + n);
+    const int G = (n + 15) / 16;
+    if (G < 2) return;
+    std::vector<uint32_t> idx(n);
+    std::vector<int> cost(G);
+    auto group_cost = [&](int g) { return half_warp_cost(&idx[16 * g], std::min(16, n - 16 * g), NC); };
+    for (int i = 0; i < n; ++i) idx[i] = idx_of_pixel[key[i].second];
+    for (int g = 0; g < G; ++g) cost[g] = group_cost(g);
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    for (int trial = 0; trial < 40 * n; ++trial) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        const int i = (int)((x >> 33) % (uint64_t)n), j = (int)((x >> 13) % (uint64_t)n);
+        const int gi = i / 16, gj = j / 16;
+        if (gi == gj) continue;
+        std::swap(idx[i], idx[j]);
+        const int ci = group_cost(gi), cj = group_cost(gj);
+        if (ci + cj <= cost[gi] + cost[gj]) {
+            std::swap(key[i], key[j]);
+            cost[gi] = ci;
+            cost[gj] = cj;
+        } else {
+            std::swap(idx[i], idx[j]);
+        }
+    }
+}
+
 template <int ND>
 static int build_point_table(spiir_sky_s *sky) {
     const int P = sky->n_pix;
     std::vector<PtEnt<ND>> h((size_t)ND * P);
     for (int r = 0; r < ND; ++r) {
         std::vector<std::pair<uint64_t, int>> key(P);
+        std::vector<uint32_t> idx(P);
         for (int p = 0; p < P; ++p) {
             const int32_t *dl = &sky->h_delays[(size_t)p * ND];
             uint64_t k = 0;
+            idx[p] = 0;
             for (int q = 0; q < ND - 1; ++q) {
                 const int J = q < r ? q : q + 1;
-                k = (k << 10) | (uint64_t)(dl[J] - dl[r] - sky->rel_min[r * ND + J]);
+                const uint32_t e = (uint32_t)(dl[J] - dl[r] - sky->rel_min[r * ND + J]);
+                k = (k << 10) | (uint64_t)e;
+                idx[p] |= e << (10 * q);
             }
             key[p] = {k, p};
         }
         for (int c0 = 0; c0 < P; c0 += kPtChunkThreads)
-            std::sort(key.begin() + c0, key.begin() + std::min(P, c0 + kPtChunkThreads));
+            order_chunk(&key[c0], idx.data(), std::min(P - c0, kPtChunkThreads), ND - 1);
         for (int i = 0; i < P; ++i) {
             const int p = key[i].second;
             PtEnt<ND> &e = h[(size_t)r * P + i];
