@@ -354,20 +354,24 @@ int spiir_frontend_run(spiir_frontend_t fe, const float *strain_dev, int64_t str
  * ---------------------------------------------------------------------------------- */
 
 /* Bytes of the workspace spiir_select_candidates needs: one 64-bit slot per
- * (detector, template, second).  Errors: SPIIR_EINVAL. */
+ * (detector, template, second), one 64-bit key per (detector, sample) and one 64-bit word
+ * for a block counter.  Errors: SPIIR_EINVAL. */
 int spiir_select_workspace_bytes(int n_templates, int n_det, int64_t n, int per_second,
                                  size_t *bytes);
 
 /* Select the candidates of samples 0 .. n-1 of snr_dev [T][n_det][snr_pitch] complex, in
- * which entry snr_offset + k is sample k (snr_offset + n <= snr_pitch; n < 2^31).
+ * which entry snr_offset + k is sample k (snr_offset + n <= snr_pitch; n_det n and
+ * n_det T seconds below 2^31).
  *   workspace_dev: device buffer of at least spiir_select_workspace_bytes, 8-byte aligned,
  *       ALL ZERO on entry (cudaMemset once after allocation); the call leaves it zero.
  *   cand_dev [max_cand][4] int32, 16-byte aligned: (detector, template, sample, bits of the
  *       FP32 |z|^2) ordered by detector, then template, then second.
  *   n_cand_dev: one int32 on the device, set to the number of candidates found (records past
  *       max_cand are dropped: a count above max_cand signals the overflow).
- * Two launches on stream; nothing is synchronised and nothing returns to the host.  The
- * threshold must be finite and >= 0.  NaN SNR values are never candidates.
+ * Two launches on stream, the second a programmatic dependent launch of the first (it may
+ * be scheduled early and waits for the first to complete); nothing is synchronised and
+ * nothing returns to the host.  The threshold must be finite and >= 0.  NaN SNR values are
+ * never candidates.
  * Errors: SPIIR_EINVAL. */
 int spiir_select_candidates(int n_templates, int n_det, const float *snr_dev, int64_t snr_pitch,
                             int64_t snr_offset, int64_t n, float threshold, int per_second,

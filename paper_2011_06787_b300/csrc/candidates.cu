@@ -6,14 +6,18 @@
 // candidate of its template, and each (detector, template, second) keeps the largest one (the
 // earliest among equals).  All decisions are taken on |z|^2 = re*re + im*im in FP32 with each
 // operation rounded (no contraction), so that they are reproducible bit for bit.
-//   k_select:  one block per (32 samples, detector); warp w reads templates w, w + 32, ... with
-//              coalesced 8-byte loads (lane = sample), the 32 warps combine in shared memory and
-//              a sample over the threshold posts the key (|z|^2 bits, ~k) to its slot
-//              (detector, template, second) with a 64-bit atomicMax: the largest value wins,
-//              then the smallest sample.
-//   k_compact: one block walks the slots in (detector, template, second) order, writes a
-//              record per occupied slot with a block-wide prefix sum and clears the slot, so the
-//              workspace is zero again for the next call; the count stays on the device.
+//   k_select:  one warp per (32 samples, detector, 32 templates), lane = sample, coalesced
+//              8-byte loads, 8 in flight per lane (one wave holds every task of a 1 s span of a
+//              1024-template, 3-detector bank).  Each lane
+//              posts (|z|^2 bits, ~template) of its best template to the sample's key with a
+//              64-bit atomicMax: the largest value wins, then the lowest template.
+//   k_compact: launched as a programmatic dependent of k_select (scheduled while the selection
+//              drains, it waits for its completion), one thread per key: a sample over the
+//              threshold posts (|z|^2 bits, ~k) to its slot (detector, template, second) with a
+//              64-bit atomicMax (the largest value, then the earliest sample); the last block
+//              to finish walks the slots in order and writes a record per occupied slot with a
+//              block-wide prefix sum.  Keys, slots and the block counter are cleared on the way,
+//              so the workspace is zero again for the next call; the count stays on the device.
 //
 // Candidate-driven scan.  A candidate (detector r, template t, sample k) is evaluated at every
 // pixel p with detector r read at its own sample and each other detector J at
@@ -39,10 +43,11 @@
 
 namespace spiir {
 
-constexpr int kSelWarps = 32;
-constexpr int kSelThreads = 32 * kSelWarps;
-constexpr int kSelUnroll = 16;
+constexpr int kSelBlock = 256;    // 8 warps, one task each
+constexpr int kSelTaskT = 32;     // templates per warp task
+constexpr int kSelUnroll = 8;     // loads in flight per lane
 constexpr int kCompThreads = 1024;
+constexpr int kCompSlots = 4;     // consecutive slots per thread and round
 constexpr int kPtThreads = 256;
 constexpr int kPtMaxSmem = 200 * 1024;
 constexpr int kPtChunkSmem = 110 * 1024;  // two blocks per SM
@@ -51,102 +56,146 @@ __device__ __forceinline__ u64 lds64(const float *p) { return *reinterpret_cast<
 
 __device__ __forceinline__ float mag2_rn(float2 z) { return __fadd_rn(__fmul_rn(z.x, z.x), __fmul_rn(z.y, z.y)); }
 
-__global__ void __launch_bounds__(kSelThreads) k_select(const float2 *__restrict__ snr, int64_t pitch, int64_t off,
-                                                       int T, int n_det, int64_t n, float thr2, int per_second,
-                                                       int64_t n_sec, u64 *__restrict__ slots) {
-    __shared__ float s_best[kSelWarps][32];
-    __shared__ int s_t[kSelWarps][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int I = blockIdx.y;
-    const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+// Task = (detector I, column of 32 samples, chunk of kSelTaskT templates), one per warp, lane =
+// sample.
+__global__ void __launch_bounds__(kSelBlock) k_select(const float2 *__restrict__ snr, int64_t pitch, int64_t off,
+                                                     int T, int n_det, int n, int n_cols, int n_chunks,
+                                                     u64 *__restrict__ keys) {
+    // the compaction grid may be scheduled now; it waits for this grid's completion
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int lane = threadIdx.x & 31;
+    const int task = blockIdx.x * (kSelBlock / 32) + (threadIdx.x >> 5);
+    if (task >= n_cols * n_det * n_chunks) return;
+    const int col = task % n_cols, rest = task / n_cols;
+    const int I = rest % n_det;
+    const int t0 = (rest / n_det) * kSelTaskT, t1 = min(T, t0 + kSelTaskT);
+    const int k = col * 32 + lane;
+    if (k >= n) return;
+    const int64_t ts = (int64_t)n_det * pitch;  // template stride
+    const float2 *p = snr + ((int64_t)t0 * n_det + I) * pitch + off + k;
     float best = -1.f;
     int bt = INT_MAX;
-    if (k < n) {
-        const float2 *p = snr + (int64_t)I * pitch + off + k;
-        const int64_t ts = (int64_t)n_det * pitch;  // template stride
-        int t = w;
-        for (; t + (kSelUnroll - 1) * kSelWarps < T; t += kSelUnroll * kSelWarps) {
-            float2 v[kSelUnroll];
+    int t = t0;
+    for (; t + kSelUnroll <= t1; t += kSelUnroll, p += kSelUnroll * ts) {
+        float2 v[kSelUnroll];
 #pragma unroll
-            for (int j = 0; j < kSelUnroll; ++j) v[j] = p[(int64_t)(t + j * kSelWarps) * ts];
+        for (int j = 0; j < kSelUnroll; ++j) v[j] = p[j * ts];
 #pragma unroll
-            for (int j = 0; j < kSelUnroll; ++j) {
-                const float m = mag2_rn(v[j]);
-                if (m > best) {
-                    best = m;
-                    bt = t + j * kSelWarps;
-                }
-            }
-        }
-        for (; t < T; t += kSelWarps) {
-            const float m = mag2_rn(p[(int64_t)t * ts]);
+        for (int j = 0; j < kSelUnroll; ++j) {
+            const float m = mag2_rn(v[j]);
             if (m > best) {
                 best = m;
-                bt = t;
+                bt = t + j;
             }
         }
     }
-    s_best[w][lane] = best;
-    s_t[w][lane] = bt;
-    __syncthreads();
-    if (w != 0 || k >= n) return;
-#pragma unroll
-    for (int q = 1; q < kSelWarps; ++q) {
-        const float m = s_best[q][lane];
-        const int tq = s_t[q][lane];
-        if (m > best || (m == best && tq < bt)) {
+    for (; t < t1; ++t, p += ts) {
+        const float m = mag2_rn(*p);
+        if (m > best) {
             best = m;
-            bt = tq;
+            bt = t;
         }
     }
-    if (best > thr2) {
-        const int64_t slot = ((int64_t)I * T + bt) * n_sec + k / per_second;
-        const u64 key = ((u64)__float_as_uint(best) << 32) | (u64)(0xFFFFFFFFu - (uint32_t)k);
-        atomicMax(slots + slot, key);
-    }
+    if (bt != INT_MAX)
+        atomicMax(keys + (int64_t)I * n + k, ((u64)__float_as_uint(best) << 32) | (u64)(0xFFFFFFFFu - (uint32_t)bt));
 }
 
-__global__ void __launch_bounds__(kCompThreads) k_compact(u64 *__restrict__ slots, int64_t n_slots, int T,
-                                                         int64_t n_sec, int4 *__restrict__ cand, int max_cand,
+// Exclusive prefix sum over the block of one int per thread (blockDim.x = kCompThreads); the
+// total in *total.  Ends with the block synchronised.
+__device__ __forceinline__ int block_exclusive_sum(int v, int *s_warp, int *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int wv = s_warp[lane];
+        int wx = wv;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wx, d);
+            if (lane >= d) wx += y;
+        }
+        s_warp[lane] = wx - wv;
+        if (lane == 31) *total = wx;
+    }
+    __syncthreads();
+    const int r = s_warp[w] + x - v;
+    __syncthreads();  // s_warp and total may be reused
+    return r;
+}
+
+// Launched as a programmatic dependent of k_select, one thread per key.  Index arithmetic in 32
+// bits: the host checks that n_det n and n_det T n_sec are below 2^31.
+//  1. every sample over the threshold posts (|z|^2 bits, ~k) of its best template to the slot
+//     (detector, template, second) with a 64-bit atomicMax (the largest value, then the
+//     earliest sample); keys are cleared;
+//  2. the last block to finish 1 (a counter; each block fences its slot updates before
+//     counting) writes one record per occupied slot in (detector, template, second) order,
+//     thread i taking kCompSlots consecutive slots of each round, and clears the slots and the
+//     counter.
+__global__ void __launch_bounds__(kCompThreads) k_compact(u64 *__restrict__ keys, int n, int n_det, int T,
+                                                         float thr2, int per_second, u64 *__restrict__ slots,
+                                                         int n_sec, unsigned *__restrict__ done,
+                                                         int4 *__restrict__ cand, int max_cand,
                                                          int32_t *__restrict__ n_cand) {
     __shared__ int s_warp[32];
     __shared__ int s_total;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ bool s_last;
+    // k_select's keys are complete and visible after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int i = blockIdx.x * kCompThreads + (int)threadIdx.x;
+    if (i < n_det * n) {
+        const u64 kv = __ldcg(reinterpret_cast<const unsigned long long *>(keys + i));
+        if (kv) {
+            keys[i] = 0;
+            if (__uint_as_float((uint32_t)(kv >> 32)) > thr2) {
+                const int I = i / n, k = i - I * n;
+                const int t = (int)(0xFFFFFFFFu - (uint32_t)kv);
+                atomicMax(slots + ((I * T + t) * n_sec + k / per_second),
+                          (kv & 0xFFFFFFFF00000000ull) | (u64)(0xFFFFFFFFu - (uint32_t)k));
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int n_slots = n_det * T * n_sec;
     int64_t base = 0;
-    for (int64_t c0 = 0; c0 < n_slots; c0 += kCompThreads) {
-        const int64_t i = c0 + threadIdx.x;
-        u64 key = 0;
-        if (i < n_slots) {
-            key = slots[i];
-            if (key) slots[i] = 0;
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, key != 0);
-        __syncthreads();  // the previous chunk is done with s_warp and s_total
-        if (lane == 0) s_warp[w] = __popc(b);
-        __syncthreads();
-        if (w == 0) {
-            const int v = s_warp[lane];
-            int x = v;
+    for (int c0 = 0; c0 < n_slots; c0 += kCompThreads * kCompSlots) {
+        const int s0 = c0 + (int)threadIdx.x * kCompSlots;
+        u64 sv[kCompSlots];
+        int cnt = 0;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, d);
-                if (lane >= d) x += y;
-            }
-            s_warp[lane] = x - v;
-            if (lane == 31) s_total = x;
+        for (int j = 0; j < kCompSlots; ++j) {
+            sv[j] = s0 + j < n_slots ? __ldcg(reinterpret_cast<const unsigned long long *>(slots + s0 + j)) : 0ull;
+            cnt += sv[j] != 0;
         }
-        __syncthreads();
-        if (key) {
-            const int64_t pos = base + s_warp[w] + __popc(b & ((1u << lane) - 1u));
+        int64_t pos = base + block_exclusive_sum(cnt, s_warp, &s_total);
+#pragma unroll
+        for (int j = 0; j < kCompSlots; ++j) {
+            if (!sv[j]) continue;
+            slots[s0 + j] = 0;
             if (pos < max_cand) {
-                const int64_t it = i / n_sec;  // I * T + t
-                cand[pos] = make_int4((int)(it / T), (int)(it % T), (int)(0xFFFFFFFFu - (uint32_t)key),
-                                      (int)(key >> 32));
+                const int it = n_sec == 1 ? s0 + j : (s0 + j) / n_sec;  // I * T + t
+                const int I = it / T;
+                cand[pos] = make_int4(I, it - I * T, (int)(0xFFFFFFFFu - (uint32_t)sv[j]), (int)(sv[j] >> 32));
             }
+            ++pos;
         }
         base += s_total;
     }
-    if (threadIdx.x == 0) *n_cand = (int32_t)std::min<int64_t>(base, INT_MAX);
+    if (threadIdx.x == 0) {
+        *n_cand = (int32_t)std::min<int64_t>(base, INT_MAX);
+        *done = 0;
+    }
 }
 
 struct PointArgs {
@@ -749,7 +798,8 @@ extern "C" int spiir_select_workspace_bytes(int T, int n_det, int64_t n, int per
     if (T < 1 || n_det < 1 || n < 1 || per_second < 1)
         return fail(SPIIR_EINVAL, "n_templates = %d, n_det = %d, n = %lld, per_second = %d", T, n_det, (long long)n,
                     per_second);
-    *bytes = sizeof(u64) * (size_t)n_det * (size_t)T * (size_t)n_seconds(n, per_second);
+    // slots, per-sample keys and the compaction's block counter
+    *bytes = sizeof(u64) * ((size_t)n_det * ((size_t)T * (size_t)n_seconds(n, per_second) + (size_t)n) + 1);
     return SPIIR_OK;
 }
 
@@ -771,18 +821,37 @@ extern "C" int spiir_select_candidates(int T, int n_det, const float *snr, int64
         return fail(SPIIR_EINVAL, "snr and workspace must be 8-byte aligned, cand 16-byte aligned");
     if (!(threshold >= 0.f) || !std::isfinite(threshold)) return fail(SPIIR_EINVAL, "threshold must be finite and >= 0");
     const int64_t n_sec = n_seconds(n, per_second);
-    const size_t need = sizeof(u64) * (size_t)n_det * (size_t)T * (size_t)n_sec;
+    const int64_t n_cols = (n + 31) / 32, n_chunks = (T + kSelTaskT - 1) / kSelTaskT;
+    if ((int64_t)n_det * n > INT_MAX || (int64_t)n_det * T * n_sec > INT_MAX || n_cols * n_det * n_chunks > INT_MAX)
+        return fail(SPIIR_EINVAL, "n_det x n and n_det x n_templates x seconds must be below 2^31");
+    size_t need = 0;
+    SPIIR_TRY(spiir_select_workspace_bytes(T, n_det, n, per_second, &need));
     if (workspace_bytes < need)
         return fail(SPIIR_EINVAL, "workspace of %zu bytes, %zu needed", workspace_bytes, need);
     const float thr2 = threshold * threshold;  // FP32, round to nearest (as the per-sample |z|^2)
     cudaStream_t st = (cudaStream_t)stream;
-    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)n_det);
-    k_select<<<grid, kSelThreads, 0, st>>>(reinterpret_cast<const float2 *>(snr), pitch, off, T, n_det, n, thr2,
-                                           per_second, n_sec, static_cast<u64 *>(workspace));
+    u64 *slots = static_cast<u64 *>(workspace);
+    u64 *keys = slots + (size_t)n_det * T * n_sec;
+    unsigned *done = reinterpret_cast<unsigned *>(keys + (size_t)n_det * n);
+    const int64_t n_tasks = n_cols * n_det * n_chunks;
+    const int blocks = (int)((n_tasks + kSelBlock / 32 - 1) / (kSelBlock / 32));
+    k_select<<<blocks, kSelBlock, 0, st>>>(reinterpret_cast<const float2 *>(snr), pitch, off, T, n_det, (int)n,
+                                           (int)n_cols, (int)n_chunks, keys);
     SPIIR_CUDA_TRY(cudaGetLastError());
-    k_compact<<<1, kCompThreads, 0, st>>>(static_cast<u64 *>(workspace), (int64_t)n_det * T * n_sec, T, n_sec,
-                                          reinterpret_cast<int4 *>(cand), max_cand, n_cand);
-    SPIIR_CUDA_TRY(cudaGetLastError());
+    // programmatic dependent launch: the compaction blocks are scheduled while the selection
+    // drains and wait for its completion
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(((int64_t)n_det * n + kCompThreads - 1) / kCompThreads));
+    cfg.blockDim = dim3(kCompThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SPIIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_compact, keys, (int)n, n_det, T, thr2, per_second, slots, (int)n_sec,
+                                      done, reinterpret_cast<int4 *>(cand), max_cand, n_cand));
     return SPIIR_OK;
 }
 

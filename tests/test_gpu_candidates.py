@@ -76,6 +76,22 @@ def test_selection_on_constructed_peaks():
                                                  (1, 1, 2047), (1, 1, 2048)]
 
 
+def test_selection_ties_across_template_groups():
+    """Equal maxima in templates far apart (the selection splits the bank into groups of 32
+    templates): the lowest template wins; a larger value later in the bank still wins."""
+    import paper_2011_06787_b300 as sp
+    T, nd, n, sec = 100, 2, 96, 32
+    z = np.zeros((T, nd, n), np.complex128)
+    z[70, 0, 10] = z[5, 0, 10] = 6.0 * np.exp(0.4j)
+    z[64, 1, 40] = z[33, 1, 40] = 5.0
+    z[99, 1, 40] = 5.5
+    z[31, 0, 95] = z[32, 0, 95] = z[63, 0, 95] = 4.5j
+    _, cand, cnt = _select(z, 0, n, 4.0, sec)
+    got = sp.Selector.records(cand, cnt)
+    _same_records(got, oracle.select_candidates(z.astype(np.complex64), 0, n, 4.0, sec))
+    assert [(a, b, c) for a, b, c, _ in got] == [(0, 5, 10), (0, 31, 95), (1, 99, 40)]
+
+
 @pytest.mark.parametrize("T,nd,n,off,per_second,thr", [
     (1, 1, 1, 0, 2048, 0.5),          # one sample, one template
     (37, 3, 5000, 13, 2048, 3.0),     # ragged: T below one unrolled pass, n % 32 != 0, last second short
