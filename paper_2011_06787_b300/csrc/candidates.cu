@@ -8,9 +8,9 @@
 // operation rounded (no contraction), so that they are reproducible bit for bit.
 //   k_select:  one warp per (32 samples, detector, 32 templates), lane = sample, coalesced
 //              8-byte loads, 8 in flight per lane (one wave holds every task of a 1 s span of a
-//              1024-template, 3-detector bank).  Each lane
-//              posts (|z|^2 bits, ~template) of its best template to the sample's key with a
-//              64-bit atomicMax: the largest value wins, then the lowest template.
+//              1024-template, 3-detector bank).  Each lane posts (|z|^2 bits, ~template) of
+//              its best template to the sample's key with a 64-bit atomicMax: the largest
+//              value wins, then the lowest template.
 //   k_compact: launched as a programmatic dependent of k_select (scheduled while the selection
 //              drains, it waits for its completion), one thread per key: a sample over the
 //              threshold posts (|z|^2 bits, ~k) to its slot (detector, template, second) with a
