@@ -297,18 +297,20 @@ __device__ __forceinline__ float xi_num_reg(const float2 *__restrict__ row, cons
     return warp_sum(num);
 }
 
-// The same statistic as k_xi2_points for templates of at most 32 NT taps and at most 4
-// detectors, with the dependent loads batched: the template's taps and the denominator once per
-// item, then lane i loads shift s0 + i's argmax pixel and that pixel's delays, which the shift
-// loop takes by shuffles.
-template <int NT>
+// The same statistic as k_xi2_points for templates of at most 32 NT taps and ND detectors, with
+// the dependent loads batched: the template's taps and the denominator once per item, then lane
+// i loads shift s0 + i's argmax pixel and that pixel's delays, which the shift loop takes by
+// shuffles; the ND - 1 companion rows of a shift are loaded together (one memory round trip per
+// shift).
+template <int NT, int ND>
 __global__ void __launch_bounds__(256) k_xi2_points_reg(const __grid_constant__ XiPointArgs a) {
+    constexpr int NC = ND - 1;
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     const int nc = min(*a.n_cand, a.max_cand);
     const int n_chunks = (a.n_shifts + kXiPtShifts - 1) / kXiPtShifts;
     const int64_t n_items = (int64_t)max(nc, 0) * n_chunks;
-    const int ntap = 2 * a.Nj + 1, nd = a.n_det;
+    const int ntap = 2 * a.Nj + 1;
     const float nan = __int_as_float(0x7fc00000);
     for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items; item += warps) {
         const int c = (int)(item / n_chunks), s0 = (int)(item % n_chunks) * kXiPtShifts;
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(256) k_xi2_points_reg(const __grid_constant__ 
         const int4 cd = a.cand[c];
         const int r = cd.x, t = cd.y;
         const int64_t e = a.off + (int64_t)cd.z;
-        const bool rec_ok = r >= 0 && r < nd && t >= 0 && t < a.n_templates && cd.z >= 0 && e - a.Nj >= 0 &&
+        const bool rec_ok = r >= 0 && r < ND && t >= 0 && t < a.n_templates && cd.z >= 0 && e - a.Nj >= 0 &&
                             e + a.Nj < a.pitch;
         const float2 *At = a.A + (int64_t)(rec_ok ? t : 0) * ntap;
         float2 Ar[NT];
@@ -329,53 +331,107 @@ __global__ void __launch_bounds__(256) k_xi2_points_reg(const __grid_constant__ 
         }
         den = warp_sum(den);
         // lane i: the argmax pixel of shift s0 + i and its delays
-        int pl = -1, dl[4] = {0, 0, 0, 0};
+        int pl = -1, dl[ND];
+#pragma unroll
+        for (int J = 0; J < ND; ++J) dl[J] = 0;
         if (lane < s1 - s0) {
             pl = a.argmax[(int64_t)c * a.n_shifts + s0 + lane];
             if (pl >= 0 && pl < a.n_pix) {
 #pragma unroll
-                for (int J = 0; J < 4; ++J)
-                    if (J < nd) dl[J] = a.delays[(int64_t)pl * nd + J];
+                for (int J = 0; J < ND; ++J) dl[J] = a.delays[(int64_t)pl * ND + J];
             }
         }
         const float xi_r =
-            rec_ok ? xi_num_reg<NT>(a.snr + ((int64_t)t * nd + r) * a.pitch + e - a.Nj, Ar, ntap, a.Nj, lane) / den : nan;
+            rec_ok ? xi_num_reg<NT>(a.snr + ((int64_t)t * ND + r) * a.pitch + e - a.Nj, Ar, ntap, a.Nj, lane) / den : nan;
         for (int si = s0; si < s1; ++si) {
             const int64_t o = (int64_t)c * a.n_shifts + si;
             const int p = __shfl_sync(0xffffffffu, pl, si - s0);
-            int dJ[4], d_r = 0;
+            int dJ[ND], d_r = 0;
 #pragma unroll
-            for (int J = 0; J < 4; ++J) {
+            for (int J = 0; J < ND; ++J) {
                 dJ[J] = __shfl_sync(0xffffffffu, dl[J], si - s0);
                 d_r = (J == r) ? dJ[J] : d_r;
             }
             const int64_t s = (int64_t)a.first_shift + si;
             bool ok = rec_ok && p >= 0 && p < a.n_pix;
-            float total = 0.f;
-            int comp = 0;
+            // companion q (detector order without r) of shift s reads around
+            // e + Delta_J - Delta_r - s (q + 1) step
+            const float2 *row[NC];
 #pragma unroll
-            for (int J = 0; J < 4; ++J) {
-                if (J >= nd || !ok) break;
-                float xi;
-                if (J == r) {
-                    xi = xi_r;
-                } else {
-                    const int64_t x = e + dJ[J] - d_r - s * (++comp) * a.step;
-                    if (x - a.Nj < 0 || x + a.Nj >= a.pitch) {
-                        ok = false;
-                        break;
+            for (int q = 0; q < NC; ++q) {
+                int J = 0, dq = 0;
+#pragma unroll
+                for (int JJ = 0; JJ < ND; ++JJ)
+                    if (JJ == (q < r ? q : q + 1)) {
+                        J = JJ;
+                        dq = dJ[JJ];
                     }
-                    xi = xi_num_reg<NT>(a.snr + ((int64_t)t * nd + J) * a.pitch + x - a.Nj, Ar, ntap, a.Nj, lane) / den;
+                const int64_t x = e + dq - d_r - s * (q + 1) * a.step;
+                ok = ok && x - a.Nj >= 0 && x + a.Nj < a.pitch;
+                row[q] = a.snr + ((int64_t)t * ND + J) * a.pitch + x - a.Nj;
+            }
+            if (!ok) {
+                if (lane == 0) {
+                    a.xi2[o] = nan;
+                    if (a.xi2_det)
+                        for (int J = 0; J < ND; ++J) a.xi2_det[o * ND + J] = nan;
                 }
+                continue;
+            }
+            float2 zc[NC], v[NC][NT];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                zc[q] = row[q][a.Nj];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    const int j = lane + 32 * i;
+                    v[q][i] = j < ntap ? row[q][j] : make_float2(0.f, 0.f);
+                }
+            }
+            float xq[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                float num = 0.f;
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    const float dr = v[q][i].x - (zc[q].x * Ar[i].x - zc[q].y * Ar[i].y);
+                    const float di = v[q][i].y - (zc[q].x * Ar[i].y + zc[q].y * Ar[i].x);
+                    num = fmaf(dr, dr, fmaf(di, di, num));
+                }
+                xq[q] = warp_sum(num) / den;
+            }
+            // the detectors' terms summed in detector order
+            float total = 0.f;
+#pragma unroll
+            for (int J = 0; J < ND; ++J) {
+                float xi = xi_r;
+#pragma unroll
+                for (int q = 0; q < NC; ++q)
+                    if (J == (q < r ? q : q + 1)) xi = xq[q];
                 total += xi;
-                if (a.xi2_det && lane == 0) a.xi2_det[o * nd + J] = xi;
+                if (a.xi2_det && lane == 0) a.xi2_det[o * ND + J] = xi;
             }
-            if (lane == 0) {
-                a.xi2[o] = ok ? total / nd : nan;
-                if (!ok && a.xi2_det)
-                    for (int J = 0; J < nd; ++J) a.xi2_det[o * nd + J] = nan;
-            }
+            if (lane == 0) a.xi2[o] = total / ND;
         }
+    }
+}
+
+template <int NT>
+static int launch_xi2_nd(int nd, int grid, const XiPointArgs &a, cudaStream_t st) {
+    switch (nd) {
+        case 2: k_xi2_points_reg<NT, 2><<<grid, 256, 0, st>>>(a); break;
+        case 3: k_xi2_points_reg<NT, 3><<<grid, 256, 0, st>>>(a); break;
+        default: k_xi2_points_reg<NT, 4><<<grid, 256, 0, st>>>(a); break;
+    }
+    return SPIIR_OK;
+}
+
+static int launch_xi2_reg(int NT, int nd, int grid, const XiPointArgs &a, cudaStream_t st) {
+    switch (NT) {
+        case 4: return launch_xi2_nd<4>(nd, grid, a, st);
+        case 8: return launch_xi2_nd<8>(nd, grid, a, st);
+        case 12: return launch_xi2_nd<12>(nd, grid, a, st);
+        default: return launch_xi2_nd<16>(nd, grid, a, st);
     }
 }
 
@@ -423,16 +479,13 @@ extern "C" int spiir_xi2_candidates(spiir_sky_t sky, int T, const float *snr, in
     const int64_t items = (int64_t)max_cand * ((n_shifts + kXiPtShifts - 1) / kXiPtShifts);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)n_sm * 8));
     const int nt = (2 * n_lags + 1 + 31) / 32;  // taps per lane
-    if (a.n_det <= 4 && nt <= 4)
-        k_xi2_points_reg<4><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    else if (a.n_det <= 4 && nt <= 8)
-        k_xi2_points_reg<8><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    else if (a.n_det <= 4 && nt <= 12)
-        k_xi2_points_reg<12><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    else if (a.n_det <= 4 && nt <= 16)
-        k_xi2_points_reg<16><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    else
+    const int nd = a.n_det;
+    if (nd >= 2 && nd <= 4 && nt <= 16) {
+        const int NT = nt <= 4 ? 4 : nt <= 8 ? 8 : nt <= 12 ? 12 : 16;
+        SPIIR_TRY(launch_xi2_reg(NT, nd, grid, a, (cudaStream_t)stream));
+    } else {
         k_xi2_points<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    }
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
 }
