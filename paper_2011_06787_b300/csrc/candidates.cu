@@ -28,7 +28,8 @@
 //              companions' windows of the chunk's shifts sit in shared memory, and the next
 //              item's windows are copied (cp.async) while the current one is evaluated; the
 //              reference detector's term is formed once per pixel; the lanes keep a maximum per
-//              shift and a butterfly of shuffles plus a shared-memory pass reduce them.
+//              shift, reduced over the warp by two redux.sync per shift (the largest value, then
+//              the lowest pixel holding it) and over the block through shared memory.
 //   k_points:  the general form, one block per (candidate, shift), for wide windows or large
 //              tables.
 // Both keep the largest statistic (the lowest pixel among equals) and the null stream at that
@@ -357,9 +358,9 @@ __global__ void __launch_bounds__(kPtThreads) k_points(const __grid_constant__ P
 // shift and is formed once per pixel; each shift adds the N_d - 1 companion terms.  The
 // windows are laid out [shift][companion][kPtWP], so that for one pixel the address of every
 // shift differs by a compile-time constant.  Each thread keeps a running maximum per shift;
-// a warp reduces its S (value, pixel) pairs in log2(32) butterfly steps that halve the pairs
-// a lane holds at each of the first log2(S) steps (S + log2(32 / S) shuffles per value instead
-// of 5 S), then the warps combine through shared memory.
+// a warp reduces each shift's (value, pixel) pairs with two integer reductions (redux.sync on
+// the value bits, which order as unsigned integers because the statistic is >= 0, then on the
+// pixels that hold the maximum), then the warps combine through shared memory.
 constexpr int kPtWP = 192;        // window entries per (shift, companion): wide skies
 constexpr int kPtWPNarrow = 96;   // the same when the relative delays span at most 96 samples
 constexpr int kPtChunkThreads = 128;
@@ -369,31 +370,6 @@ __device__ __forceinline__ void take_pair(float &kv, int &kp, float rv, int rp) 
         kv = rv;
         kp = rp;
     }
-}
-
-// after the halving steps lane L holds the pair of shift (L >> (5 - log2 S)) reduced over the
-// lanes that share those bits; the remaining steps reduce over the low lane bits
-template <int S>
-__device__ __forceinline__ void warp_reduce_shifts(float (&v)[S], int (&p)[S], int lane) {
-    static_assert(S == 1 || S == 2 || S == 4 || S == 8 || S == 16 || S == 32, "S must be a power of two <= 32");
-#pragma unroll
-    for (int n = S, bit = 16; n > 1; n >>= 1, bit >>= 1) {
-        const bool up = (lane & bit) != 0;
-#pragma unroll
-        for (int i = 0; i < n / 2; ++i) {
-            const float sv = up ? v[i] : v[i + n / 2];
-            const int sp = up ? p[i] : p[i + n / 2];
-            float kv = up ? v[i + n / 2] : v[i];
-            int kp = up ? p[i + n / 2] : p[i];
-            take_pair(kv, kp, __shfl_xor_sync(0xffffffffu, sv, bit), __shfl_xor_sync(0xffffffffu, sp, bit));
-            v[i] = kv;
-            p[i] = kp;
-        }
-    }
-    constexpr int kDone = (S == 1) ? 0 : (S == 2) ? 1 : (S == 4) ? 2 : (S == 8) ? 3 : (S == 16) ? 4 : 5;
-#pragma unroll
-    for (int bit = 16 >> kDone; bit > 0; bit >>= 1)
-        take_pair(v[0], p[0], __shfl_xor_sync(0xffffffffu, v[0], bit), __shfl_xor_sync(0xffffffffu, p[0], bit));
 }
 
 __device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
@@ -432,12 +408,13 @@ struct PtItem {
     int Jq[ND - 1], dmn[ND - 1], dmx[ND - 1];
 };
 
+// Items number fewer than 2^30 (the host checks), so their arithmetic is 32-bit.
 template <int ND, int S>
-__device__ __forceinline__ PtItem<ND> decode_item(const PointArgs &a, int64_t item, int n_chunks, int lane) {
+__device__ __forceinline__ PtItem<ND> decode_item(const PointArgs &a, int item, int n_chunks, int lane) {
     constexpr int NC = ND - 1;
     PtItem<ND> it;
-    it.c = (int)(item / n_chunks);
-    it.s_first = (int)(item % n_chunks) * S;
+    it.c = item / n_chunks;
+    it.s_first = (item - it.c * n_chunks) * S;
     it.ns = min(S, a.n_shifts - it.s_first);
     const int4 cd = a.cand[it.c];
     it.r = cd.x;
@@ -494,7 +471,6 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
     constexpr int NC = ND - 1;                    // companions of the reference detector
     constexpr int kShiftWords = NC * WP;          // float2 entries per shift
     constexpr int kWarps = kPtChunkThreads / 32;
-    constexpr int kLog = (S == 1) ? 0 : (S == 2) ? 1 : (S == 4) ? 2 : (S == 8) ? 3 : (S == 16) ? 4 : 5;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_v[kWarps][S];
     __shared__ int s_p[kWarps][S];
@@ -504,8 +480,8 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
     float2 *wbuf = reinterpret_cast<float2 *>(smem);                             // [2][S][NC][WP]
     const int nc = min(*a.n_cand, a.max_cand);
     const int n_chunks = (a.n_shifts + S - 1) / S;
-    const int64_t n_items = (int64_t)max(nc, 0) * n_chunks;
-    int64_t item = blockIdx.x;
+    const int n_items = max(nc, 0) * n_chunks;
+    int item = blockIdx.x;
     if (item >= n_items) return;
     PtItem<ND> cur = decode_item<ND, S>(a, item, n_chunks, lane);
     stage_item<ND, S, WP>(a, cur, wbuf, wid, lane);
@@ -514,7 +490,7 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
         float2 *win = wbuf + (k & 1) * S * kShiftWords;
         // prefetch the next item into the other buffer (freed by the barrier that ended the
         // previous iteration), then wait for this item's copies
-        const int64_t nxt = item + gridDim.x;
+        const int nxt = item + gridDim.x;
         PtItem<ND> nit = cur;
         if (nxt < n_items) {
             nit = decode_item<ND, S>(a, nxt, n_chunks, lane);
@@ -577,10 +553,22 @@ __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __g
             else
                 scan(std::integral_constant<int, S>{});
         }
-        warp_reduce_shifts<S>(best, arg, lane);
-        if ((lane & ((32 >> kLog) - 1)) == 0) {
-            s_v[wid][lane >> (5 - kLog)] = best[0];
-            s_p[wid][lane >> (5 - kLog)] = arg[0];
+        // per shift, the warp's largest value (statistics are >= 0, so their bits order as
+        // unsigned integers; no pixel counts as 0) and the lowest pixel holding it; lane i
+        // keeps shift i's pair
+        float rv = -1.f;
+        int rp = INT_MAX;
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const unsigned u = best[i] >= 0.f ? __float_as_uint(best[i]) : 0u;
+            const unsigned m = __reduce_max_sync(0xffffffffu, u);
+            const unsigned pm = __reduce_min_sync(0xffffffffu, u == m ? (unsigned)arg[i] : 0xFFFFFFFFu);
+            rv = lane == i ? __uint_as_float(m) : rv;
+            rp = lane == i ? (int)pm : rp;
+        }
+        if (lane < S) {
+            s_v[wid][lane] = rv;
+            s_p[wid][lane] = rp;
         }
         __syncthreads();
         if (tid < cur.ns) {
@@ -928,7 +916,8 @@ extern "C" int spiir_coherent_candidates(spiir_sky_t sky, int T, const float *sn
     {
         const int S = chunk_shifts(ND, n_shifts);
         const size_t chunk_bytes = 2 * sizeof(float2) * (size_t)S * (ND - 1) * kPtWP;  // double-buffered windows
-        if (Wmax <= kPtWP && chunk_bytes <= (size_t)kPtChunkSmem) {
+        const int64_t items = (int64_t)max_cand * ((n_shifts + S - 1) / S);              // 32-bit item numbers
+        if (Wmax <= kPtWP && chunk_bytes <= (size_t)kPtChunkSmem && items < (1 << 30)) {
             a.tab_bytes = 0;
             switch (ND) {
                 case 2: return dispatch_chunked<2>(a, st);
