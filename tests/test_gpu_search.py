@@ -233,3 +233,32 @@ def test_search_rejects_bad_arguments_and_resets():
     assert torch.equal(s.cand[:n], c1[0][:n]) and torch.equal(s.fg[0][:n], c1[2][:n])
     with pytest.raises(sp.SpiirError):
         s.run(torch.zeros((3, 100), dtype=torch.float32, device="cuda"))   # rows shorter than a chunk
+
+
+def test_search_candidate_overflow_keeps_the_first_records():
+    """With max_cand below the number of candidates, the first max_cand records and their
+    zero-lag, background and xi^2 results are those of a search with room for all of them,
+    and the count reports the total."""
+    import torch
+    import paper_2011_06787_b300 as sp
+    det = synth.detectors(5, 3)
+    sigma = synth.noise_weights(5, 3, 0.5, 2.0)
+    sky = sp.Sky(*sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, sigma, 4, 2048.0))
+    bank = synth.random_bank(synth.rng(5, "misc", 2), [20, 30, 25, 18], d_max=300)
+    A = torch.zeros((4, 2 * 10 + 1), dtype=torch.complex64, device="cuda")
+    A[:, 10] = 1.0
+    kw = dict(threshold=0.5, per_second=64, n_shifts=3, shift_step=40)
+    big = sp.Search(sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay), sky, sky, A, 10, 512, max_cand=4096, **kw)
+    small = sp.Search(sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay), sky, sky, A, 10, 512, max_cand=8, **kw)
+    for c in range(4):
+        x = torch.from_numpy(synth.white_noise(5, 3, 512, sub=40 + c)).cuda()
+        assert big.run(x) == small.run(x)
+        torch.cuda.synchronize()
+        n = int(big.n_cand.item())
+        assert n > 8 and int(small.n_cand.item()) == n
+        assert torch.equal(small.cand[:8], big.cand[:8])
+        for a, b in zip(small.fg, big.fg):
+            assert torch.equal(a[:8], b[:8]) or torch.allclose(a[:8], b[:8], equal_nan=True, rtol=0, atol=0)
+        for a, b in zip(small.bg, big.bg):
+            assert torch.equal(a[:8], b[:8]) or torch.allclose(a[:8], b[:8], equal_nan=True, rtol=0, atol=0)
+    sp.device_status()
