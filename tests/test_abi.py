@@ -95,3 +95,16 @@ def test_wait_timeout_hook_rejects_bad_limits():
     L = native.lib()
     for it in (0, (1 << 26) + 1):
         assert L.spiir_debug_wait_timeout(it, None) == native.EINVAL
+
+
+def test_select_workspace_size():
+    """One 64-bit slot per (detector, template, second), one 64-bit key per (detector, sample)
+    and one word for the compaction's block counter; invalid sizes are rejected."""
+    L = native.lib()
+    nb = ctypes.c_size_t()
+    for T, nd, n, ps in [(1024, 3, 2048, 2048), (37, 3, 5000, 2048), (1, 1, 1, 7)]:
+        assert L.spiir_select_workspace_bytes(T, nd, n, ps, ctypes.byref(nb)) == 0
+        n_sec = -(-n // ps)
+        assert nb.value == 8 * (nd * (T * n_sec + n) + 1)
+    assert L.spiir_select_workspace_bytes(0, 3, 2048, 2048, ctypes.byref(nb)) == native.EINVAL
+    assert L.spiir_select_workspace_bytes(16, 3, 0, 2048, ctypes.byref(nb)) == native.EINVAL
