@@ -818,6 +818,7 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop, bank):
     t_xf = float(np.mean(timed_loop(xi_fore, steps)))
     t_xb = float(np.mean(timed_loop(xi_back, steps)))
     t_all = float(np.mean(timed_loop(whole, steps)))
+    kern_us = candidate_kernel_times(torch, whole)
     xi_fin = float(torch.nanmean(xf[:n_c]).item()) if n_c else None
     sp.device_status()
     sel_bytes = T * 3 * n * 8
@@ -838,6 +839,11 @@ def candidates_rate(args, torch, sp, det, sigma, timed_loop, bank):
            "pixel_evaluations_per_s": (evals_fg + evals_bg) / (t_all * 1e-3),
            "select_gbs": sel_bytes / (t_sel * 1e-3) / 1e9,
            "select_frac_of_measured_hbm": (sel_bytes / (t_sel * 1e-3) / 1e9 / hbm) if hbm else None,
+           # the kernels alone (CUDA activity records, outside the timed region): the selection
+           # kernel's own HBM fraction, without the compaction launch and the launch gaps
+           "kernel_us_profiler": kern_us,
+           "select_kernel_frac_of_measured_hbm": (sel_bytes / (kern_us["k_select"] * 1e-6) / 1e9 / hbm)
+           if hbm and kern_us.get("k_select") else None,
            # xi^2 under the shifts: companion c of a candidate reads n_sh windows of 2 Nj + 1
            # samples, c step apart (overlapping when c step < 2 Nj + 1), and the reference detector
            # one window; each sample read once from HBM at best
@@ -923,6 +929,44 @@ def adjoint_rate(args, torch, dev, flush, timed_loop):
             "forward_steps_per_s": fs / (f_ms * 1e-3), "backward_steps_per_s": fs / (b_ms * 1e-3),
             "backward_note": "loss.backward(): torch ops of the overlap loss plus the adjoint kernel",
             "kernel_shares": shares}
+
+
+def candidate_kernel_times(torch, step, reps=4):
+    """Device time per launch (us) of each candidate-stage kernel over reps calls of step, each
+    after a 512 MiB L2-flushing write, from the CUDA activity records of torch.profiler (an
+    untimed pass; the section's timings are the CUDA-event ones).  The zero-lag and background
+    scans are told apart by their shift-chunk template argument."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            for i in range(reps):
+                flush.fill_(float(i))
+                step(i)
+            torch.cuda.synchronize()
+        keys = (("k_select", "k_select"), ("k_compact", "k_compact"),
+                ("k_points_chunked<3, 1,", "k_points_chunked zero lag"),
+                ("k_points_chunked<3, 16,", "k_points_chunked background"))
+        tot, cnt, xi = {}, {}, []
+        for ev in prof.events():
+            if getattr(ev.device_type, "name", "") != "CUDA":
+                continue
+            if "k_xi2_points_reg" in ev.name:
+                xi.append((ev.time_range.start, ev.time_range.elapsed_us()))
+            for pat, name in keys:
+                if pat in ev.name:
+                    tot[name] = tot.get(name, 0.0) + ev.time_range.elapsed_us()
+                    cnt[name] = cnt.get(name, 0) + 1
+        # each step launches the zero-lag xi^2, then the background one
+        for j, (_, us) in enumerate(sorted(xi)):
+            name = "k_xi2_points_reg zero lag" if j % 2 == 0 else "k_xi2_points_reg background"
+            tot[name] = tot.get(name, 0.0) + us
+            cnt[name] = cnt.get(name, 0) + 1
+        del flush
+        return {k: round(tot[k] / cnt[k], 2) for k in tot}
+    except Exception as e:  # the profiler is optional; the measurement above stands without it
+        return {"unavailable": str(e)[:200]}
 
 
 def adjoint_kernel_shares(torch, fwd, loss_and_bwd):
