@@ -636,7 +636,20 @@ def search_rate(args, torch, sp, det, sigma, timed_loop):
     sp.device_status()
     ms = float(np.mean(t))
     updates = int(bank.n_filters) * 3 * n
-    del srch, b, zb, A
+    del srch, b, zb
+    # overlapped mode: each call's candidate stages (the previous chunk's span) on the search's
+    # own stream beside the filter bank's new chunk
+    b2 = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+    srch2 = sp.Search(b2, sky16, sky8, A, Nj, n, 4.0, 2048, n_sh, step, max_cand=16384, overlap=True)
+    L2 = srch2.info()[0]
+    fill2 = (L2 + n - 1) // n
+    xs2 = [xs[i % len(xs)] for i in range(fill2 + steps)]
+    for i in range(fill2):
+        srch2.run(xs2[i])
+    t2 = timed_loop(lambda i: srch2.run(xs2[fill2 + i]), steps)
+    sp.device_status()
+    ms2 = float(np.mean(t2))
+    del srch2, b2, A
     torch.cuda.empty_cache()
     return {"workload": f"online bank (1024 templates, E|z|^2 ~ 2), 3 det, {n}-sample chunks; threshold 4; "
                         f"zero lag nside 16, {n_sh} shifts x {step} samples on nside 8; xi^2 Nj = {Nj}; "
@@ -644,6 +657,9 @@ def search_rate(args, torch, sp, det, sigma, timed_loop):
             "steps": steps, "ms_per_second_of_data": ms, "candidates_per_chunk": float(np.mean(cnts)),
             "updates_per_s": updates / (ms * 1e-3), "filter_bank_ms": k1,
             "candidate_stages_ms": ms - k1,
+            "overlapped": {"ms_per_second_of_data": ms2, "updates_per_s": updates / (ms2 * 1e-3),
+                           "ring_samples": L2, "note": "each call analyses the previous chunk's span on the "
+                                                       "search's own stream beside the new chunk's filter bank"},
             "roofline": k1_roofline(updates, k1)}
 
 

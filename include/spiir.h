@@ -434,18 +434,26 @@ int spiir_xi2_candidates(spiir_sky_t sky, int n_templates, const float *snr_dev,
  * stored twice so that any L consecutive samples are contiguous).  Samples before the stream
  * start are zero.  Seconds (one candidate per template per second) are blocks of per_second
  * samples counted from S0.
+ * Overlapped mode (SPIIR_SEARCH_OVERLAP): a call analyses the span that the ring surrounded
+ * before the call, S0 = (samples filtered before the call) - chunk - La, on an internal
+ * stream, while the filter bank takes the new chunk on the caller's stream; the caller's
+ * stream then waits for the candidate stages.  The search lags one chunk more, the ring keeps
+ * L = Hb + 2 chunk + La samples, and the first call's span lies before the stream start.
  * ---------------------------------------------------------------------------------- */
+
+#define SPIIR_SEARCH_OVERLAP 1 /* flag of spiir_search_create */
 
 /* bank, sky_fg (zero lag; nside 16 in the paper), sky_bg (time shifts; nside 8) must share
  * n_det >= 2 and outlive the search, and the bank is driven only through it.  A_dev
  * [T][2 n_lags + 1] complex: each template's autocorrelation as for spiir_xi2 (copied).
  * chunk: strain samples per call.  threshold: |z| above which a sample is a candidate (4 in
  * the paper).  n_shifts (100 in the paper, 0 for none) time shifts of shift_step samples per
- * companion (205 = 0.1 s at 2048 Hz).  max_cand: rows of the candidate outputs.
- * Errors: SPIIR_EINVAL, SPIIR_ENOMEM, SPIIR_ECUDA. */
+ * companion (205 = 0.1 s at 2048 Hz).  max_cand: rows of the candidate outputs.  flags: 0 or
+ * SPIIR_SEARCH_OVERLAP (the search then owns a CUDA stream and two events on the current
+ * device).  Errors: SPIIR_EINVAL, SPIIR_ENOMEM, SPIIR_ECUDA. */
 int spiir_search_create(spiir_bank_t bank, spiir_sky_t sky_fg, spiir_sky_t sky_bg, const float *A_dev,
                         int n_lags, int64_t chunk, float threshold, int per_second, int n_shifts,
-                        int shift_step, int max_cand, spiir_search_t *out);
+                        int shift_step, int max_cand, int flags, spiir_search_t *out);
 void spiir_search_destroy(spiir_search_t search);
 /* Ring length L, history Hb and lag La (samples), and S0 of the next call's span. */
 int spiir_search_info(spiir_search_t search, int64_t *ring_len, int64_t *history, int64_t *lag,
@@ -462,7 +470,9 @@ int spiir_search_reset(spiir_search_t search, void *stream);
  *   bg_*_dev [max_cand][n_shifts]: the same for shifts 1 .. n_shifts on the background sky
  *     (may be NULL when n_shifts = 0).
  *   span_start: NULL or a host int64 that receives S0.
- * Calls on one search must be ordered on one stream.  Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
+ * Calls on one search must be ordered on one stream; in overlapped mode the outputs are
+ * written on the internal stream and are complete, in the caller's stream order, after the
+ * call's work.  Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
 int spiir_search_run(spiir_search_t search, const float *strain_dev, int64_t strain_pitch,
                      int32_t *cand_dev, int32_t *n_cand_dev, float *fg_max_dev,
                      int32_t *fg_argmax_dev, float *fg_null_dev, float *fg_xi2_dev,

@@ -303,16 +303,22 @@ class Search:
     ring, candidate selection, zero-lag scan on sky_fg, time-shift background on sky_bg and
     xi_C^2 at the candidates (Sec. II.C.1 - II.C.3).  A [T][2 n_lags + 1] complex64 CUDA tensor
     of the templates' autocorrelations.  Output tensors are allocated once and overwritten by
-    every run(); rows past the count keep older values."""
+    every run(); rows past the count keep older values.  overlap=True: each run() analyses the
+    span completed by the previous chunk on an internal stream while the new chunk is filtered
+    (SPIIR_SEARCH_OVERLAP)."""
+
+    OVERLAP = 1
 
     def __init__(self, bank: Bank, sky_fg: Sky, sky_bg: Sky, A, n_lags: int, chunk: int, threshold: float = 4.0,
-                 per_second: int = 2048, n_shifts: int = 100, shift_step: int = 205, max_cand: int = 16384):
+                 per_second: int = 2048, n_shifts: int = 100, shift_step: int = 205, max_cand: int = 16384,
+                 overlap: bool = False):
         import torch
         _require_cuda(A, torch.complex64, "A")
         h = ctypes.c_void_p()
         check(native.lib().spiir_search_create(bank.handle, sky_fg.handle, sky_bg.handle, _dev_ptr(A), int(n_lags),
                                                int(chunk), float(threshold), int(per_second), int(n_shifts),
-                                               int(shift_step), int(max_cand), ctypes.byref(h)))
+                                               int(shift_step), int(max_cand), self.OVERLAP if overlap else 0,
+                                               ctypes.byref(h)))
         self._h = h
         self.bank, self.sky_fg, self.sky_bg = bank, sky_fg, sky_bg
         self.chunk, self.n_shifts, self.max_cand = int(chunk), int(n_shifts), int(max_cand)

@@ -18,6 +18,13 @@
 // sample (H the larger sky halo, Nj the xi^2 half-width), the most the zero-lag stages read
 // past a candidate; the background and xi^2 read back at most
 // Hb = n_shifts (n_det - 1) step + 2 H + Nj samples before it.  L = Hb + chunk + La.
+//
+// Overlapped mode.  A call forks an internal stream from the caller's, runs the candidate
+// stages there on the span the ring surrounded before the call, while the filter bank writes
+// the new chunk on the caller's stream, and joins back.  The ring then keeps one chunk more,
+// L = Hb + 2 chunk + La, so that the chunk being written (samples pos .. pos + chunk - 1, at
+// the ring positions of samples pos - L ..) never shares an entry with the span's reads
+// (samples pos - L + chunk .. pos - 1).
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
@@ -38,6 +45,9 @@ struct spiir_search_s {
     float2 *A = nullptr;                // [T][2 n_lags + 1]
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    bool overlap = false;
+    cudaStream_t side = nullptr;          // overlapped mode: the candidate stages' stream
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace spiir {
@@ -47,6 +57,9 @@ static void search_free(spiir_search_s *s) {
     dev_free(s->ring);
     dev_free(s->A);
     dev_free(s->ws);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->join) cudaEventDestroy(s->join);
     delete s;
 }
 
@@ -61,7 +74,7 @@ using namespace spiir;
 
 extern "C" int spiir_search_create(spiir_bank_t bank, spiir_sky_t sky_fg, spiir_sky_t sky_bg, const float *A_dev,
                                    int n_lags, int64_t chunk, float threshold, int per_second, int n_shifts,
-                                   int shift_step, int max_cand, spiir_search_t *out) {
+                                   int shift_step, int max_cand, int flags, spiir_search_t *out) {
     clear_error();
     if (!out) return fail(SPIIR_EINVAL, "out is NULL");
     *out = nullptr;
@@ -78,6 +91,7 @@ extern "C" int spiir_search_create(spiir_bank_t bank, spiir_sky_t sky_fg, spiir_
     if (max_cand < 1 || (int64_t)max_cand * std::max(n_shifts, 1) > INT32_MAX)
         return fail(SPIIR_EINVAL, "max_cand = %d (with %d shifts)", max_cand, n_shifts);
     if (((uintptr_t)A_dev) % 8) return fail(SPIIR_EINVAL, "A_dev must be 8-byte aligned");
+    if (flags & ~SPIIR_SEARCH_OVERLAP) return fail(SPIIR_EINVAL, "unknown flags 0x%x", flags);
     spiir_search_s *s = new (std::nothrow) spiir_search_s();
     if (!s) return fail(SPIIR_ENOMEM, "host allocation of the search failed");
     s->bank = bank;
@@ -95,9 +109,15 @@ extern "C" int spiir_search_create(spiir_bank_t bank, spiir_sky_t sky_fg, spiir_
     const int64_t H = std::max(sky_fg->halo, sky_bg->halo);
     s->look = 2 * H + n_lags;
     s->hist = (int64_t)n_shifts * (s->n_det - 1) * shift_step + 2 * H + n_lags;
-    s->L = s->hist + chunk + s->look;
+    s->overlap = (flags & SPIIR_SEARCH_OVERLAP) != 0;
+    s->L = s->hist + (s->overlap ? 2 : 1) * chunk + s->look;
     const size_t ring_bytes = sizeof(float2) * (size_t)s->T * s->n_det * 2 * (size_t)s->L;
     int rc = dev_alloc((void **)&s->ring, ring_bytes, "SNR ring");
+    if (rc == SPIIR_OK && s->overlap &&
+        (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming) != cudaSuccess))
+        rc = fail(SPIIR_ECUDA, "stream or event creation failed");
     if (rc == SPIIR_OK) rc = dev_alloc((void **)&s->A, sizeof(float2) * (size_t)s->T * (2 * n_lags + 1), "autocorrelations");
     if (rc == SPIIR_OK) rc = spiir_select_workspace_bytes(s->T, s->n_det, chunk, per_second, &s->ws_bytes);
     if (rc == SPIIR_OK) rc = dev_alloc(&s->ws, s->ws_bytes, "selection workspace");
@@ -124,7 +144,7 @@ extern "C" int spiir_search_info(spiir_search_t s, int64_t *ring_len, int64_t *h
     if (ring_len) *ring_len = s->L;
     if (history) *history = s->hist;
     if (lag) *lag = s->look;
-    if (next_span_start) *next_span_start = s->pos - s->look;
+    if (next_span_start) *next_span_start = s->pos - (s->overlap ? s->chunk : 0) - s->look;
     return SPIIR_OK;
 }
 
@@ -136,6 +156,60 @@ extern "C" int spiir_search_reset(spiir_search_t s, void *stream) {
     s->pos = 0;
     return SPIIR_OK;
 }
+
+namespace spiir {
+
+// The chunk's SNR into the ring at p = pos mod L, then its mirror image.
+static int filter_into_ring(spiir_search_s *s, const float *strain_dev, int64_t strain_pitch, cudaStream_t st) {
+    const int64_t n = s->chunk, L = s->L, P2 = 2 * L;
+    const size_t rows = (size_t)s->T * s->n_det, pitch_b = sizeof(float2) * (size_t)P2;
+    const int64_t p = floor_mod(s->pos, L);
+    SPIIR_TRY(bank_filter(s->bank, strain_dev, strain_pitch, n, s->ring + p, P2, st));
+    if (p < L) {
+        const int64_t w = std::min(p + n, L) - p;
+        if (cudaMemcpy2DAsync(s->ring + p + L, pitch_b, s->ring + p, pitch_b, sizeof(float2) * w, rows,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return fail(SPIIR_ECUDA, "mirror copy failed");
+    }
+    if (p + n > L) {
+        const int64_t w = p + n - L;
+        if (cudaMemcpy2DAsync(s->ring, pitch_b, s->ring + L, pitch_b, sizeof(float2) * w, rows,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return fail(SPIIR_ECUDA, "mirror copy failed");
+    }
+    return SPIIR_OK;
+}
+
+// The candidate stages on the span [S0, S0 + n): entry off + k of a row is stream sample
+// S0 + k, and the entries off - Hb .. off + n + La are the consecutive samples they read.
+static int candidate_stages(spiir_search_s *s, int64_t S0, int32_t *cand_dev, int32_t *n_cand_dev,
+                            float *fg_max_dev, int32_t *fg_argmax_dev, float *fg_null_dev, float *fg_xi2_dev,
+                            float *bg_max_dev, int32_t *bg_argmax_dev, float *bg_null_dev, float *bg_xi2_dev,
+                            cudaStream_t st) {
+    const int64_t n = s->chunk, L = s->L, P2 = 2 * L;
+    const int64_t off = floor_mod(S0 - s->hist, L) + s->hist;
+    const float *ring = reinterpret_cast<const float *>(s->ring);
+    void *stream = (void *)st;
+    // 2. selection
+    SPIIR_TRY(spiir_select_candidates(s->T, s->n_det, ring, P2, off, n, s->threshold, s->per_second, s->ws,
+                                      s->ws_bytes, cand_dev, s->max_cand, n_cand_dev, stream));
+    // 3. zero lag on the foreground sky; 4. shifts 1 .. n_shifts on the background sky
+    SPIIR_TRY(spiir_coherent_candidates(s->fg, s->T, ring, P2, off, cand_dev, n_cand_dev, s->max_cand, 0, 1, s->step,
+                                        fg_max_dev, fg_argmax_dev, fg_null_dev, stream));
+    if (s->n_shifts > 0)
+        SPIIR_TRY(spiir_coherent_candidates(s->bg, s->T, ring, P2, off, cand_dev, n_cand_dev, s->max_cand, 1,
+                                            s->n_shifts, s->step, bg_max_dev, bg_argmax_dev, bg_null_dev, stream));
+    // 5. xi_C^2 at each candidate's coherent argmax, zero lag and every shift
+    const float *A = reinterpret_cast<const float *>(s->A);
+    SPIIR_TRY(spiir_xi2_candidates(s->fg, s->T, ring, P2, off, A, s->n_lags, cand_dev, n_cand_dev, s->max_cand, 0, 1,
+                                   s->step, fg_argmax_dev, fg_xi2_dev, nullptr, stream));
+    if (s->n_shifts > 0)
+        SPIIR_TRY(spiir_xi2_candidates(s->bg, s->T, ring, P2, off, A, s->n_lags, cand_dev, n_cand_dev, s->max_cand,
+                                       1, s->n_shifts, s->step, bg_argmax_dev, bg_xi2_dev, nullptr, stream));
+    return SPIIR_OK;
+}
+
+}  // namespace spiir
 
 extern "C" int spiir_search_run(spiir_search_t s, const float *strain_dev, int64_t strain_pitch, int32_t *cand_dev,
                                 int32_t *n_cand_dev, float *fg_max_dev, int32_t *fg_argmax_dev, float *fg_null_dev,
@@ -151,50 +225,36 @@ extern "C" int spiir_search_run(spiir_search_t s, const float *strain_dev, int64
     if (((uintptr_t)cand_dev) % 16) return fail(SPIIR_EINVAL, "cand_dev must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     nvtxRangePushA("spiir.search_chunk");
-    const int64_t n = s->chunk, L = s->L, P2 = 2 * L;
-    const size_t rows = (size_t)s->T * s->n_det, pitch_b = sizeof(float2) * (size_t)P2;
-    // 1. the chunk's SNR into the ring at p = pos mod L, then its mirror image
-    const int64_t p = floor_mod(s->pos, L);
-    int rc = bank_filter(s->bank, strain_dev, strain_pitch, n, s->ring + p, P2, st);
-    if (rc == SPIIR_OK && p < L) {
-        const int64_t w = std::min(p + n, L) - p;
-        if (cudaMemcpy2DAsync(s->ring + p + L, pitch_b, s->ring + p, pitch_b, sizeof(float2) * w, rows,
-                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            rc = fail(SPIIR_ECUDA, "mirror copy failed");
+    const int64_t n = s->chunk;
+    int rc = SPIIR_OK;
+    int64_t S0 = 0;
+    if (!s->overlap) {
+        // 1. the chunk into the ring, then the span that the ring now surrounds
+        rc = filter_into_ring(s, strain_dev, strain_pitch, st);
+        if (rc == SPIIR_OK) {
+            s->pos += n;
+            S0 = s->pos - n - s->look;
+            rc = candidate_stages(s, S0, cand_dev, n_cand_dev, fg_max_dev, fg_argmax_dev, fg_null_dev, fg_xi2_dev,
+                                  bg_max_dev, bg_argmax_dev, bg_null_dev, bg_xi2_dev, st);
+        }
+    } else {
+        // the span the ring surrounded before this call, on the internal stream, beside the
+        // filter bank's new chunk on the caller's stream; then the caller's stream waits
+        S0 = s->pos - n - s->look;
+        if (cudaEventRecord(s->fork, st) != cudaSuccess || cudaStreamWaitEvent(s->side, s->fork, 0) != cudaSuccess) {
+            nvtxRangePop();
+            return fail(SPIIR_ECUDA, "stream fork failed");
+        }
+        rc = candidate_stages(s, S0, cand_dev, n_cand_dev, fg_max_dev, fg_argmax_dev, fg_null_dev, fg_xi2_dev,
+                              bg_max_dev, bg_argmax_dev, bg_null_dev, bg_xi2_dev, s->side);
+        const int rc_f = rc == SPIIR_OK ? filter_into_ring(s, strain_dev, strain_pitch, st) : rc;
+        // joined whatever happened, so that the caller's stream never runs ahead of the stages
+        const bool joined = cudaEventRecord(s->join, s->side) == cudaSuccess &&
+                            cudaStreamWaitEvent(st, s->join, 0) == cudaSuccess;
+        rc = rc_f;
+        if (rc == SPIIR_OK && !joined) rc = fail(SPIIR_ECUDA, "stream join failed");
+        if (rc == SPIIR_OK) s->pos += n;
     }
-    if (rc == SPIIR_OK && p + n > L) {
-        const int64_t w = p + n - L;
-        if (cudaMemcpy2DAsync(s->ring, pitch_b, s->ring + L, pitch_b, sizeof(float2) * w, rows,
-                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            rc = fail(SPIIR_ECUDA, "mirror copy failed");
-    }
-    if (rc != SPIIR_OK) {
-        nvtxRangePop();
-        return rc;
-    }
-    s->pos += n;
-    // 2. the span [S0, S0 + n): entry off + k of a row is stream sample S0 + k, and the
-    //    entries off - Hb .. off + n + La are the L consecutive samples the later stages read
-    const int64_t S0 = s->pos - n - s->look;
-    const int64_t off = floor_mod(S0 - s->hist, L) + s->hist;
-    const float *ring = reinterpret_cast<const float *>(s->ring);
-    rc = spiir_select_candidates(s->T, s->n_det, ring, P2, off, n, s->threshold, s->per_second, s->ws, s->ws_bytes,
-                                 cand_dev, s->max_cand, n_cand_dev, stream);
-    // 3. zero lag on the foreground sky; 4. shifts 1 .. n_shifts on the background sky
-    if (rc == SPIIR_OK)
-        rc = spiir_coherent_candidates(s->fg, s->T, ring, P2, off, cand_dev, n_cand_dev, s->max_cand, 0, 1, s->step,
-                                       fg_max_dev, fg_argmax_dev, fg_null_dev, stream);
-    if (rc == SPIIR_OK && s->n_shifts > 0)
-        rc = spiir_coherent_candidates(s->bg, s->T, ring, P2, off, cand_dev, n_cand_dev, s->max_cand, 1, s->n_shifts,
-                                       s->step, bg_max_dev, bg_argmax_dev, bg_null_dev, stream);
-    // 5. xi_C^2 at each candidate's coherent argmax, zero lag and every shift
-    const float *A = reinterpret_cast<const float *>(s->A);
-    if (rc == SPIIR_OK)
-        rc = spiir_xi2_candidates(s->fg, s->T, ring, P2, off, A, s->n_lags, cand_dev, n_cand_dev, s->max_cand, 0, 1,
-                                  s->step, fg_argmax_dev, fg_xi2_dev, nullptr, stream);
-    if (rc == SPIIR_OK && s->n_shifts > 0)
-        rc = spiir_xi2_candidates(s->bg, s->T, ring, P2, off, A, s->n_lags, cand_dev, n_cand_dev, s->max_cand, 1,
-                                  s->n_shifts, s->step, bg_argmax_dev, bg_xi2_dev, nullptr, stream);
     nvtxRangePop();
     if (rc == SPIIR_OK && span_start) *span_start = S0;
     return rc;

@@ -80,7 +80,7 @@ SIGNATURES = {
     "spiir_batch_set_shape": (_I, [_P, _I, _I, _I, _I]),
     "spiir_batch_run": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "spiir_batch_filter_time": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
-    "spiir_search_create": (_I, [_P, _P, _P, _P, _I, _I64, ctypes.c_float, _I, _I, _I, _I, ctypes.POINTER(_P)]),
+    "spiir_search_create": (_I, [_P, _P, _P, _P, _I, _I64, ctypes.c_float, _I, _I, _I, _I, _I, ctypes.POINTER(_P)]),
     "spiir_search_destroy": (None, [_P]),
     "spiir_search_info": (_I, [_P, _P, _P, _P, _P]),
     "spiir_search_reset": (_I, [_P, _P]),

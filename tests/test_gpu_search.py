@@ -104,10 +104,12 @@ def _xi2_oracle(zp, A, Nj, t, r, e, p, d_or, shift):
     return float(np.mean(vals))
 
 
-@pytest.mark.parametrize("case,nd", [("short", 3), ("paper", 3), ("short", 2), ("short", 4)])
-def test_search_on_injected_chirps_matches_the_oracle(case, nd):
+@pytest.mark.parametrize("case,nd,overlap", [("short", 3, False), ("paper", 3, False), ("short", 2, False),
+                                             ("short", 4, False), ("short", 3, True), ("paper", 3, True)])
+def test_search_on_injected_chirps_matches_the_oracle(case, nd, overlap):
     """Three detectors with short and with the paper's shifts; two (null stream zero) and four
-    detectors (three companions per candidate) with short shifts."""
+    detectors (three companions per candidate) with short shifts; the overlapped mode (the span
+    of the previous chunk analysed beside the filter bank) with three detectors."""
     import torch
     import paper_2011_06787_b300 as sp
     cfg = 5
@@ -142,16 +144,17 @@ def test_search_on_injected_chirps_matches_the_oracle(case, nd):
     _, Gb, db = oracle.sky_geometry(det, sigma, nside_bg, 2048.0)
     b = sp.Bank(nd, bank.offsets, bank.a1, bank.b0, bank.delay)
     At = torch.from_numpy(A).cuda()
-    srch = sp.Search(b, skf, skb, At, Nj, chunk, thr, per_second, n_sh, step, max_cand=4096)
+    srch = sp.Search(b, skf, skb, At, Nj, chunk, thr, per_second, n_sh, step, max_cand=4096, overlap=overlap)
     L, Hb, La, _ = srch.info()
     H = max(skf.halo, skb.halo)
-    assert La == 2 * H + Nj and Hb == n_sh * (nd - 1) * step + 2 * H + Nj and L == Hb + chunk + La
+    lag = chunk if overlap else 0  # the overlapped mode analyses the previous call's span
+    assert La == 2 * H + Nj and Hb == n_sh * (nd - 1) * step + 2 * H + Nj and L == Hb + chunk + lag + La
     assert N > L    # the ring wraps around
 
     # oracle: the whole stream through the FP64 bank, zero before the stream start
     oracle.set_threads(16)
     z_or, _, _ = oracle.filter_bank(x, bank.offsets, bank.a1, bank.b0, bank.delay)
-    pad = Hb + La
+    pad = Hb + La + lag
     zp = np.concatenate([np.zeros((T, nd, pad)), z_or], axis=2)
 
     n_matched = n_diff = 0
@@ -160,7 +163,7 @@ def test_search_on_injected_chirps_matches_the_oracle(case, nd):
         xc = torch.from_numpy(np.ascontiguousarray(x[:, c * chunk:(c + 1) * chunk])).cuda()
         S0 = srch.run(xc)
         torch.cuda.synchronize()
-        assert S0 == (c + 1) * chunk - chunk - La
+        assert S0 == (c + 1) * chunk - chunk - La - lag
         cnt = int(srch.n_cand.item())
         assert cnt <= srch.max_cand
         got = [tuple(r) for r in srch.cand[:cnt].cpu().numpy()]
@@ -235,7 +238,8 @@ def test_search_rejects_bad_arguments_and_resets():
         s.run(torch.zeros((3, 100), dtype=torch.float32, device="cuda"))   # rows shorter than a chunk
 
 
-def test_search_candidate_overflow_keeps_the_first_records():
+@pytest.mark.parametrize("overlap", [False, True])
+def test_search_candidate_overflow_keeps_the_first_records(overlap):
     """With max_cand below the number of candidates, the first max_cand records and their
     zero-lag, background and xi^2 results are those of a search with room for all of them,
     and the count reports the total."""
@@ -247,14 +251,17 @@ def test_search_candidate_overflow_keeps_the_first_records():
     bank = synth.random_bank(synth.rng(5, "misc", 2), [20, 30, 25, 18], d_max=300)
     A = torch.zeros((4, 2 * 10 + 1), dtype=torch.complex64, device="cuda")
     A[:, 10] = 1.0
-    kw = dict(threshold=0.5, per_second=64, n_shifts=3, shift_step=40)
+    kw = dict(threshold=0.5, per_second=64, n_shifts=3, shift_step=40, overlap=overlap)
     big = sp.Search(sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay), sky, sky, A, 10, 512, max_cand=4096, **kw)
     small = sp.Search(sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay), sky, sky, A, 10, 512, max_cand=8, **kw)
-    for c in range(4):
+    for c in range(5):
         x = torch.from_numpy(synth.white_noise(5, 3, 512, sub=40 + c)).cuda()
         assert big.run(x) == small.run(x)
         torch.cuda.synchronize()
         n = int(big.n_cand.item())
+        if overlap and c == 0:
+            assert n == 0       # the first span lies before the stream start
+            continue
         assert n > 8 and int(small.n_cand.item()) == n
         assert torch.equal(small.cand[:8], big.cand[:8])
         for a, b in zip(small.fg, big.fg):
