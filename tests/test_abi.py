@@ -108,3 +108,18 @@ def test_select_workspace_size():
         assert nb.value == 8 * (nd * (T * n_sec + n) + 1)
     assert L.spiir_select_workspace_bytes(0, 3, 2048, 2048, ctypes.byref(nb)) == native.EINVAL
     assert L.spiir_select_workspace_bytes(16, 3, 0, 2048, ctypes.byref(nb)) == native.EINVAL
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    """include/spiir.h is a C header: it compiles as C99 with warnings as errors (no C++ or CUDA
+    types in the signatures)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "spiir.h"\nint main(void) { return SPIIR_OK; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
