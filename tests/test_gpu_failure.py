@@ -102,6 +102,33 @@ def test_injected_allocation_failures_fail_the_create_calls_cleanly():
     sp.device_status()
 
 
+@pytest.mark.parametrize("overlap", [False, True])
+def test_injected_allocation_failures_fail_the_search_cleanly(overlap):
+    """Every allocation of a streaming search's set-up and first chunk (its bank, sky, ring,
+    autocorrelations, selection workspace and the sky's lazily built point table) fails
+    cleanly when injected, and the library stays usable."""
+    import torch
+    import paper_2011_06787_b300 as sp
+    from paper_2011_06787_b300 import native
+    L = native.lib()
+    det = synth.detectors(5, 3)
+    tabs = sp.sky_tables(det.pos_m, det.arm_x, det.arm_y, synth.noise_weights(5, 3, 0.5, 2.0), 4, 2048.0)
+    bank = synth.random_bank(synth.rng(5, "misc", 3), [20, 30, 25], d_max=300)
+
+    def search_and_run():
+        sky = sp.Sky(*tabs)
+        b = sp.Bank(3, bank.offsets, bank.a1, bank.b0, bank.delay)
+        A = torch.zeros((3, 21), dtype=torch.complex64, device="cuda")
+        A[:, 10] = 1.0
+        s = sp.Search(b, sky, sky, A, 10, 512, n_shifts=2, shift_step=40, max_cand=64, overlap=overlap)
+        s.run(torch.zeros((3, 512), device="cuda"))
+        torch.cuda.synchronize()
+
+    assert _walk_allocation_sites(L, native, sp, search_and_run) >= 6
+    _tiny_filter_check()
+    sp.device_status()
+
+
 def test_injected_failures_in_the_first_asynchronous_step_are_resumable():
     """The second staging set of the asynchronous host-buffer steps is allocated on the first
     submission: failing each of its allocations in turn makes that call fail with SPIIR_ENOMEM,
