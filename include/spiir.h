@@ -332,7 +332,8 @@ int spiir_frontend_reset(spiir_frontend_t fe, void *stream);
 /* One segment: strain_dev [n_det][strain_pitch] f32 at the input rate, n_in samples (a positive
  * multiple of M, at most max_in); out_dev [n_det][out_pitch] f32 receives the n_in / M
  * whitened samples at the output rate.  Continues the stream of the previous call.  Two
- * launches on stream.  Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
+ * launches on stream, the second a programmatic dependent launch of the first.
+ * Errors: SPIIR_EINVAL, SPIIR_ECUDA. */
 int spiir_frontend_run(spiir_frontend_t fe, const float *strain_dev, int64_t strain_pitch,
                        int64_t n_in, float *out_dev, int64_t out_pitch, void *stream);
 
