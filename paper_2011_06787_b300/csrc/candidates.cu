@@ -62,8 +62,7 @@ __device__ __forceinline__ float mag2_rn(float2 z) { return __fadd_rn(__fmul_rn(
 __global__ void __launch_bounds__(kSelBlock) k_select(const float2 *__restrict__ snr, int64_t pitch, int64_t off,
                                                      int T, int n_det, int n, int n_cols, int n_chunks,
                                                      u64 *__restrict__ keys) {
-    // the compaction grid may be scheduled now; it waits for this grid's completion
-    asm volatile("griddepcontrol.launch_dependents;");
+    grid_dependents_trigger();  // the compaction grid may be scheduled now
     const int lane = threadIdx.x & 31;
     const int task = blockIdx.x * (kSelBlock / 32) + (threadIdx.x >> 5);
     if (task >= n_cols * n_det * n_chunks) return;
@@ -147,8 +146,7 @@ __global__ void __launch_bounds__(kCompThreads) k_compact(u64 *__restrict__ keys
     __shared__ int s_warp[32];
     __shared__ int s_total;
     __shared__ bool s_last;
-    // k_select's keys are complete and visible after this
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    grid_dependency_wait();  // k_select's keys are complete and visible after this
     const int i = blockIdx.x * kCompThreads + (int)threadIdx.x;
     if (i < n_det * n) {
         const u64 kv = __ldcg(reinterpret_cast<const unsigned long long *>(keys + i));
@@ -235,6 +233,7 @@ __device__ __forceinline__ void take(Best &a, float v, int p, float nul) {
 
 template <int ND, bool SMEM_TAB>
 __global__ void __launch_bounds__(kPtThreads) k_points(const __grid_constant__ PointArgs a) {
+    grid_dependency_wait();  // the candidate records and count come from the previous kernel
     using Entry = TabEntry<ND>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Best s_red[kPtThreads / 32];
@@ -467,6 +466,7 @@ __device__ __forceinline__ void stage_item(const PointArgs &a, const PtItem<ND> 
 
 template <int ND, int S, int WP>
 __global__ void __launch_bounds__(kPtChunkThreads, 4) k_points_chunked(const __grid_constant__ PointArgs a) {
+    grid_dependency_wait();  // the candidate records and count come from the previous kernel
     using Entry = TabEntry<ND>;
     constexpr int NC = ND - 1;                    // companions of the reference detector
     constexpr int kShiftWords = NC * WP;          // float2 entries per shift
@@ -635,8 +635,7 @@ static int launch_chunked(const PointArgs &a, size_t smem, cudaStream_t stream) 
     SPIIR_TRY(resident_blocks(kern, kPtChunkThreads, smem, kPtChunkSmem, n_sm, per_sm));
     const int64_t items = (int64_t)a.max_cand * ((a.n_shifts + S - 1) / S);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
-    kern<<<grid, kPtChunkThreads, smem, stream>>>(a);
-    SPIIR_CUDA_TRY(cudaGetLastError());
+    SPIIR_CUDA_TRY(launch_dependent(kern, dim3(grid), dim3(kPtChunkThreads), smem, stream, a));
     return SPIIR_OK;
 }
 
@@ -667,8 +666,7 @@ static int launch_points(const PointArgs &a, size_t smem, cudaStream_t stream) {
     SPIIR_TRY(resident_blocks(kern, kPtThreads, smem, kPtMaxSmem, n_sm, per_sm));
     const int64_t items = (int64_t)a.max_cand * a.n_shifts;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(per_sm, 1)));
-    kern<<<grid, kPtThreads, smem, stream>>>(a);
-    SPIIR_CUDA_TRY(cudaGetLastError());
+    SPIIR_CUDA_TRY(launch_dependent(kern, dim3(grid), dim3(kPtThreads), smem, stream, a));
     return SPIIR_OK;
 }
 
@@ -828,18 +826,9 @@ extern "C" int spiir_select_candidates(int T, int n_det, const float *snr, int64
     SPIIR_CUDA_TRY(cudaGetLastError());
     // programmatic dependent launch: the compaction blocks are scheduled while the selection
     // drains and wait for its completion
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(((int64_t)n_det * n + kCompThreads - 1) / kCompThreads));
-    cfg.blockDim = dim3(kCompThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    SPIIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_compact, keys, (int)n, n_det, T, thr2, per_second, slots, (int)n_sec,
-                                      done, reinterpret_cast<int4 *>(cand), max_cand, n_cand));
+    SPIIR_CUDA_TRY(launch_dependent(k_compact, dim3((unsigned)(((int64_t)n_det * n + kCompThreads - 1) / kCompThreads)),
+                                    dim3(kCompThreads), 0, st, keys, (int)n, n_det, T, thr2, per_second, slots,
+                                    (int)n_sec, done, reinterpret_cast<int4 *>(cand), max_cand, n_cand));
     return SPIIR_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <cstdarg>
+#include <utility>
 
 #include "../../include/spiir.h"
 
@@ -86,6 +87,30 @@ __device__ __forceinline__ u64 sub2(u64 a, u64 b) {
     return d;
 }
 __device__ __forceinline__ u64 neg2(u64 a) { return a ^ 0x8000000080000000ull; }
+
+// Programmatic dependent launch.  A kernel launched with launch_dependent() may be scheduled
+// before the previous kernel on its stream has completed; it calls grid_dependency_wait()
+// before it reads anything that kernel wrote (without the launch attribute the wait returns at
+// once).  grid_dependents_trigger() lets the stream's next dependent launch be scheduled once
+// every block of this grid has called it or exited.
+__device__ __forceinline__ void grid_dependents_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                           cudaStream_t stream, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -56,8 +56,7 @@ __global__ void __launch_bounds__(kFeDecOut) k_fe_decimate(const float *__restri
                                                            const float *__restrict__ hist_in, float *__restrict__ hist_out,
                                                            const float *__restrict__ taps, int Ld, int M,
                                                            float *__restrict__ dec, int64_t dec_pitch) {
-    // the whitening grid may be scheduled now; it waits for this grid before reading its output
-    asm volatile("griddepcontrol.launch_dependents;");
+    grid_dependents_trigger();  // the whitening grid may be scheduled now
     extern __shared__ float fe_smem[];
     const int det = blockIdx.y;
     const int L1 = Ld - 1;
@@ -110,7 +109,7 @@ __global__ void __launch_bounds__(kFeWhThreads) k_fe_whiten(const float *__restr
     for (int i = threadIdx.x; i < L; i += kFeWhThreads) w[i] = tw[i];
     // launched as a programmatic dependent of the decimation: its output is complete and
     // visible after this (the taps above do not depend on it)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    grid_dependency_wait();
     for (int i = threadIdx.x; i < W; i += kFeWhThreads) xs[i] = cat_at(hr, L1, dr, n, k0 + i);
     __syncthreads();
     const int og = threadIdx.x % (kFeWhOut / kFeWhQ), sl = threadIdx.x / (kFeWhOut / kFeWhQ);
@@ -338,19 +337,10 @@ extern "C" int spiir_frontend_run(spiir_frontend_t f, const float *strain, int64
     SPIIR_CUDA_TRY(cudaGetLastError());
     // programmatic dependent launch: the whitening blocks stage their taps while the decimation
     // drains
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((n_out + kFeWhOut - 1) / kFeWhOut), (unsigned)f->n_det);
-    cfg.blockDim = dim3(kFeWhThreads);
-    cfg.dynamicSmemBytes = white_smem(f->Lw_pad);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    SPIIR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fe_whiten, (const float *)f->dec, dec_pitch, n_out,
-                                      (const float *)f->hist2[p], f->hist2[1 - p], (const float *)f->taps_w, f->Lw_pad,
-                                      out, out_pitch));
+    SPIIR_CUDA_TRY(launch_dependent(k_fe_whiten, dim3((unsigned)((n_out + kFeWhOut - 1) / kFeWhOut), (unsigned)f->n_det),
+                                    dim3(kFeWhThreads), white_smem(f->Lw_pad), s, (const float *)f->dec, dec_pitch,
+                                    n_out, (const float *)f->hist2[p], f->hist2[1 - p], (const float *)f->taps_w,
+                                    f->Lw_pad, out, out_pitch));
     f->par = 1 - p;
     return SPIIR_OK;
 }

@@ -217,6 +217,7 @@ __device__ __forceinline__ float xi_num(const float2 *__restrict__ row, const fl
 // read at its sample for every pixel and shift, so its xi^2 is evaluated once per item; the
 // companions at each shift's argmax pixel.
 __global__ void __launch_bounds__(256) k_xi2_points(const __grid_constant__ XiPointArgs a) {
+    grid_dependency_wait();  // the argmax pixels and the candidates come from earlier kernels
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     const int nc = min(*a.n_cand, a.max_cand);
@@ -304,6 +305,7 @@ __device__ __forceinline__ float xi_num_reg(const float2 *__restrict__ row, cons
 // shift).
 template <int NT, int ND>
 __global__ void __launch_bounds__(256) k_xi2_points_reg(const __grid_constant__ XiPointArgs a) {
+    grid_dependency_wait();  // the argmax pixels and the candidates come from earlier kernels
     constexpr int NC = ND - 1;
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
@@ -418,11 +420,8 @@ __global__ void __launch_bounds__(256) k_xi2_points_reg(const __grid_constant__ 
 
 template <int NT>
 static int launch_xi2_nd(int nd, int grid, const XiPointArgs &a, cudaStream_t st) {
-    switch (nd) {
-        case 2: k_xi2_points_reg<NT, 2><<<grid, 256, 0, st>>>(a); break;
-        case 3: k_xi2_points_reg<NT, 3><<<grid, 256, 0, st>>>(a); break;
-        default: k_xi2_points_reg<NT, 4><<<grid, 256, 0, st>>>(a); break;
-    }
+    auto kern = nd == 2 ? k_xi2_points_reg<NT, 2> : nd == 3 ? k_xi2_points_reg<NT, 3> : k_xi2_points_reg<NT, 4>;
+    SPIIR_CUDA_TRY(launch_dependent(kern, dim3(grid), dim3(256), 0, st, a));
     return SPIIR_OK;
 }
 
@@ -484,7 +483,7 @@ extern "C" int spiir_xi2_candidates(spiir_sky_t sky, int T, const float *snr, in
         const int NT = nt <= 4 ? 4 : nt <= 8 ? 8 : nt <= 12 ? 12 : 16;
         SPIIR_TRY(launch_xi2_reg(NT, nd, grid, a, (cudaStream_t)stream));
     } else {
-        k_xi2_points<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+        SPIIR_CUDA_TRY(launch_dependent(k_xi2_points, dim3(grid), dim3(256), 0, (cudaStream_t)stream, a));
     }
     SPIIR_CUDA_TRY(cudaGetLastError());
     return SPIIR_OK;
