@@ -391,7 +391,9 @@ int spiir_select_candidates(int n_templates, int n_det, const float *snr_dev, in
  * detector or template outside the sky or bank, is (NaN, -1, NaN).  Rows past the count are
  * not written.  For the background the SNR must hold first_shift + n_shifts - 1 times
  * (n_det - 1) shift_step samples of history before the earliest candidate, plus the sky's
- * delay range.  One persistent launch on stream; the count is read on the device.
+ * delay range.  One persistent launch on stream, a programmatic dependent launch (it may be
+ * scheduled before the stream's previous kernel completes and waits for it before reading);
+ * the count is read on the device.
  * Errors: SPIIR_EINVAL, SPIIR_EUNSUPPORTED (SNR windows above 200 KB of shared memory). */
 int spiir_coherent_candidates(spiir_sky_t sky, int n_templates, const float *snr_dev,
                               int64_t snr_pitch, int64_t snr_offset, const int32_t *cand_dev,
@@ -410,7 +412,8 @@ int spiir_coherent_candidates(spiir_sky_t sky, int n_templates, const float *snr
  * (1 / N_d) sum_J xi_J^2; xi2_det_dev, if not NULL, [max_cand][n_shifts][n_det] the
  * per-detector values.  NaN where p is not a pixel of the sky, the record names a detector or
  * template outside the sky or bank, or a read would leave [0, snr_pitch).  Rows past the count
- * are not written.  One persistent launch on stream.  Errors: SPIIR_EINVAL. */
+ * are not written.  One persistent launch on stream, a programmatic dependent launch as for
+ * spiir_coherent_candidates.  Errors: SPIIR_EINVAL. */
 int spiir_xi2_candidates(spiir_sky_t sky, int n_templates, const float *snr_dev, int64_t snr_pitch,
                          int64_t snr_offset, const float *A_dev, int n_lags, const int32_t *cand_dev,
                          const int32_t *n_cand_dev, int max_cand, int first_shift, int n_shifts,
